@@ -1,0 +1,803 @@
+/*
+ * logm_oracle.c -- plain, slow, obviously-correct FP64 CPU oracle for the
+ * inverse-scaling-and-squaring matrix logarithm with computation-graph
+ * polynomials of Jarlebring, Sastre and Ibanez, "Polynomial approximations
+ * for the matrix logarithm with computation graphs" (arXiv 2401.10089).
+ *
+ * TEST INFRASTRUCTURE. Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this file's library. It shares no code, header,
+ * table or helper with the CUDA library; every constant here is transcribed
+ * from the paper on its own.
+ *
+ * Every routine takes the algorithm's steps in the paper's order: no
+ * blocking, no fusion, no reordering. Matrices are dense, row-major, n x n.
+ * The only parallelism is one OpenMP thread per matrix of a batch.
+ *
+ * Readings of passages the paper leaves open (each also listed in the design
+ * notes of the repository):
+ *  - every norm is the 1-norm (Sec. 6, the estimator it cites is a 1-norm
+ *    estimator); ||A - I|| and ||A_I2|| are exact, powers are estimated;
+ *  - the estimator is Hager's method with Higham's refinements (Higham 1988,
+ *    cited in Sec. 6), one vector, at most 5 sweeps, ties broken at the
+ *    smallest index, sign(0) = +1, plus the alternating-sign extra test;
+ *  - with s = 0 there is no A_I2 yet, so the powers are applied with A - I;
+ *  - comparisons "x^{1/m} <= Theta" are made as "x <= Theta^m", both sides
+ *    formed by repeated multiplication, so that the decision is exact;
+ *  - the Denman-Beavers stop rule is not given: stop when the relative
+ *    change of X in the 1-norm is <= 10 sqrt(n) u, or, once scaling is off
+ *    and the change has reached 1e-7, when it no longer halves; scaling by
+ *    mu is switched off once the change drops below 1e-2;
+ *  - only k = 1, 2 (exact Taylor, eq. Taylor_log) and k = 5 (Table
+ *    table_simple_experiment) have coefficients, so k_max <= 5.
+ */
+#include "logm_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_U 0x1p-53 /* unit roundoff of IEEE binary64 */
+
+int orc_version(void) { return 1; }
+
+/* ------------------------------------------------------------------------ */
+/* Coefficients of the degree-optimal form, eq. (five_mult_degopt).         */
+/* ------------------------------------------------------------------------ */
+
+/* Table table_simple_experiment (Sec. 3): k = 5, fitted to -log(1 - x). */
+static const double K5_H[14] = {
+    7.363757032799957e-02,  -1.050281301619960e+00,                         /* h_{2,2..3} */
+    8.897468955192446e-02,  -1.599651928992725e-01, 9.577281350989334e-01,  /* h_{3,2..4} */
+    5.394999133948797e-01,  6.700731102561937e-02,  -5.158769100223212e-02,
+    1.094308587350110e+00,                                                  /* h_{4,2..5} */
+    1.027072285939197e-01,  -8.964023050065877e-03, -2.100705663612491e-01,
+    1.949655359168707e-01,  1.117368056772713e+00};                         /* h_{5,2..6} */
+static const double K5_G[14] = {
+    -9.666134174379001e-01, -4.395519034717933e-01,                         /* g_{2,2..3} */
+    1.048664069004776e-01,  1.585606124033259e-01,  1.668066506920988e-01,  /* g_{3,2..4} */
+    -8.025600931705978e-02, -1.159854366397558e-01, 1.066554944706011e-01,
+    1.127094008297975e+00,                                                  /* g_{4,2..5} */
+    2.702180425508705e-01,  4.137541209720699e-02,  4.857347452405025e-01,
+    -6.000256005636980e-01, 1.063393233943084e+00};                         /* g_{5,2..6} */
+static const double K5_Y[7] = {0.0,
+                               1.0,
+                               5.065546620208965e-01,
+                               3.832512052972577e-01,
+                               1.088307723749078e+00,
+                               2.787461897212877e-01,
+                               8.157421998489228e-01};
+
+void orc_coeffs_k5(double* h, double* g, double* y) {
+  memcpy(h, K5_H, sizeof(K5_H));
+  memcpy(g, K5_G, sizeof(K5_G));
+  memcpy(y, K5_Y, sizeof(K5_Y));
+}
+
+/* A degree-optimal scheme with k products: P_1 = I, P_2 = X and, for
+ * j = 1..k, P_{j+2} = (sum_{i=1}^{j+1} h_{j,i} P_i)(sum_{i=1}^{j+1} g_{j,i} P_i);
+ * z = sum_{i=1}^{k+2} y_i P_i (eq. five_mult_degopt). Indices are 1-based in
+ * the arrays below (entry 0 unused) so that they read like the paper. */
+typedef struct {
+  int k;
+  double h[6][8];
+  double g[6][8];
+  double y[8];
+} orc_scheme;
+
+static void scheme_for(int k, orc_scheme* S) {
+  memset(S, 0, sizeof(*S));
+  S->k = k;
+  /* Theorem of Sec. 3: h_{1,2} = g_{1,2} = 1, h_{1,1} = g_{1,1} = 0, so P_3 = X^2. */
+  S->h[1][2] = 1.0;
+  S->g[1][2] = 1.0;
+  if (k == 1) {
+    /* Taylor T_2 of eq. (Taylor_log): z = X + X^2/2. */
+    S->y[2] = 1.0;
+    S->y[3] = 0.5;
+  } else if (k == 2) {
+    /* Taylor T_4: P_4 = X^2 (X/3 + X^2/4) = X^3/3 + X^4/4; z = X + X^2/2 + P_4. */
+    S->h[2][3] = 1.0;
+    S->g[2][2] = 1.0 / 3.0;
+    S->g[2][3] = 0.25;
+    S->y[2] = 1.0;
+    S->y[3] = 0.5;
+    S->y[4] = 1.0;
+  } else if (k == 5) {
+    int t = 0;
+    for (int j = 2; j <= 5; ++j)
+      for (int i = 2; i <= j + 1; ++i, ++t) {
+        S->h[j][i] = K5_H[t];
+        S->g[j][i] = K5_G[t];
+      }
+    for (int i = 1; i <= 7; ++i) S->y[i] = K5_Y[i - 1];
+  }
+}
+
+/* m_k of Table Table_theta for the schemes that have coefficients. */
+static int m_of_k(int k) { return k == 1 ? 2 : (k == 2 ? 4 : 14); }
+
+static int theta_index(int k) { return k == 1 ? 0 : (k == 2 ? 1 : 2); }
+
+/* ------------------------------------------------------------------------ */
+/* Dense linear algebra, textbook forms.                                    */
+/* ------------------------------------------------------------------------ */
+
+static double* alloc_mat(int n) { return (double*)malloc(sizeof(double) * (size_t)n * (size_t)n); }
+
+static void set_identity(int n, double* A) {
+  memset(A, 0, sizeof(double) * (size_t)n * (size_t)n);
+  for (int i = 0; i < n; ++i) A[(size_t)i * n + i] = 1.0;
+}
+
+/* C = A B by the definition c_ij = sum_l a_il b_lj. */
+void orc_gemm(int n, const double* A, const double* B, double* C) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double acc = 0.0;
+      for (int l = 0; l < n; ++l) acc += A[(size_t)i * n + l] * B[(size_t)l * n + j];
+      C[(size_t)i * n + j] = acc;
+    }
+}
+
+/* ||A||_1 = max_j sum_i |a_ij|. */
+double orc_norm1(int n, const double* A) {
+  double best = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += fabs(A[(size_t)i * n + j]);
+    if (s > best || isnan(s)) best = s;
+  }
+  return best;
+}
+
+/* In-place LU with partial pivoting, P A = L U (unit lower L). piv[k] is the
+ * row swapped with row k at step k. Returns 0, or k+1 if the pivot of column
+ * k is exactly zero. */
+int orc_lu(int n, double* LU, int32_t* piv) {
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = fabs(LU[(size_t)k * n + k]);
+    for (int i = k + 1; i < n; ++i) {
+      double v = fabs(LU[(size_t)i * n + k]);
+      if (v > best) {
+        best = v;
+        p = i;
+      }
+    }
+    piv[k] = p;
+    if (best == 0.0) return k + 1;
+    if (p != k)
+      for (int j = 0; j < n; ++j) {
+        double t = LU[(size_t)k * n + j];
+        LU[(size_t)k * n + j] = LU[(size_t)p * n + j];
+        LU[(size_t)p * n + j] = t;
+      }
+    double d = LU[(size_t)k * n + k];
+    for (int i = k + 1; i < n; ++i) {
+      double l = LU[(size_t)i * n + k] / d;
+      LU[(size_t)i * n + k] = l;
+      for (int j = k + 1; j < n; ++j) LU[(size_t)i * n + j] -= l * LU[(size_t)k * n + j];
+    }
+  }
+  return 0;
+}
+
+/* A^{-1} column by column from P A = L U (left division A \ I), and
+ * log|det A| = sum_k log|u_kk|. Returns ORC_OK or ORC_SINGULAR. */
+int orc_inverse(int n, const double* A, double* Ainv, double* logabsdet) {
+  double* LU = alloc_mat(n);
+  int32_t* piv = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  double* col = (double*)malloc(sizeof(double) * (size_t)n);
+  memcpy(LU, A, sizeof(double) * (size_t)n * (size_t)n);
+  int r = orc_lu(n, LU, piv);
+  int status = ORC_OK;
+  if (r != 0) {
+    status = ORC_SINGULAR;
+    for (size_t t = 0; t < (size_t)n * n; ++t) Ainv[t] = NAN;
+    if (logabsdet) *logabsdet = -INFINITY;
+  } else {
+    if (logabsdet) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k) s += log(fabs(LU[(size_t)k * n + k]));
+      *logabsdet = s;
+    }
+    for (int c = 0; c < n; ++c) {
+      /* b = P e_c */
+      for (int i = 0; i < n; ++i) col[i] = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < n; ++k) {
+        double t = col[k];
+        col[k] = col[piv[k]];
+        col[piv[k]] = t;
+      }
+      /* forward substitution with unit L */
+      for (int i = 0; i < n; ++i) {
+        double s = col[i];
+        for (int l = 0; l < i; ++l) s -= LU[(size_t)i * n + l] * col[l];
+        col[i] = s;
+      }
+      /* back substitution with U */
+      for (int i = n - 1; i >= 0; --i) {
+        double s = col[i];
+        for (int l = i + 1; l < n; ++l) s -= LU[(size_t)i * n + l] * col[l];
+        col[i] = s / LU[(size_t)i * n + i];
+      }
+      for (int i = 0; i < n; ++i) Ainv[(size_t)i * n + c] = col[i];
+    }
+  }
+  free(LU);
+  free(piv);
+  free(col);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Scaled Denman-Beavers square root, eq. (ScalDB), Sec. 6.                 */
+/* X_{k+1} = (mu_k X_k + mu_k^{-1} Y_k^{-1}) / 2,                           */
+/* Y_{k+1} = (mu_k Y_k + mu_k^{-1} X_k^{-1}) / 2,                           */
+/* X_0 = A, Y_0 = I, mu_k = |det X_k det Y_k|^{-1/(2n)}.                    */
+/* ------------------------------------------------------------------------ */
+int orc_sqrtm_db(int n, const double* A, double* Xout, int max_iter, int32_t* iters) {
+  double* X = alloc_mat(n);
+  double* Y = alloc_mat(n);
+  double* Xi = alloc_mat(n);
+  double* Yi = alloc_mat(n);
+  double* Xn = alloc_mat(n);
+  double* D = alloc_mat(n);
+  memcpy(X, A, sizeof(double) * (size_t)n * n);
+  set_identity(n, Y);
+  const double tol = 10.0 * sqrt((double)n) * ORC_U;
+  int scale = 1, status = ORC_NO_CONVERGENCE, it = 0;
+  double dprev = INFINITY;
+  const size_t nn = (size_t)n * n;
+  for (it = 1; it <= max_iter; ++it) {
+    double ldx, ldy;
+    if (orc_inverse(n, X, Xi, &ldx) != ORC_OK || orc_inverse(n, Y, Yi, &ldy) != ORC_OK) {
+      status = ORC_SINGULAR;
+      break;
+    }
+    /* mu = |det X det Y|^{-1/(2n)} = exp(-(log|det X| + log|det Y|)/(2n)). */
+    double mu = scale ? exp(-(ldx + ldy) / (2.0 * n)) : 1.0;
+    for (size_t t = 0; t < nn; ++t) {
+      Xn[t] = 0.5 * (mu * X[t] + Yi[t] / mu);
+      Y[t] = 0.5 * (mu * Y[t] + Xi[t] / mu);
+      D[t] = Xn[t] - X[t];
+    }
+    double delta = orc_norm1(n, D) / orc_norm1(n, Xn);
+    memcpy(X, Xn, sizeof(double) * nn);
+    if (!(delta == delta)) { /* NaN: give up */
+      status = ORC_NO_CONVERGENCE;
+      break;
+    }
+    if (delta <= tol) {
+      status = ORC_OK;
+      break;
+    }
+    if (!scale && dprev <= 1e-7 && delta > 0.5 * dprev) {
+      status = ORC_OK; /* converged to rounding level */
+      break;
+    }
+    if (delta < 1e-2) scale = 0;
+    dprev = delta;
+  }
+  if (iters) *iters = it > max_iter ? max_iter : it;
+  memcpy(Xout, X, sizeof(double) * nn);
+  free(X);
+  free(Y);
+  free(Xi);
+  free(Yi);
+  free(Xn);
+  free(D);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 1-norm estimate of M = B^p (Higham 1988, cited in Sec. 6).               */
+/* With A_I2 = B^2 given (eq. AI2), M = B^{p mod 2} (A_I2)^{p div 2}, which */
+/* needs fewer matrix-vector products (Sec. 6, item 2).                     */
+/* ------------------------------------------------------------------------ */
+
+static void matvec(int n, const double* M, const double* x, double* y, int trans) {
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int l = 0; l < n; ++l) s += (trans ? M[(size_t)l * n + i] : M[(size_t)i * n + l]) * x[l];
+    y[i] = s;
+  }
+}
+
+/* y = M x (trans = 0) or y = M^T x (trans = 1); tmp has n entries. */
+static void apply_power(int n, const double* B, const double* AI2, int p, const double* x,
+                        double* y, double* tmp, int trans) {
+  int q = AI2 ? (p & 1) : p;     /* factors of B */
+  int r = AI2 ? (p >> 1) : 0;    /* factors of A_I2 */
+  memcpy(y, x, sizeof(double) * (size_t)n);
+  if (!trans) {
+    /* M x = B^q (A_I2^r x) */
+    for (int t = 0; t < r; ++t) {
+      matvec(n, AI2, y, tmp, 0);
+      memcpy(y, tmp, sizeof(double) * (size_t)n);
+    }
+    for (int t = 0; t < q; ++t) {
+      matvec(n, B, y, tmp, 0);
+      memcpy(y, tmp, sizeof(double) * (size_t)n);
+    }
+  } else {
+    /* M^T x = (A_I2^T)^r (B^T)^q x */
+    for (int t = 0; t < q; ++t) {
+      matvec(n, B, y, tmp, 1);
+      memcpy(y, tmp, sizeof(double) * (size_t)n);
+    }
+    for (int t = 0; t < r; ++t) {
+      matvec(n, AI2, y, tmp, 1);
+      memcpy(y, tmp, sizeof(double) * (size_t)n);
+    }
+  }
+}
+
+static double vsum_abs(int n, const double* v) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += fabs(v[i]);
+  return s;
+}
+
+static int argmax_abs(int n, const double* v) {
+  int j = 0;
+  double best = fabs(v[0]);
+  for (int i = 1; i < n; ++i)
+    if (fabs(v[i]) > best) {
+      best = fabs(v[i]);
+      j = i;
+    }
+  return j;
+}
+
+double orc_normest_pow(int n, const double* B, const double* AI2, int p) {
+  if (n < 1) return 0.0;
+  double* x = (double*)malloc(sizeof(double) * (size_t)n);
+  double* y = (double*)malloc(sizeof(double) * (size_t)n);
+  double* z = (double*)malloc(sizeof(double) * (size_t)n);
+  double* xi = (double*)malloc(sizeof(double) * (size_t)n);
+  double* tmp = (double*)malloc(sizeof(double) * (size_t)n);
+  double est;
+  /* Start from x = e/n. */
+  for (int i = 0; i < n; ++i) x[i] = 1.0 / n;
+  apply_power(n, B, AI2, p, x, y, tmp, 0);
+  est = vsum_abs(n, y);
+  if (n > 1) {
+    for (int i = 0; i < n; ++i) xi[i] = (y[i] >= 0.0) ? 1.0 : -1.0;
+    apply_power(n, B, AI2, p, xi, z, tmp, 1);
+    int j = argmax_abs(n, z);
+    for (int sweep = 2; sweep <= 5; ++sweep) {
+      /* x = e_j */
+      for (int i = 0; i < n; ++i) x[i] = (i == j) ? 1.0 : 0.0;
+      apply_power(n, B, AI2, p, x, y, tmp, 0);
+      double est_new = vsum_abs(n, y);
+      int same_sign = 1;
+      for (int i = 0; i < n; ++i) {
+        double sg = (y[i] >= 0.0) ? 1.0 : -1.0;
+        if (sg != xi[i]) same_sign = 0;
+      }
+      if (same_sign || est_new <= est) {
+        if (est_new > est) est = est_new;
+        break;
+      }
+      est = est_new;
+      for (int i = 0; i < n; ++i) xi[i] = (y[i] >= 0.0) ? 1.0 : -1.0;
+      apply_power(n, B, AI2, p, xi, z, tmp, 1);
+      int jlast = j;
+      j = argmax_abs(n, z);
+      if (fabs(z[jlast]) == fabs(z[j])) break; /* no new column to try */
+    }
+    /* Extra test with x_i = (-1)^i (1 + i/(n-1)), i = 0..n-1. */
+    for (int i = 0; i < n; ++i) x[i] = ((i & 1) ? -1.0 : 1.0) * (1.0 + (double)i / (double)(n - 1));
+    apply_power(n, B, AI2, p, x, y, tmp, 0);
+    double alt = 2.0 * vsum_abs(n, y) / (3.0 * n);
+    if (alt > est) est = alt;
+  }
+  free(x);
+  free(y);
+  free(z);
+  free(xi);
+  free(tmp);
+  return est;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Computation-graph evaluation, eq. (five_mult_degopt).                    */
+/* ------------------------------------------------------------------------ */
+
+/* Z = z(X) for the scheme with k products. P3 may be NULL (then P_3 = X X is
+ * formed by one product) or the caller's X^2 (Algorithm 1 saves that
+ * product with A_I2 when s >= 1). Returns 0, or -1 for an unsupported k. */
+int orc_graph_eval(int n, int k, const double* X, const double* P3, double* Z) {
+  if (k != 1 && k != 2 && k != 5) return -1;
+  orc_scheme S;
+  scheme_for(k, &S);
+  const size_t nn = (size_t)n * n;
+  double* P[8] = {0};
+  for (int i = 1; i <= k + 2; ++i) P[i] = alloc_mat(n);
+  double* Lf = alloc_mat(n);
+  double* Rf = alloc_mat(n);
+  set_identity(n, P[1]);
+  memcpy(P[2], X, sizeof(double) * nn);
+  for (int j = 1; j <= k; ++j) {
+    if (j == 1 && P3) {
+      memcpy(P[3], P3, sizeof(double) * nn);
+      continue;
+    }
+    for (size_t t = 0; t < nn; ++t) {
+      double l = 0.0, r = 0.0;
+      for (int i = 1; i <= j + 1; ++i) {
+        l += S.h[j][i] * P[i][t];
+        r += S.g[j][i] * P[i][t];
+      }
+      Lf[t] = l;
+      Rf[t] = r;
+    }
+    orc_gemm(n, Lf, Rf, P[j + 2]);
+  }
+  for (size_t t = 0; t < nn; ++t) {
+    double acc = 0.0;
+    for (int i = 1; i <= k + 2; ++i) acc += S.y[i] * P[i][t];
+    Z[t] = acc;
+  }
+  for (int i = 1; i <= k + 2; ++i) free(P[i]);
+  free(Lf);
+  free(Rf);
+  return 0;
+}
+
+/* Z = sum_{i=0}^{deg} b_i X^i by Horner's rule (test cross-check only). */
+void orc_horner(int n, int deg, const double* b, const double* X, double* Z) {
+  const size_t nn = (size_t)n * n;
+  double* T = alloc_mat(n);
+  memset(Z, 0, sizeof(double) * nn);
+  for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = b[deg];
+  for (int d = deg - 1; d >= 0; --d) {
+    orc_gemm(n, Z, X, T);
+    for (size_t t = 0; t < nn; ++t) Z[t] = T[t];
+    for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] += b[d];
+  }
+  free(T);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Backward-error test alpha_m <= Theta, eqs. (alphaapprox), (normAm9),     */
+/* (alpha2term1), (normAm9plus1) of Sec. 6.                                  */
+/* ------------------------------------------------------------------------ */
+
+static double ipow(double x, int m) {
+  double r = 1.0;
+  for (int i = 0; i < m; ++i) r *= x;
+  return r;
+}
+
+typedef struct {
+  double t_m;   /* estimate of ||B^m||_1 or -1 */
+  double t_m1;  /* estimate of ||B^{m+1}||_1 or -1 */
+  int m;        /* m these estimates belong to */
+  int n_est;    /* estimator calls made */
+} est_state;
+
+/* Returns 1 when alpha_m <= theta. *alpha gets max(term1^{1/m},
+ * term2^{1/(m+1)}) of the values used (estimates or bounds; term2 only if it
+ * was needed). AI2 NULL means s = 0: powers are applied with B. */
+static int alpha_test(int n, const double* B, const double* AI2, double nB, double nI2, int m,
+                      double theta, est_state* st, double* alpha) {
+  const double th_m = ipow(theta, m), th_m1 = ipow(theta, m + 1);
+  double t1, t2;
+  int have_est1 = 0;
+  st->m = m;
+  st->t_m = -1.0;
+  st->t_m1 = -1.0;
+  /* First term ||B^m||: with A_I2, bounded by ||A_I2||^{m/2} (eq. normAm9). */
+  if (AI2 && m == 2) {
+    t1 = nI2; /* B^2 = A_I2 exactly */
+  } else if (AI2 && ipow(nI2, m / 2) <= th_m) {
+    t1 = ipow(nI2, m / 2); /* eq. (alpha2term1): no estimate needed */
+  } else {
+    t1 = orc_normest_pow(n, B, AI2, m);
+    st->n_est++;
+    st->t_m = t1;
+    have_est1 = 1;
+  }
+  if (!(t1 <= th_m)) {
+    *alpha = pow(t1, 1.0 / m);
+    return 0;
+  }
+  /* Second term ||B^{m+1}|| <= ||B^m|| ||B|| (eq. normAm9plus1), with the
+   * estimate of ||B^m|| when there is one, else ||A_I2||^{m/2}. */
+  double base = have_est1 ? t1 : (AI2 ? ipow(nI2, m / 2) : t1);
+  if (base * nB <= th_m1) {
+    t2 = base * nB;
+  } else {
+    t2 = orc_normest_pow(n, B, AI2, m + 1);
+    st->n_est++;
+    st->t_m1 = t2;
+  }
+  double a1 = pow(t1, 1.0 / m), a2 = pow(t2, 1.0 / (m + 1));
+  *alpha = a1 > a2 ? a1 : a2;
+  return t2 <= th_m1;
+}
+
+/* Order search of Sec. 6 (Step 'StepFinminm' of Algorithm 1), read as:
+ *  min_im from the last loop pass's estimates (eqs. min_in, min_inp);
+ *  max_in = first k whose rough bound passes (eqs. alpharoughbound_even,
+ *  roughmax_even; every available m_k is even);
+ *  if min_im >= max_in take max_in, else test k = min_im.. in turn, taking
+ *  k+1 at once when alpha_{m_k} > Theta_k but <= Theta_{k+1}. */
+static int order_search(int n, const double* B, const double* AI2, double nB, double nI2,
+                        const orc_opts* o, const est_state* loop_est, int* n_est) {
+  int cands[3], nc = 0;
+  const int all[3] = {1, 2, 5};
+  for (int t = 0; t < 3; ++t)
+    if (all[t] <= o->k_max) cands[nc++] = all[t];
+  if (nc == 0) return o->k_max;
+  /* min_im */
+  int lo = 0;
+  if (loop_est && loop_est->t_m >= 0.0) {
+    int mm = loop_est->m;
+    while (lo < nc - 1) {
+      double th = o->theta[theta_index(cands[lo])];
+      int ok = loop_est->t_m <= ipow(th, mm);
+      if (ok && loop_est->t_m1 >= 0.0) ok = loop_est->t_m1 <= ipow(th, mm + 1);
+      if (ok) break;
+      ++lo;
+    }
+  }
+  /* max_in */
+  int hi = nc - 1;
+  for (int t = 0; t < nc; ++t) {
+    int m = m_of_k(cands[t]);
+    double th = o->theta[theta_index(cands[t])];
+    if (ipow(nI2, m / 2) * nB <= ipow(th, m + 1)) {
+      hi = t;
+      break;
+    }
+  }
+  if (lo >= hi) return cands[hi];
+  for (int t = lo; t < hi; ++t) {
+    int m = m_of_k(cands[t]);
+    double th = o->theta[theta_index(cands[t])];
+    est_state st = {-1.0, -1.0, m, 0};
+    double a;
+    int ok = alpha_test(n, B, AI2, nB, nI2, m, th, &st, &a);
+    *n_est += st.n_est;
+    if (ok) return cands[t];
+    /* alpha_{m_k} <= Theta_{k+1} gives alpha_{m_{k+1}} <= Theta_{k+1}. */
+    double thn = o->theta[theta_index(cands[t + 1])];
+    double t1 = (st.t_m >= 0.0) ? st.t_m : (m == 2 ? nI2 : ipow(nI2, m / 2));
+    if (t1 <= ipow(thn, m)) {
+      double t2 = st.t_m1;
+      if (t2 < 0.0) {
+        if (t1 * nB <= ipow(thn, m + 1)) {
+          t2 = t1 * nB;
+        } else {
+          t2 = orc_normest_pow(n, B, AI2, m + 1);
+          *n_est += 1;
+        }
+      }
+      if (t2 <= ipow(thn, m + 1)) return cands[t + 1];
+    }
+  }
+  return cands[hi];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Plan alone: one pass of the while-loop test of Algorithm 1 at the given  */
+/* A (with A_I2 when s >= 1, else NULL), then the order search.             */
+/* ------------------------------------------------------------------------ */
+int orc_plan(int n, const double* A, const double* AI2in, const orc_opts* o, int32_t* finish,
+             int32_t* k, double* alpha) {
+  const size_t nn = (size_t)n * n;
+  double* B = alloc_mat(n);
+  double* AI2 = alloc_mat(n);
+  memcpy(B, A, sizeof(double) * nn);
+  for (int i = 0; i < n; ++i) B[(size_t)i * n + i] -= 1.0;
+  double nB = orc_norm1(n, B);
+  if (!isfinite(nB)) {
+    *finish = 0;
+    *k = o->k_max;
+    *alpha = NAN;
+    free(B);
+    free(AI2);
+    return ORC_NONFINITE;
+  }
+  const int m = m_of_k(o->k_max);
+  const double th = o->theta[theta_index(o->k_max)];
+  est_state st = {-1.0, -1.0, m, 0};
+  int fin;
+  double a;
+  if (!AI2in && nB <= th) {
+    fin = 1; /* finish = ||A - I|| <= Theta (Algorithm 1, before the loop) */
+    a = nB;
+  } else {
+    double nI2 = AI2in ? orc_norm1(n, AI2in) : 0.0;
+    fin = alpha_test(n, B, AI2in, nB, nI2, m, th, &st, &a);
+  }
+  *finish = fin;
+  *alpha = a;
+  if (AI2in)
+    memcpy(AI2, AI2in, sizeof(double) * nn);
+  else
+    orc_gemm(n, B, B, AI2);
+  int ne = 0;
+  *k = fin ? order_search(n, B, AI2, nB, orc_norm1(n, AI2), o, &st, &ne) : o->k_max;
+  free(B);
+  free(AI2);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 with T = I (no balancing).                                   */
+/* ------------------------------------------------------------------------ */
+int orc_logm(int n, const double* A, double* L, const orc_opts* o, orc_diag* d) {
+  const size_t nn = (size_t)n * n;
+  orc_diag dd;
+  memset(&dd, 0, sizeof(dd));
+  for (size_t t = 0; t < nn; ++t)
+    if (!isfinite(A[t])) {
+      for (size_t u = 0; u < nn; ++u) L[u] = NAN;
+      dd.info = ORC_NONFINITE;
+      dd.k = o->k_max;
+      if (d) *d = dd;
+      return ORC_NONFINITE;
+    }
+  double* Acur = alloc_mat(n);
+  double* A2 = alloc_mat(n);
+  double* B = alloc_mat(n);
+  double* AI2 = alloc_mat(n);
+  double* Z = alloc_mat(n);
+  memcpy(Acur, A, sizeof(double) * nn);
+  memcpy(B, A, sizeof(double) * nn);
+  for (int i = 0; i < n; ++i) B[(size_t)i * n + i] -= 1.0;
+  double nB = orc_norm1(n, B), nI2 = 0.0;
+  int have_ai2 = 0, s = 0, info = ORC_OK;
+  const int m = m_of_k(o->k_max);
+  const double th = o->theta[theta_index(o->k_max)];
+  est_state last = {-1.0, -1.0, m, 0};
+  int finish;
+  double alpha = nB;
+  if (o->force_s >= 0)
+    finish = (o->force_s == 0);
+  else
+    finish = nB <= th; /* finish = ||A - I|| <= Theta_{m_kmax} */
+  while (!finish && s < o->max_sqrt) {
+    if (o->force_s < 0) {
+      est_state st = {-1.0, -1.0, m, 0};
+      finish = alpha_test(n, B, have_ai2 ? AI2 : NULL, nB, nI2, m, th, &st, &alpha);
+      dd.n_estimates += st.n_est;
+      last = st;
+      if (finish) break;
+    }
+    /* A_2 <- A; A <- A^{1/2} by eq. (ScalDB); A_I2 = A_2 - 2A + I (eq. AI2). */
+    memcpy(A2, Acur, sizeof(double) * nn);
+    int32_t it = 0;
+    int r = orc_sqrtm_db(n, A2, Acur, o->max_db_iter, &it);
+    dd.db_iters += it;
+    if (r == ORC_SINGULAR) {
+      info = ORC_SINGULAR;
+      break;
+    }
+    if (r == ORC_NO_CONVERGENCE && info == ORC_OK) info = ORC_NO_CONVERGENCE;
+    for (size_t t = 0; t < nn; ++t) AI2[t] = A2[t] - 2.0 * Acur[t];
+    for (int i = 0; i < n; ++i) AI2[(size_t)i * n + i] += 1.0;
+    memcpy(B, Acur, sizeof(double) * nn);
+    for (int i = 0; i < n; ++i) B[(size_t)i * n + i] -= 1.0;
+    nB = orc_norm1(n, B);
+    nI2 = orc_norm1(n, AI2);
+    have_ai2 = 1;
+    ++s;
+    if (o->force_s >= 0) finish = (s >= o->force_s);
+  }
+  if (info == ORC_SINGULAR) {
+    for (size_t t = 0; t < nn; ++t) L[t] = NAN;
+  } else {
+    if (!finish && info == ORC_OK) info = ORC_MAX_SQRT;
+    if (!have_ai2) { /* s = 0: A_I2 = (A - I)^2 by one product */
+      orc_gemm(n, B, B, AI2);
+      nI2 = orc_norm1(n, AI2);
+    }
+    int k;
+    if (o->force_k > 0) {
+      k = o->force_k;
+    } else if (!finish) {
+      k = o->k_max;
+    } else {
+      int ne = 0;
+      k = order_search(n, B, AI2, nB, nI2, o, (last.t_m >= 0.0) ? &last : NULL, &ne);
+      dd.n_estimates += ne;
+    }
+    /* L = -2^s z(X) with X = -(A - I) and P_3 = X^2 = A_I2 (eq. logipASTM). */
+    double* X = A2;
+    for (size_t t = 0; t < nn; ++t) X[t] = -B[t];
+    orc_graph_eval(n, k, X, AI2, Z);
+    for (size_t t = 0; t < nn; ++t) L[t] = -ldexp(Z[t], s);
+    dd.k = k;
+  }
+  dd.s = s;
+  dd.info = info;
+  dd.alpha = alpha;
+  dd.norm_b = nB;
+  dd.norm_ai2 = nI2;
+  if (d) *d = dd;
+  free(Acur);
+  free(A2);
+  free(B);
+  free(AI2);
+  free(Z);
+  return info;
+}
+
+int orc_logm_batch(int count, const int32_t* n, const int64_t* offset, const double* A,
+                   double* L, const orc_opts* o, orc_diag* d, int nthreads) {
+  int worst = ORC_OK;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(max : worst)
+#endif
+  for (int b = 0; b < count; ++b) {
+    int r = orc_logm(n[b], A + offset[b], L + offset[b], o, d ? d + b : NULL);
+    if (r > worst) worst = r;
+  }
+  (void)nthreads;
+  return worst;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Independent checks.                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* exp(A) by Taylor scaling and squaring: scale by 2^-j so ||A/2^j||_1 <= 1/2,
+ * Taylor degree 18 by Horner's rule, then square j times. (Test cross-check;
+ * not part of the paper's method.) */
+void orc_expm_taylor(int n, const double* A, double* E) {
+  const size_t nn = (size_t)n * n;
+  double nrm = orc_norm1(n, A);
+  int j = 0;
+  while (ldexp(nrm, -j) > 0.5) ++j;
+  double* As = alloc_mat(n);
+  double* T = alloc_mat(n);
+  for (size_t t = 0; t < nn; ++t) As[t] = ldexp(A[t], -j);
+  /* E = I + As/1 (I + As/2 (I + ... (I + As/18))) */
+  set_identity(n, E);
+  for (int d = 18; d >= 1; --d) {
+    orc_gemm(n, As, E, T);
+    for (size_t t = 0; t < nn; ++t) E[t] = T[t] / d;
+    for (int i = 0; i < n; ++i) E[(size_t)i * n + i] += 1.0;
+  }
+  for (int r = 0; r < j; ++r) {
+    orc_gemm(n, E, E, T);
+    memcpy(E, T, sizeof(double) * nn);
+  }
+  free(As);
+  free(T);
+}
+
+/* G = L(A^T, W), the adjoint of the Frechet derivative of log at A applied
+ * to W, read off the top-right block of log([[A^T, tW], [0, A^T]]) / t. */
+int orc_frechet_adjoint(int n, const double* A, const double* W, double* G, const orc_opts* o) {
+  const int N = 2 * n;
+  double* M = alloc_mat(N);
+  double* LM = alloc_mat(N);
+  memset(M, 0, sizeof(double) * (size_t)N * N);
+  double na = orc_norm1(n, A), nw = orc_norm1(n, W);
+  double t = (nw > 0.0) ? na / nw : 1.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double at = A[(size_t)j * n + i];
+      M[(size_t)i * N + j] = at;
+      M[(size_t)(i + n) * N + (j + n)] = at;
+      M[(size_t)i * N + (j + n)] = t * W[(size_t)i * n + j];
+    }
+  orc_diag dd;
+  int r = orc_logm(N, M, LM, o, &dd);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) G[(size_t)i * n + j] = LM[(size_t)i * N + (j + n)] / t;
+  free(M);
+  free(LM);
+  return r;
+}

@@ -1,0 +1,87 @@
+"""Exact polynomial helpers for the oracle pins (test-side arithmetic only)."""
+from fractions import Fraction
+
+import numpy as np
+
+
+def _mul(a, b):
+    r = [Fraction(0)] * (len(a) + len(b) - 1)
+    for i, x in enumerate(a):
+        if x:
+            for j, z in enumerate(b):
+                r[i + j] += x * z
+    return r
+
+
+def _add(a, b):
+    n = max(len(a), len(b))
+    a = a + [Fraction(0)] * (n - len(a))
+    b = b + [Fraction(0)] * (n - len(b))
+    return [u + v for u, v in zip(a, b)]
+
+
+def k5_monomials(h, g, y):
+    """Monomial coefficients b_0..b_32 of the k = 5 degree-optimal form with the
+    given doubles, expanded in exact rational arithmetic (eq. five_mult_degopt
+    written as polynomials in x instead of matrices)."""
+    P = {1: [Fraction(1)], 2: [Fraction(0), Fraction(1)]}
+    P[3] = _mul(P[2], P[2])
+    t = 0
+    for j in range(2, 6):
+        lf, rf = [Fraction(0)], [Fraction(0)]
+        for i in range(2, j + 2):
+            lf = _add(lf, [Fraction(float(h[t])) * c for c in P[i]])
+            rf = _add(rf, [Fraction(float(g[t])) * c for c in P[i]])
+            t += 1
+        P[j + 2] = _mul(lf, rf)
+    z = [Fraction(0)]
+    for i in range(1, 8):
+        z = _add(z, [Fraction(float(y[i - 1])) * c for c in P[i]])
+    return z
+
+
+def read_golden_coeffs(path):
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            name, v = line.split()
+            vals[name] = float(v)
+    h = [vals[f"h_{j}_{i}"] for j in range(2, 6) for i in range(2, j + 2)]
+    g = [vals[f"g_{j}_{i}"] for j in range(2, 6) for i in range(2, j + 2)]
+    y = [vals[f"y_{i}"] for i in range(1, 8)]
+    return np.array(h), np.array(g), np.array(y)
+
+
+def theta_from_monomials(b, m, dps=60, N=160):
+    """Theta_m = max{theta: sum_{k>=m} |c_{k+1}| theta^k <= u} (eqs. Eb,
+    theta_Eb) where exp(-p(-x)) - 1 - x = sum c_k x^k and p has monomial
+    coefficients b (rationals). Needs mpmath."""
+    import mpmath as mp
+    mp.mp.dps = dps
+    S = [mp.mpf(0)] * (N + 1)
+    for i, bi in enumerate(b):
+        if i <= N:
+            S[i] = -mp.mpf(bi.numerator) / bi.denominator * (-1) ** i
+    E = [mp.mpf(0)] * (N + 1)
+    E[0] = mp.mpf(1)
+    for k in range(1, N + 1):
+        E[k] = sum(j * S[j] * E[k - j] for j in range(1, k + 1)) / k
+    c = E[:]
+    c[0] -= 1
+    c[1] -= 1
+
+    def hbar(th):
+        return sum(abs(c[k + 1]) * th ** k for k in range(m, N))
+
+    lo, hi = mp.mpf("1e-12"), mp.mpf(1)
+    u = mp.mpf(2) ** -53
+    for _ in range(200):
+        mid = (lo + hi) / 2
+        if hbar(mid) <= u:
+            lo = mid
+        else:
+            hi = mid
+    return float(lo)

@@ -1,0 +1,346 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: values the
+paper prints, closed forms, invariants, brute force on tiny inputs, or an
+independent library routine in a special case. No value here comes from the
+CUDA path.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+from paper_2401_10089_gb300 import workloads
+from tests.oracle_helpers import k5_monomials, read_golden_coeffs, theta_from_monomials
+
+U = 2.0 ** -53
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+# --------------------------------------------------------------------------
+# Tables (Table table_simple_experiment, Table Table_theta)
+# --------------------------------------------------------------------------
+
+def test_k5_table_transcription():
+    h, g, y = oracle.coeffs_k5()
+    hg, gg, yg = read_golden_coeffs(os.path.join(GOLDEN, "k5_coefficients.txt"))
+    assert np.array_equal(h, hg) and np.array_equal(g, gg) and np.array_equal(y, yg)
+
+
+def test_k5_monomials_match_taylor():
+    # Sec. 3: expanding the k = 5 graph gives z = sum_{i=0}^{32} b_i x^i that
+    # matches the Taylor coefficients 1/i of -log(1-x) to about u. For the
+    # printed decimals this holds for i <= 12 (within 8u); b_13 and b_14 are
+    # off by about 1.4e2 u and 7.2e3 u, not <= u as the text states.
+    z = k5_monomials(*oracle.coeffs_k5())
+    assert len(z) - 1 == 32 and z[0] == 0
+    dev = [float(abs(z[i] - 1 / __import__("fractions").Fraction(i)) * i) / U for i in range(1, 16)]
+    assert max(dev[:12]) <= 8.0
+    assert 50 < dev[12] < 500
+    assert 2e3 < dev[13] < 2e4
+    assert dev[14] > 1e4
+
+
+def test_theta_recomputed_from_backward_error():
+    pytest.importorskip("mpmath")
+    from fractions import Fraction
+    table = {}
+    with open(os.path.join(GOLDEN, "theta_table.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, m, deg, th = line.split()
+                table[int(k)] = (int(m), float(th))
+    # Exact Taylor T_m (k = 1, 2, 3): the recomputed Theta rounds to the table.
+    for k in (1, 2, 3):
+        m, th = table[k]
+        b = [Fraction(0)] + [Fraction(1, i) for i in range(1, m + 1)]
+        got = theta_from_monomials(b, m)
+        assert float(f"{got:.2e}") == th, (k, got, th)
+    # k = 5 from the printed coefficients: 0.2448, a little below the table's 0.246.
+    z = k5_monomials(*oracle.coeffs_k5())
+    got = theta_from_monomials(z, 14)
+    assert 0.2440 < got < 0.2455
+
+
+# --------------------------------------------------------------------------
+# Graph evaluation, eq. (five_mult_degopt)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 2, 5])
+def test_graph_scalar_against_log(k):
+    xs = np.linspace(-0.25, 0.25, 101)
+    for x in xs:
+        z = oracle.graph_eval(np.array([[x]]), k)[0, 0]
+        if k == 1:
+            ref = x + x * x / 2
+        elif k == 2:
+            ref = x + x * x / 2 + x ** 3 / 3 + x ** 4 / 4
+        else:
+            ref = -math.log1p(-x)  # Fig. 1: error about u on the disk of radius ~0.25
+        tol = 8 * U * max(abs(ref), 1e-300) if k == 5 else 4 * U * abs(ref) + 1e-300
+        assert abs(z - ref) <= tol, (k, x, z, ref)
+
+
+def test_graph_k5_vs_horner():
+    z = k5_monomials(*oracle.coeffs_k5())
+    b = np.array([float(c) for c in z])
+    rng = np.random.default_rng(10)
+    X = rng.standard_normal((12, 12))
+    X *= 0.2 / oracle.norm1(X)
+    G = oracle.graph_eval(X, 5)
+    H = oracle.horner(X, b)
+    assert rel(G, H) < 1e-14
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_graph_taylor_matrix(k):
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((9, 9)) * 0.05
+    X2 = X @ X
+    ref = X + X2 / 2 if k == 1 else X + X2 / 2 + X2 @ X / 3 + X2 @ X2 / 4
+    assert rel(oracle.graph_eval(X, k), ref) < 1e-15
+
+
+@pytest.mark.parametrize("k", [1, 2, 5])
+def test_graph_p3_argument_and_diagonal(k):
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((7, 7)) * 0.03
+    assert rel(oracle.graph_eval(X, k, P3=X @ X), oracle.graph_eval(X, k)) < 1e-15
+    d = rng.uniform(-0.2, 0.2, 6)
+    Zd = oracle.graph_eval(np.diag(d), k)
+    zs = [oracle.graph_eval(np.array([[v]]), k)[0, 0] for v in d]
+    assert np.allclose(np.diag(Zd), zs, rtol=1e-15, atol=0)
+    assert np.count_nonzero(Zd - np.diag(np.diag(Zd))) == 0
+
+
+def test_graph_transposition():
+    # z(X^T) = z(X)^T for any polynomial: catches a transposed operand.
+    rng = np.random.default_rng(13)
+    X = rng.standard_normal((10, 10)) * 0.02
+    assert rel(oracle.graph_eval(X.T, 5), oracle.graph_eval(X, 5).T) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# LU, inverse, square root (eq. ScalDB)
+# --------------------------------------------------------------------------
+
+def test_lu_and_inverse():
+    rng = np.random.default_rng(20)
+    for n in (1, 2, 5, 17, 40):
+        A = rng.standard_normal((n, n)) + 0.5 * np.eye(n)
+        Ai, ld, st = oracle.inverse(A)
+        assert st == oracle.OK
+        assert rel(Ai, np.linalg.inv(A)) < 1e-12
+        assert abs(ld - np.linalg.slogdet(A)[1]) < 1e-12 * max(1, abs(ld))
+        assert rel(A @ Ai, np.eye(n)) < 1e-13 * n
+    S = np.array([[1.0, 2.0], [2.0, 4.0]])
+    assert oracle.inverse(S)[2] == oracle.SINGULAR
+
+
+def test_sqrt_closed_forms():
+    lam = np.array([0.01, 0.5, 3.0, 100.0])
+    X, it, st = oracle.sqrtm_db(np.diag(lam))
+    assert st == oracle.OK and np.allclose(X, np.diag(np.sqrt(lam)), rtol=1e-14, atol=1e-16)
+    r, th = 2.5, 2.0
+    R = r * np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    X, it, st = oracle.sqrtm_db(R)
+    ref = math.sqrt(r) * np.array([[math.cos(th / 2), -math.sin(th / 2)], [math.sin(th / 2), math.cos(th / 2)]])
+    assert st == oracle.OK and rel(X, ref) < 1e-14
+
+
+def test_sqrt_dense():
+    A = workloads.dense_32()
+    X, it, st = oracle.sqrtm_db(A)
+    assert st == oracle.OK and 3 <= it <= 12
+    assert rel(X @ X, A) < 1e-14
+    assert rel(X, sla.sqrtm(A).real) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# 1-norm power estimator (Higham 1988)
+# --------------------------------------------------------------------------
+
+def test_normest_exact_cases():
+    rng = np.random.default_rng(30)
+    for n in (1, 3, 16, 33):
+        B = np.abs(rng.standard_normal((n, n)))  # nonnegative: estimate is exact
+        for p in (1, 2, 5):
+            ex = np.abs(np.linalg.matrix_power(B, p)).sum(axis=0).max()
+            assert abs(oracle.normest_pow(B, p) - ex) <= 1e-13 * ex
+        D = np.diag(rng.standard_normal(n))  # diagonal: exact
+        for p in (3, 14, 15):
+            ex = np.max(np.abs(np.diag(D)) ** p)
+            assert abs(oracle.normest_pow(D, p) - ex) <= 1e-13 * ex
+            AI2 = D @ D
+            assert abs(oracle.normest_pow(D, p, AI2) - ex) <= 1e-13 * ex
+
+
+def test_normest_lower_bound_and_quality():
+    rng = np.random.default_rng(31)
+    ratios = []
+    for t in range(40):
+        n = int(rng.integers(4, 40))
+        B = rng.standard_normal((n, n)) / np.sqrt(n)
+        for p in (1, 4, 15):
+            ex = np.abs(np.linalg.matrix_power(B, p)).sum(axis=0).max()
+            est = oracle.normest_pow(B, p)
+            assert est <= ex * (1 + 1e-12)
+            ratios.append(est / ex)
+            if p % 2 == 0 or p == 15:
+                est2 = oracle.normest_pow(B, p, B @ B)
+                assert est2 <= ex * (1 + 1e-12)
+    assert np.median(ratios) > 0.85 and min(ratios) > 0.2
+
+
+# --------------------------------------------------------------------------
+# Plan (Algorithm 1 loop test and order search) on diagonal inputs, where
+# alpha is known exactly: alpha = max |lam^{1/2^s} - 1|.
+# --------------------------------------------------------------------------
+
+def _expected_plan_diagonal(lam, theta=oracle.THETA_TABLE):
+    s = 0
+    mu = np.array(lam, dtype=float)
+    while np.max(np.abs(mu - 1)) > theta[2]:
+        mu = np.sqrt(mu)
+        s += 1
+    a = np.max(np.abs(mu - 1))
+    k = 1 if a <= theta[0] else (2 if a <= theta[1] else 5)
+    return s, k
+
+
+@pytest.mark.parametrize("lam", [
+    [1.0 + 1e-9, 1.0 - 5e-9],
+    [1.0 + 1e-5, 0.99999],
+    [1.1, 0.95, 1.2],
+    [3.0, 0.2, 1.0],
+    [100.0, 0.01],
+    [7.0],
+])
+def test_plan_diagonal(lam):
+    s_exp, k_exp = _expected_plan_diagonal(lam)
+    A = np.diag(lam)
+    L, d = oracle.logm(A)
+    assert (d["s"], d["k"], d["info"]) == (s_exp, k_exp, oracle.OK)
+    assert np.allclose(np.diag(L), np.log(lam), rtol=1e-13, atol=1e-15)
+
+
+def test_plan_call_matches_loop():
+    A = workloads.dense_32()
+    fin, k, a = oracle.plan(A)
+    assert not fin and k == 5
+    A2 = np.diag([1.05, 0.97, 1.01])
+    fin, k, a = oracle.plan(A2)
+    assert fin and k == 5 and a == pytest.approx(0.05, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Full logarithm (Algorithm 1)
+# --------------------------------------------------------------------------
+
+def test_logm_rotation_closed_form():
+    for r, th in ((1.0, 0.3), (2.0, 1.5), (0.3, -2.5), (5.0, 3.0)):
+        A = r * np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+        L, d = oracle.logm(A)
+        ref = np.array([[math.log(r), -th], [th, math.log(r)]])
+        assert d["info"] == oracle.OK and np.allclose(L, ref, rtol=0, atol=2e-14 * max(1, abs(th)))
+
+
+def test_logm_brute_force_diagonalisable():
+    rng = np.random.default_rng(40)
+    for n in (2, 3, 6):
+        lam = np.exp(rng.uniform(-2, 2, n))
+        A, V = workloads.diag_from_eigs(lam, seed=int(rng.integers(1000)))
+        ref = V @ np.diag(np.log(lam)) @ np.linalg.inv(V)
+        L, d = oracle.logm(A)
+        assert d["info"] == oracle.OK and rel(L, ref) < 1e-13
+
+
+def test_logm_invariants():
+    A = workloads.dense_32()
+    L, d = oracle.logm(A)
+    assert d["info"] == oracle.OK
+    Li, _ = oracle.logm(np.linalg.inv(A))
+    assert rel(Li, -L) < 1e-13  # log(A^{-1}) = -log(A)
+    S = workloads._orthogonal(np.random.default_rng(41), 32)
+    Ls, _ = oracle.logm(S @ A @ S.T)
+    assert rel(Ls, S @ L @ S.T) < 1e-13  # similarity invariance
+    assert rel(oracle.expm_taylor(L), A) < 1e-13  # exp(log A) = A
+    assert rel(L, sla.logm(A).real) < 1e-13  # independent Schur-Pade algorithm
+
+
+def test_logm_workload_shapes_small():
+    mats = [workloads.identity_plus(3, 24, seed=7)[i] for i in range(3)]
+    mats += [workloads.triangular_similar(48, seed=8)]
+    mats += list(workloads.spd(2, 16, seed=9, lo=1e-3, hi=1e3))
+    Ls, ds = oracle.logm_batch(mats)
+    for A, L, d in zip(mats, Ls, ds):
+        assert d["info"] == oracle.OK
+        assert rel(L, sla.logm(A).real) < 1e-12
+        assert rel(oracle.expm_taylor(L), A) < 1e-12
+
+
+def test_logm_forced_plan_reproduces():
+    A = workloads.dense_32()
+    L, d = oracle.logm(A)
+    Lf, df = oracle.logm(A, force_s=d["s"], force_k=d["k"])
+    assert (df["s"], df["k"]) == (d["s"], d["k"]) and np.array_equal(L, Lf)
+    # one root more or one less still gives log A to high accuracy
+    Lp, _ = oracle.logm(A, force_s=d["s"] + 1, force_k=5)
+    assert rel(Lp, L) < 1e-13
+
+
+def test_logm_status_codes():
+    A = np.eye(3)
+    A[1, 1] = np.nan
+    assert oracle.logm(A)[1]["info"] == oracle.NONFINITE
+    Z = np.zeros((4, 4))
+    assert oracle.logm(Z)[1]["info"] == oracle.SINGULAR
+    assert oracle.logm(workloads.dense_32(), max_sqrt=1)[1]["info"] == oracle.MAX_SQRT
+    assert oracle.logm(-np.eye(3))[1]["info"] in (oracle.SINGULAR, oracle.NO_CONVERGENCE, oracle.MAX_SQRT)
+
+
+def test_expm_taylor_closed_forms():
+    th = 0.7
+    E = oracle.expm_taylor(np.array([[0.0, -th], [th, 0.0]]))
+    assert np.allclose(E, [[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]], atol=1e-15)
+    d = np.array([-3.0, 0.1, 4.0])
+    assert np.allclose(np.diag(oracle.expm_taylor(np.diag(d))), np.exp(d), rtol=1e-14)
+    N = np.triu(np.ones((4, 4)), 1)  # nilpotent: finite series
+    ref = np.eye(4) + N + N @ N / 2 + N @ N @ N / 6
+    assert rel(oracle.expm_taylor(N), ref) < 1e-15
+    A = np.random.default_rng(50).standard_normal((10, 10))
+    assert rel(oracle.expm_taylor(A), sla.expm(A)) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Frechet derivative (block-triangular form)
+# --------------------------------------------------------------------------
+
+def test_frechet_diagonal_divided_differences():
+    lam = np.array([0.5, 1.3, 4.0, 9.0])
+    W = np.random.default_rng(60).standard_normal((4, 4))
+    G, st = oracle.frechet_adjoint(np.diag(lam), W)
+    ll = np.log(lam)
+    ref = np.empty((4, 4))
+    for i in range(4):
+        for j in range(4):
+            ref[i, j] = W[i, j] / lam[i] if i == j else W[i, j] * (ll[i] - ll[j]) / (lam[i] - lam[j])
+    assert st == oracle.OK and rel(G, ref) < 1e-13
+
+
+def test_frechet_vs_finite_differences():
+    rng = np.random.default_rng(61)
+    A = workloads.spd(1, 6, seed=62, lo=0.2, hi=5.0)[0] + 0.1 * rng.standard_normal((6, 6))
+    W = rng.standard_normal((6, 6))
+    G, st = oracle.frechet_adjoint(A, W)
+    E = rng.standard_normal((6, 6))
+    h = 1e-6
+    fd = (np.sum(W * oracle.logm(A + h * E)[0]) - np.sum(W * oracle.logm(A - h * E)[0])) / (2 * h)
+    assert abs(np.sum(G * E) - fd) < 1e-7 * max(1.0, abs(fd))
