@@ -1,0 +1,277 @@
+"""Benchmark: matrix logarithms per second (and TFLOP/s) on GB300.
+
+Default workload: a batch of 512 real 256 x 256 matrices A = I + E, E seeded
+Gaussian rescaled so ||E||_1 is uniform in [0.2, 5] (synthetic stand-in for
+the paper's test sets, which are not available). One step = Algorithm 1 on the
+whole batch (plan, square roots, graph polynomial, 2^s scaling), FP64 path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank runs its own batch (weak
+scaling, no collective on the data path); value = matrices of all ranks / the
+slowest rank's time. ``--impl reference`` times the CPU oracle on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "logm matrices/s and TFLOP/s at stated rel. error: mixed/batched vs plain FP64"
+UNIT = "matrices/s"
+COUNT, N = 512, 256
+WORKLOAD = "batch of 512 real 256x256 A = I + E, ||E||_1 ~ U[0.2, 5] (seeded), FP64 path"
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp64_peak_tflops():
+    """FP64 dense peak = measured BF16 dense peak x nominal FP64/BF16 ratio (1.25 / 2250)."""
+    pk = measured_peaks()
+    if "bf16_tflops" in pk:
+        return pk["bf16_tflops"] * 1.25 / 2250.0, "of measured (bf16 burst x nominal fp64/bf16 ratio)"
+    return 1900.0 * 1.25 / 2250.0, "of fallback (1.9 PFLOP/s bf16 x nominal fp64/bf16 ratio)"
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region (reads settings only)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_flops(stats: np.ndarray, n: int) -> float:
+    """2n^3 per inverse (LU 2/3 n^3 + inversion 4/3 n^3) and per product, 2n^2 per
+    estimator matrix-vector product; O(n^2) lin-combs excluded (Sec. 2.2)."""
+    st = stats.reshape(-1, 4).astype(np.float64)
+    return float(((st[:, 1] + st[:, 2]) * 2.0 * n ** 3 + st[:, 3] * 2.0 * n ** 2).sum())
+
+
+def cpu_baseline(A_np, sample: int):
+    """The oracle as it stands, on the host cores, on `sample` matrices of the workload."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    mats = [A_np[i] for i in range(sample)]
+    oracle.logm_batch(mats[:1], nthreads=cores)  # build/load outside the timing
+    t0 = time.perf_counter()
+    Ls, ds = oracle.logm_batch(mats, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} of the {COUNT} matrices (same seed), one OpenMP thread per matrix",
+            "seconds": dt}, Ls, ds
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2401_10089_gb300 import workloads
+    A = workloads.identity_plus(COUNT, N, seed=1)
+    sample = args.ref_sample
+    cb, Ls, ds = cpu_baseline(A, sample)
+    # warm-up / timed steps, each a bounded sample of the workload
+    import oracle
+    cores = cb["cores"]
+    for _ in range(args.warmup):
+        oracle.logm_batch([A[0]], nthreads=cores)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.logm_batch([A[(s * sample + i) % COUNT] for i in range(sample)], nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    value = sample * len(times) / sum(times)
+    cb["value"] = value
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD + f"; oracle on {sample} matrices per step"},
+           "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-sample", type=int, default=COUNT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--count", type=int, default=COUNT, help="matrices per rank (smaller for profiling)")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2401_10089_gb300 as lg
+    from paper_2401_10089_gb300 import workloads
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    count = args.count
+    A_np = workloads.identity_plus(count, N, seed=1 + rank)
+    A_host = torch.from_numpy(A_np).pin_memory()
+    A_dev = A_host.to(dev)
+    stats = torch.zeros(4 * count, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        lg.logm_execute(A_dev, stats=stats)
+    barrier()
+
+    # device-timed region: inputs resident in HBM (268 MB > 129 MB L2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            L, s, k, info = lg.logm_execute(A_dev, stats=stats)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clocks = clk.summary()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+
+    st = stats.cpu().numpy()
+    flops = algorithmic_flops(st, N)
+    info_np = info.cpu().numpy()
+    s_np, k_np = s.cpu().numpy(), k.cpu().numpy()
+
+    # end to end through the public call with host buffers: H2D + execute + D2H
+    L_host = torch.empty_like(A_host).pin_memory()
+    for _ in range(0 if args.no_e2e else 1):
+        Ad = A_host.to(dev, non_blocking=True)
+        Lo, _, _, _ = lg.logm_execute(Ad)
+        L_host.copy_(Lo, non_blocking=True)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(0 if args.no_e2e else args.steps):
+        Ad = A_host.to(dev, non_blocking=True)
+        Lo, _, _, inf2 = lg.logm_execute(Ad)
+        L_host.copy_(Lo, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps if not args.no_e2e else float("nan")
+    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(e2e_t.item())
+
+    if rank == 0:
+        peak, peak_note = fp64_peak_tflops()
+        achieved = flops / (ms * 1e-3) / 1e12
+        out = {
+            "metric": METRIC, "value": count * world / (ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if count == COUNT else WORKLOAD.replace(str(COUNT), str(count), 1),
+                       "count": count, "n": N, "precision": "fp64",
+                       "l2": f"inputs ({count * N * N * 8 / 1e6:.0f} MB) vs 129 MB L2; no flush", "parallelism": f"batch-sharded x{world}"},
+            "tflops": achieved * world * ms / ms_max,
+            "plan": {"s_hist": np.bincount(s_np).tolist(), "k_hist": np.bincount(k_np, minlength=6).tolist(),
+                     "info_nonzero": int((info_np != 0).sum())},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "peak_note": "FP64 dense " + peak_note,
+                         "kernel": "k_logm_small<execute> (persistent, one block per matrix)",
+                         "flops_per_launch": flops},
+            "e2e": {"value": count * world / (e2e_ms * 1e-3) if not args.no_e2e else None, "unit": UNIT,
+                    "h2d_bytes_per_step": int(A_host.numel() * 8), "d2h_bytes_per_step": int(A_host.numel() * 8)},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            cb, Ls, ds = cpu_baseline(A_np, args.ref_sample)
+            Lg = L.cpu().numpy()
+            errs = [np.linalg.norm(Lg[i] - Ls[i]) / np.linalg.norm(Ls[i]) for i in range(len(Ls))
+                    if (ds[i]["s"], ds[i]["k"]) == (int(s_np[i]), int(k_np[i]))]
+            out["cpu_baseline"] = cb
+            out["rel_err_vs_oracle"] = {"max": float(max(errs)) if errs else None, "matrices": len(errs)}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

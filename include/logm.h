@@ -1,0 +1,164 @@
+/*
+ * logm.h -- C ABI of the GB300 (sm_103a) matrix-logarithm library.
+ *
+ * Method: inverse scaling and squaring with computation-graph polynomials,
+ * Jarlebring, Sastre and Ibanez, "Polynomial approximations for the matrix
+ * logarithm with computation graphs" (arXiv 2401.10089), Algorithm 1 (Sec. 6):
+ *   log A = 2^s log(A^{1/2^s})                 (Sec. 2.1, eq. matrix_logarithm_identity)
+ *   A^{1/2} by the scaled Denman-Beavers iteration  (Sec. 6, eq. ScalDB)
+ *   log(I + B) ~= -z(-B), z a degree-optimal graph  (Sec. 3, eqs. Taylor_log,
+ *                                                     logipASTM, five_mult_degopt)
+ *   s and the number of products k chosen by the backward-error bound
+ *   alpha_m <= Theta_m                        (Sec. 5 Table Table_theta; Sec. 6
+ *                                               eqs. alphaapprox, AI2, normAm9)
+ *
+ * Conventions shared by every call:
+ *  - Matrices are dense, square, row-major. A batch holds `count` matrices.
+ *    With n_uniform > 0 matrix b starts at element b * n_uniform^2. With
+ *    n_uniform == 0 the sizes and element offsets come from the device arrays
+ *    `n` and `offset`, and n_max must bound every n.
+ *  - Pointers named *_dev, and every matrix pointer, are DEVICE pointers that
+ *    the caller allocates and owns; the library never allocates, frees or
+ *    keeps them after the call returns.
+ *  - `ws` is caller-owned device workspace of at least logm_workspace_size()
+ *    bytes, 256-byte aligned. It may be reused between calls on one stream.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Every call only
+ *    enqueues work on it: no host synchronisation, no allocation.
+ *  - Return value: LOGM_SUCCESS, or a negative LOGM_ERR_* for an invalid
+ *    argument or a CUDA launch error (nothing is enqueued after an argument
+ *    error). Per-matrix outcomes go to the caller's `info_dev[count]`
+ *    (LOGM_INFO_*); kernels never trap and every loop is bounded.
+ */
+#ifndef LOGM_H
+#define LOGM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes of every call. */
+#define LOGM_SUCCESS 0
+#define LOGM_ERR_INVALID_ARG (-1)
+#define LOGM_ERR_UNSUPPORTED (-2)
+#define LOGM_ERR_WORKSPACE (-3)
+#define LOGM_ERR_CUDA (-4)
+
+/* Per-matrix status written to info_dev. */
+#define LOGM_INFO_OK 0
+#define LOGM_INFO_SINGULAR 1       /* exact zero (or non-finite) pivot in a left division */
+#define LOGM_INFO_NO_CONVERGENCE 2 /* Denman-Beavers iteration hit max_db_iter */
+#define LOGM_INFO_MAX_SQRT 3       /* square-root count hit max_sqrt (maxiter of Algorithm 1) */
+#define LOGM_INFO_NONFINITE 4      /* NaN or Inf in the input */
+
+/* Storage type of A, L, X, Z (arithmetic is FP64 except where `precision` says). */
+#define LOGM_DTYPE_F64 0
+#define LOGM_DTYPE_F32 1
+
+/* Arithmetic of the graph products (Sec. 3). Square roots, norm estimates and
+ * the 2^s scaling are FP64 in every precision. */
+#define LOGM_PREC_FP64 0
+#define LOGM_PREC_TF32X3 1  /* a = hi + lo in TF32, hi*hi + hi*lo + lo*hi, FP32 accumulation */
+#define LOGM_PREC_BF16X3 2  /* a = a0 + a1 + a2 in BF16, the 6 products with i + j <= 2, FP32 accumulation */
+
+typedef struct logm_batch {
+  int32_t count;          /* number of matrices, >= 0 */
+  int32_t dtype;          /* LOGM_DTYPE_* of A, L, X, Z */
+  int32_t n_uniform;      /* > 0: every matrix is n_uniform x n_uniform */
+  int32_t n_max;          /* ragged batches: upper bound of n (ignored if n_uniform > 0) */
+  const int32_t* n;       /* ragged: device int32[count] of sizes, 1 <= n <= n_max */
+  const int64_t* offset;  /* ragged: device int64[count] element offset of each matrix */
+} logm_batch;
+
+typedef struct logm_options {
+  int32_t k_max;          /* largest number of graph products: 1, 2 or 5 (Table Table_theta) */
+  int32_t precision;      /* LOGM_PREC_* of the graph products */
+  int32_t max_sqrt;       /* maxiter of Algorithm 1 (default 40) */
+  int32_t max_db_iter;    /* cap on Denman-Beavers iterations per root (default 50) */
+  double theta[3];        /* Theta_{m_k} for k = 1, 2, 5; 0 selects the paper's
+                             1.83e-8, 1.53e-4, 2.46e-1 (Table Table_theta) */
+} logm_options;
+
+/* Bytes of device workspace the calls below need for this batch and options
+ * (the maximum over all calls). Returns 0 for an invalid batch. */
+size_t logm_workspace_size(const logm_batch* batch, const logm_options* opts);
+
+/* Bytes of the checkpoint context logm_execute writes for logm_backward
+ * (per-level square-root inputs). Returns 0 for an invalid batch. */
+size_t logm_context_size(const logm_batch* batch, const logm_options* opts);
+
+/* logm_plan -- the decision of one pass of Algorithm 1's while loop and the
+ * order search (Sec. 6, eqs. alphaapprox, normAm9, alpha2term1,
+ * normAm9plus1, min_in, min_inp, roughmax_even), at the given A.
+ *   A       : device, the current A (F64 or F32 per batch->dtype).
+ *   AI2     : device or NULL. NULL means s = 0: finish = ||A - I||_1 <= Theta
+ *             first, else the power norms are estimated with A - I. Non-NULL
+ *             is A_I2 = (A - I)^2 of eq. (AI2) (same dtype), s >= 1.
+ *   finish_dev int32[count]: 1 if alpha_{m_kmax} <= Theta_kmax.
+ *   k_dev      int32[count]: products the order search picks (k_max if not finished).
+ *   alpha_dev  double[count]: the alpha_{m_kmax} value of the test.
+ *   info_dev   int32[count]: LOGM_INFO_OK or LOGM_INFO_NONFINITE. */
+int logm_plan(const logm_batch* batch, const logm_options* opts, const void* A,
+              const void* AI2, int32_t* finish_dev, int32_t* k_dev, double* alpha_dev,
+              int32_t* info_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* logm_sqrt -- one square root A <- A^{1/2} by the scaled Denman-Beavers
+ * iteration (Sec. 6, eq. ScalDB; two LU-type left divisions per iteration,
+ * mu_k from their determinants), plus A_I2 = A_2 - 2A + I (eq. AI2).
+ *   A         : device in/out (dtype per batch). Replaced by its square root.
+ *   A2_out    : device or NULL; receives the input A (the A_2 of Algorithm 1).
+ *   AI2_out   : device or NULL; receives (A^{1/2} - I)^2 = A_2 - 2 A^{1/2} + I.
+ *   active_dev: device int32[count] or NULL; matrices with 0 are left as they are.
+ *   iters_dev : device int32[count] or NULL; Denman-Beavers iterations taken.
+ *   info_dev  : int32[count]; LOGM_INFO_OK / SINGULAR / NO_CONVERGENCE / NONFINITE. */
+int logm_sqrt(const logm_batch* batch, const logm_options* opts, void* A, void* A2_out,
+              void* AI2_out, const int32_t* active_dev, int32_t* iters_dev, int32_t* info_dev,
+              void* ws, size_t ws_bytes, void* stream);
+
+/* logm_graph_eval -- Z = z(X) with the degree-optimal graph of k products
+ * (Sec. 3, eq. five_mult_degopt): P_1 = I, P_2 = X, P_3 = X^2 and
+ * P_{j+2} = (sum_i h_{j,i} P_i)(sum_i g_{j,i} P_i), z = sum_i y_i P_i, with
+ * Table table_simple_experiment for k = 5 and exact Taylor T_2, T_4 (eq.
+ * Taylor_log) for k = 1, 2.
+ *   X    : device (dtype per batch).
+ *   P3   : device or NULL; X^2 if the caller has it (saves one product, as
+ *          Algorithm 1 does with A_I2 when s >= 1).
+ *   k_dev: device int32[count], each 1, 2 or 5.
+ *   Z    : device output (dtype per batch).
+ *   precision: LOGM_PREC_* for the products. */
+int logm_graph_eval(const logm_batch* batch, int32_t precision, const void* X, const void* P3,
+                    const int32_t* k_dev, void* Z, void* ws, size_t ws_bytes, void* stream);
+
+/* logm_execute -- L = log(A) by Algorithm 1 (T = I: no balancing).
+ *   A      : device input, untouched.   L : device output (dtype per batch).
+ *   s_dev, k_dev : device int32[count] or NULL; square roots and products used.
+ *   info_dev     : device int32[count].
+ *   stats_dev    : device int32[4 * count] or NULL; per matrix the work done:
+ *                  Denman-Beavers iterations, n x n inverses (left divisions),
+ *                  n x n graph products, estimator matrix-vector products.
+ *   ctx    : device buffer of logm_context_size() bytes or NULL. When given,
+ *            the inputs of every square-root level and the plan are saved for
+ *            logm_backward. */
+int logm_execute(const logm_batch* batch, const logm_options* opts, const void* A, void* L,
+                 int32_t* s_dev, int32_t* k_dev, int32_t* info_dev, int32_t* stats_dev, void* ctx,
+                 void* ws, size_t ws_bytes, void* stream);
+
+/* logm_backward -- dA = adjoint of the computed map A -> L at the forward's
+ * plan, applied to dL (i.e. the gradient of sum(dL o L) with respect to A):
+ * the graph products and the Denman-Beavers iterations of every level are
+ * reversed; the iterates of a level are recomputed from its checkpoint in ctx.
+ * The plan (s, k) and the scaling mu are held fixed.
+ *   A   : the forward's input.  ctx: the forward's context.  dL, dA: device. */
+int logm_backward(const logm_batch* batch, const logm_options* opts, const void* A,
+                  const void* ctx, const void* dL, void* dA, int32_t* info_dev, void* ws,
+                  size_t ws_bytes, void* stream);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int logm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

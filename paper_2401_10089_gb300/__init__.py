@@ -1,0 +1,12 @@
+"""GB300-native (sm_103a) matrix logarithm by inverse scaling and squaring
+with computation-graph polynomials (Jarlebring, Sastre, Ibanez, arXiv
+2401.10089).
+
+The compute path is the CUDA library built from ``csrc/`` (C ABI in
+``include/logm.h``); this package is its thin Python binding.
+"""
+from .api import (Ragged, logm_backward, logm_context_size, logm_execute, logm_graph_eval, logm_plan,
+                  logm_sqrt, logm_version, logm_workspace_size)
+
+__all__ = ["Ragged", "logm_backward", "logm_context_size", "logm_execute", "logm_graph_eval", "logm_plan",
+           "logm_sqrt", "logm_version", "logm_workspace_size"]

@@ -1,0 +1,83 @@
+"""ctypes view of the C ABI in ``include/logm.h`` (argument marshalling only).
+
+Loading fails loudly when the compiled library is missing: there is no CPU or
+PyTorch fallback for any step of the method.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+SUCCESS, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_CUDA = 0, -1, -2, -3, -4
+INFO_OK, INFO_SINGULAR, INFO_NO_CONVERGENCE, INFO_MAX_SQRT, INFO_NONFINITE = 0, 1, 2, 3, 4
+DTYPE_F64, DTYPE_F32 = 0, 1
+PREC_FP64, PREC_TF32X3, PREC_BF16X3 = 0, 1, 2
+
+_ERRORS = {ERR_INVALID_ARG: "invalid argument", ERR_UNSUPPORTED: "unsupported", ERR_WORKSPACE: "workspace",
+           ERR_CUDA: "CUDA launch error"}
+
+# Every symbol include/logm.h declares.
+EXPORTS = ("logm_workspace_size", "logm_context_size", "logm_plan", "logm_sqrt", "logm_graph_eval",
+           "logm_execute", "logm_backward", "logm_version")
+
+
+class LogmBatch(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("dtype", ctypes.c_int32), ("n_uniform", ctypes.c_int32),
+                ("n_max", ctypes.c_int32), ("n", ctypes.c_void_p), ("offset", ctypes.c_void_p)]
+
+
+class LogmOptions(ctypes.Structure):
+    _fields_ = [("k_max", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_sqrt", ctypes.c_int32),
+                ("max_db_iter", ctypes.c_int32), ("theta", ctypes.c_double * 3)]
+
+
+class LogmError(RuntimeError):
+    pass
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load ``liblogm.so`` (building it in-tree if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and _build._stale():
+            _build.build()
+        if not os.path.exists(path):
+            raise LogmError(f"CUDA library {path} is missing; run paper_2401_10089_gb300._build.build()")
+        L = ctypes.CDLL(path)
+        P, I32, SZ, V = ctypes.POINTER, ctypes.c_int32, ctypes.c_size_t, ctypes.c_void_p
+        B, O = P(LogmBatch), P(LogmOptions)
+        L.logm_workspace_size.restype = SZ
+        L.logm_workspace_size.argtypes = [B, O]
+        L.logm_context_size.restype = SZ
+        L.logm_context_size.argtypes = [B, O]
+        L.logm_plan.argtypes = [B, O, V, V, V, V, V, V, V, SZ, V]
+        L.logm_sqrt.argtypes = [B, O, V, V, V, V, V, V, V, SZ, V]
+        L.logm_graph_eval.argtypes = [B, I32, V, V, V, V, V, SZ, V]
+        L.logm_execute.argtypes = [B, O, V, V, V, V, V, V, V, V, SZ, V]
+        L.logm_backward.argtypes = [B, O, V, V, V, V, V, V, SZ, V]
+        L.logm_version.argtypes = []
+        for name in EXPORTS:
+            getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
+        L.logm_workspace_size.restype = SZ
+        L.logm_context_size.restype = SZ
+        _lib = L
+        return _lib
+
+
+def check(rc: int, what: str):
+    if rc != SUCCESS:
+        raise LogmError(f"{what} failed: {_ERRORS.get(rc, rc)}")

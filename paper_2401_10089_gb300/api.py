@@ -1,0 +1,227 @@
+"""Python binding of the C ABI: same names as ``include/logm.h``.
+
+These functions only marshal arguments. Matrices are CUDA tensors owned by
+PyTorch (its caching allocator provides device memory and workspace, its
+current stream orders the work); every step of the method runs in the CUDA
+library. A batch is either a (count, n, n) tensor or a :class:`Ragged`
+(packed values, device sizes, device element offsets).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+
+_PREC = {"fp64": _lib.PREC_FP64, "tf32x3": _lib.PREC_TF32X3, "bf16x3": _lib.PREC_BF16X3}
+
+
+@dataclass
+class Ragged:
+    """Packed ragged batch: matrix b is values[offset[b] : offset[b] + n[b]**2] (row-major)."""
+    values: torch.Tensor   # 1-D float64/float32 CUDA tensor
+    n: torch.Tensor        # int32 CUDA tensor [count]
+    offset: torch.Tensor   # int64 CUDA tensor [count]
+    n_max: int
+
+    @property
+    def count(self) -> int:
+        return int(self.n.numel())
+
+    @property
+    def device(self):
+        return self.values.device
+
+    @property
+    def dtype(self):
+        return self.values.dtype
+
+    def empty_like(self):
+        return Ragged(torch.empty_like(self.values), self.n, self.offset, self.n_max)
+
+
+def _dtype_code(t: torch.dtype) -> int:
+    if t == torch.float64:
+        return _lib.DTYPE_F64
+    if t == torch.float32:
+        return _lib.DTYPE_F32
+    raise TypeError(f"unsupported dtype {t}")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _batch(A) -> _lib.LogmBatch:
+    b = _lib.LogmBatch()
+    if isinstance(A, Ragged):
+        if not A.values.is_cuda:
+            raise ValueError("Ragged.values must be a CUDA tensor")
+        b.count, b.dtype, b.n_uniform, b.n_max = A.count, _dtype_code(A.values.dtype), 0, A.n_max
+        b.n, b.offset = A.n.data_ptr(), A.offset.data_ptr()
+        return b
+    if A.dim() == 2:
+        A = A.unsqueeze(0)
+    if A.dim() != 3 or A.shape[1] != A.shape[2]:
+        raise ValueError("expected a (count, n, n) or (n, n) tensor")
+    if not A.is_cuda or not A.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    b.count, b.dtype, b.n_uniform, b.n_max = A.shape[0], _dtype_code(A.dtype), A.shape[1], A.shape[1]
+    b.n = b.offset = None
+    return b
+
+
+def _values(A):
+    return A.values if isinstance(A, Ragged) else A
+
+
+def _options(k_max=5, precision="fp64", max_sqrt=40, max_db_iter=50, theta=None) -> _lib.LogmOptions:
+    o = _lib.LogmOptions()
+    o.k_max, o.max_sqrt, o.max_db_iter = k_max, max_sqrt, max_db_iter
+    o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
+    th = (0.0, 0.0, 0.0) if theta is None else theta
+    for t in range(3):
+        o.theta[t] = th[t]
+    return o
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class _Workspace:
+    """Per-device cache of the largest workspace requested so far."""
+
+    def __init__(self):
+        self.buf = {}
+
+    def get(self, device, nbytes: int) -> torch.Tensor:
+        key = torch.device(device).index
+        cur = self.buf.get(key)
+        if cur is None or cur.numel() < nbytes:
+            cur = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+            self.buf[key] = cur
+        return cur
+
+
+_ws = _Workspace()
+
+
+def logm_workspace_size(A, **opts) -> int:
+    L = _lib.load()
+    b, o = _batch(A), _options(**opts)
+    return int(L.logm_workspace_size(ctypes.byref(b), ctypes.byref(o)))
+
+
+def logm_context_size(A, **opts) -> int:
+    L = _lib.load()
+    b, o = _batch(A), _options(**opts)
+    return int(L.logm_context_size(ctypes.byref(b), ctypes.byref(o)))
+
+
+def _workspace(A, b, o, L):
+    nbytes = int(L.logm_workspace_size(ctypes.byref(b), ctypes.byref(o)))
+    if nbytes == 0:
+        raise _lib.LogmError("unsupported batch (workspace size 0)")
+    w = _ws.get(_values(A).device, nbytes)
+    return w, nbytes
+
+
+def _i32(count, device):
+    return torch.empty(count, dtype=torch.int32, device=device)
+
+
+def logm_plan(A, AI2=None, **opts):
+    """(finish, k, alpha, info) of one pass of Algorithm 1's loop test and the order search."""
+    L = _lib.load()
+    b, o = _batch(A), _options(**opts)
+    dev = _values(A).device
+    fin, k, info = _i32(b.count, dev), _i32(b.count, dev), _i32(b.count, dev)
+    alpha = torch.empty(b.count, dtype=torch.float64, device=dev)
+    w, nb = _workspace(A, b, o, L)
+    rc = L.logm_plan(ctypes.byref(b), ctypes.byref(o), _ptr(_values(A)),
+                     _ptr(None if AI2 is None else _values(AI2)), _ptr(fin), _ptr(k), _ptr(alpha),
+                     _ptr(info), _ptr(w), nb, _stream(dev))
+    _lib.check(rc, "logm_plan")
+    return fin, k, alpha, info
+
+
+def logm_sqrt(A, active=None, **opts):
+    """One square root in place: returns (A, A2, AI2, iters, info)."""
+    L = _lib.load()
+    b, o = _batch(A), _options(**opts)
+    v = _values(A)
+    dev = v.device
+    A2 = torch.empty_like(v)
+    AI2 = torch.empty_like(v)
+    it, info = _i32(b.count, dev), _i32(b.count, dev)
+    w, nb = _workspace(A, b, o, L)
+    rc = L.logm_sqrt(ctypes.byref(b), ctypes.byref(o), _ptr(v), _ptr(A2), _ptr(AI2), _ptr(active), _ptr(it),
+                     _ptr(info), _ptr(w), nb, _stream(dev))
+    _lib.check(rc, "logm_sqrt")
+    return A, A2, AI2, it, info
+
+
+def logm_graph_eval(X, k, P3=None, precision="fp64"):
+    """Z = z(X) with k graph products per matrix (k: int or int32 CUDA tensor)."""
+    L = _lib.load()
+    b = _batch(X)
+    v = _values(X)
+    dev = v.device
+    if not torch.is_tensor(k):
+        k = torch.full((b.count,), int(k), dtype=torch.int32, device=dev)
+    Z = torch.empty_like(v)
+    prec = _PREC[precision] if isinstance(precision, str) else int(precision)
+    o = _options()
+    w, nb = _workspace(X, b, o, L)
+    rc = L.logm_graph_eval(ctypes.byref(b), prec, _ptr(v), _ptr(None if P3 is None else _values(P3)),
+                           _ptr(k), _ptr(Z), _ptr(w), nb, _stream(dev))
+    _lib.check(rc, "logm_graph_eval")
+    return Z
+
+
+def logm_execute(A, with_ctx=False, stats=None, **opts):
+    """L = log(A) by Algorithm 1: returns (L, s, k, info[, ctx]).
+
+    ``stats``: optional int32 CUDA tensor of 4 * count entries that receives,
+    per matrix, the Denman-Beavers iterations, inverses, graph products and
+    estimator matrix-vector products the plan executed."""
+    L = _lib.load()
+    b, o = _batch(A), _options(**opts)
+    v = _values(A)
+    dev = v.device
+    out = torch.empty_like(v)
+    s, k, info = _i32(b.count, dev), _i32(b.count, dev), _i32(b.count, dev)
+    ctx = None
+    if with_ctx:
+        ctx = torch.empty(int(L.logm_context_size(ctypes.byref(b), ctypes.byref(o))), dtype=torch.uint8,
+                          device=dev)
+    w, nb = _workspace(A, b, o, L)
+    rc = L.logm_execute(ctypes.byref(b), ctypes.byref(o), _ptr(v), _ptr(out), _ptr(s), _ptr(k), _ptr(info),
+                        _ptr(stats), _ptr(ctx), _ptr(w), nb, _stream(dev))
+    _lib.check(rc, "logm_execute")
+    Lout = out if not isinstance(A, Ragged) else Ragged(out, A.n, A.offset, A.n_max)
+    if with_ctx:
+        return Lout, s, k, info, ctx
+    return Lout, s, k, info
+
+
+def logm_backward(A, ctx, dL, **opts):
+    """dA = gradient of sum(dL * log(A)) with respect to A at the forward's plan."""
+    L = _lib.load()
+    b, o = _batch(A), _options(**opts)
+    v = _values(A)
+    dev = v.device
+    dA = torch.empty_like(v)
+    info = _i32(b.count, dev)
+    w, nb = _workspace(A, b, o, L)
+    rc = L.logm_backward(ctypes.byref(b), ctypes.byref(o), _ptr(v), _ptr(ctx), _ptr(_values(dL)), _ptr(dA),
+                         _ptr(info), _ptr(w), nb, _stream(dev))
+    _lib.check(rc, "logm_backward")
+    return dA, info
+
+
+def logm_version() -> int:
+    return int(_lib.load().logm_version())

@@ -1,0 +1,452 @@
+// cta_linalg.cuh -- CTA-level FP64 dense linear algebra for one matrix per
+// thread block (n <= kMaxN). Everything here runs on the FP64 pipe, which on
+// GB300 is the bottleneck by a wide margin (about 1 TFLOP/s for the chip), so
+// the routines keep every FP64 instruction useful: divisions, logarithms and
+// exponentials are computed once per CTA and broadcast through shared memory,
+// index arithmetic stays in integer registers, and the O(n^3) parts run as
+// DMMA (mma.sync m8n8k4 f64) tiles or register-blocked DFMA.
+//
+// Matrices live in global memory (L2-resident working set), row-major with
+// leading dimension n. All block-wide control flow is uniform: every scalar
+// that decides a branch comes out of a block reduction broadcast through
+// shared memory.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lg {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxN = 256;   // largest n of the one-block-per-matrix kernels (= kSmallMaxN)
+constexpr int kPanel = 16;   // Gauss-Jordan panel width
+constexpr int kTileM = 64, kTileN = 64, kTileK = 16;
+constexpr int kAsStride = kTileK + 4;  // shared-memory row strides that keep
+constexpr int kBsStride = kTileN + 4;  // DMMA fragment loads conflict-free
+
+struct Reduce {
+  double v[kWarps];
+  int i[kWarps];
+};
+
+struct GemmSmem {
+  double As[kTileM * kAsStride];
+  double Bs[kTileK * kBsStride];
+};
+
+struct GjSmem {
+  double P[kPanel * kMaxN];  // panel, column-major: P[c * kMaxN + i]
+  double R[kPanel * kMaxN];  // rows of the panel's pivots, R[c * kMaxN + j]
+};
+
+struct VecSmem {
+  double x[kMaxN], y[kMaxN], z[kMaxN], t[kMaxN];
+};
+
+struct BlockSmem {
+  union {
+    GemmSmem gemm;
+    GjSmem gj;
+  } u;
+  VecSmem vec;
+  int piv[kMaxN];
+  Reduce red;
+  double bc[4];  // broadcast slots
+  int ibc[4];
+  int work[4];   // thread 0's tally: DB iterations, inverses, products, matvecs
+};
+
+// ---------------------------------------------------------------------------
+// Block reductions (all threads get the result).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double nanmax(double a, double b) {
+  return (a > b || a != a) ? a : b;
+}
+
+__device__ double block_sum(double v, Reduce& r) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) r.v[w] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int t = 0; t < kWarps; ++t) s += r.v[t];
+  __syncthreads();
+  return s;
+}
+
+__device__ double block_max(double v, Reduce& r) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) r.v[w] = v;
+  __syncthreads();
+  double s = r.v[0];
+#pragma unroll
+  for (int t = 1; t < kWarps; ++t) s = nanmax(s, r.v[t]);
+  __syncthreads();
+  return s;
+}
+
+// max of v with the smallest index among ties; v < 0 marks "not a candidate".
+__device__ void block_argmax(double v, int idx, Reduce& r, double* out_v, int* out_i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (v2 > v || (v2 == v && i2 < idx)) {
+      v = v2;
+      idx = i2;
+    }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    r.v[w] = v;
+    r.i[w] = idx;
+  }
+  __syncthreads();
+  double bv = r.v[0];
+  int bi = r.i[0];
+#pragma unroll
+  for (int t = 1; t < kWarps; ++t)
+    if (r.v[t] > bv || (r.v[t] == bv && r.i[t] < bi)) {
+      bv = r.v[t];
+      bi = r.i[t];
+    }
+  __syncthreads();
+  *out_v = bv;
+  *out_i = bi;
+}
+
+__device__ int block_and(int pred, Reduce& r) {
+  int w_all = __all_sync(0xffffffffu, pred);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) r.i[w] = w_all;
+  __syncthreads();
+  int a = 1;
+#pragma unroll
+  for (int t = 0; t < kWarps; ++t) a &= r.i[t];
+  __syncthreads();
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise helpers over an n x n matrix (ld = n).
+// ---------------------------------------------------------------------------
+__device__ void mat_copy(double* __restrict__ dst, const double* __restrict__ src, int n) {
+  const int nn = n * n;
+  for (int t = threadIdx.x; t < nn; t += kThreads) dst[t] = src[t];
+}
+
+__device__ void mat_identity(double* __restrict__ dst, int n) {
+  const int nn = n * n;
+  for (int t = threadIdx.x; t < nn; t += kThreads) dst[t] = (t / n == t % n) ? 1.0 : 0.0;
+}
+
+// ||M - shift I||_1 = max_j sum_i |m_ij - shift delta_ij|. NaN propagates.
+__device__ double mat_norm1(const double* __restrict__ M, int n, double shift, Reduce& r) {
+  double best = 0.0;
+  for (int j = threadIdx.x; j < n; j += kThreads) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double v = M[i * n + j];
+      if (i == j) v -= shift;
+      s += fabs(v);
+    }
+    best = nanmax(best, s);
+  }
+  return block_max(best, r);
+}
+
+// y = (M - shift I) x (trans = 0) or y = (M - shift I)^T x (trans = 1);
+// x, y in shared memory (distinct).
+__device__ void mat_vec(const double* __restrict__ M, int n, double shift, const double* x,
+                        double* y, int trans) {
+  if (!trans) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int i = w; i < n; i += kWarps) {
+      double s = 0.0;
+      for (int c = l; c < n; c += 32) s = fma(M[i * n + c], x[c], s);
+      s = warp_sum(s);
+      if (l == 0) y[i] = s - shift * x[i];
+    }
+  } else {
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      double s = 0.0;
+      for (int i = 0; i < n; ++i) s = fma(M[i * n + j], x[i], s);
+      y[j] = s - shift * x[j];
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// GEMM: out = alpha * (A - a_shift I)(B - b_shift I) + sum_t c_t E_t,
+// FP64 DMMA (mma.sync.m8n8k4.f64) on 64 x 64 output tiles.
+// ---------------------------------------------------------------------------
+struct EpiTerms {
+  const double* M[6];
+  double c[6];
+  int count;
+};
+
+struct OutView {
+  void* p;     // element 0 of the matrix
+  int dtype;   // 0: F64, 1: F32
+};
+
+__device__ __forceinline__ void store_out(const OutView& o, int idx, double v) {
+  if (o.dtype == 0)
+    static_cast<double*>(o.p)[idx] = v;
+  else
+    static_cast<float*>(o.p)[idx] = static_cast<float>(v);
+}
+
+__device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
+__device__ void gemm_block(int n, const double* __restrict__ A, double a_shift,
+                           const double* __restrict__ B, double b_shift, double alpha,
+                           const EpiTerms& epi, OutView out, GemmSmem& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1;
+  const int g = lane >> 2, q = lane & 3;
+  const int tiles = (n + kTileM - 1) / kTileM;
+  for (int tile = 0; tile < tiles * tiles; ++tile) {
+    const int r0 = (tile / tiles) * kTileM, c0 = (tile % tiles) * kTileN;
+    double acc[2][4][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+    for (int k0 = 0; k0 < n; k0 += kTileK) {
+#pragma unroll
+      for (int e = tid; e < kTileM * kTileK; e += kThreads) {
+        const int rr = e / kTileK, kk = e % kTileK;
+        const int gr = r0 + rr, gk = k0 + kk;
+        double v = 0.0;
+        if (gr < n && gk < n) {
+          v = A[gr * n + gk];
+          if (gr == gk) v -= a_shift;
+        }
+        sm.As[rr * kAsStride + kk] = v;
+      }
+#pragma unroll
+      for (int e = tid; e < kTileK * kTileN; e += kThreads) {
+        const int kk = e / kTileN, cc = e % kTileN;
+        const int gk = k0 + kk, gc = c0 + cc;
+        double v = 0.0;
+        if (gk < n && gc < n) {
+          v = B[gk * n + gc];
+          if (gk == gc) v -= b_shift;
+        }
+        sm.Bs[kk * kBsStride + cc] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int ks = 0; ks < kTileK; ks += 4) {
+        double af[2], bf[4];
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) af[mb] = sm.As[(wm * 16 + mb * 8 + g) * kAsStride + ks + q];
+#pragma unroll
+        for (int nb = 0; nb < 4; ++nb) bf[nb] = sm.Bs[(ks + q) * kBsStride + wn * 32 + nb * 8 + g];
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+          for (int nb = 0; nb < 4; ++nb) dmma_8x8x4(acc[mb][nb][0], acc[mb][nb][1], af[mb], bf[nb]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int gr = r0 + wm * 16 + mb * 8 + g;
+          const int gc = c0 + wn * 32 + nb * 8 + 2 * q + h;
+          if (gr < n && gc < n) {
+            const int idx = gr * n + gc;
+            double v = alpha * acc[mb][nb][h];
+            for (int t = 0; t < epi.count; ++t) v = fma(epi.c[t], epi.M[t][idx], v);
+            store_out(out, idx, v);
+          }
+        }
+  }
+  __syncthreads();
+}
+
+// out = sum_t c_t E_t elementwise (lin-comb node of the computation graph).
+__device__ void lincomb_block(int n, const EpiTerms& e, double* __restrict__ out) {
+  const int nn = n * n;
+  for (int t = threadIdx.x; t < nn; t += kThreads) {
+    double v = 0.0;
+    for (int s = 0; s < e.count; ++s) v = fma(e.c[s], e.M[s][t], v);
+    out[t] = v;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// In-place inverse by blocked Gauss-Jordan elimination with partial pivoting
+// (the left division X \ I of the square-root iteration). Each step k picks
+// the largest |w_ik|, i >= k, swaps rows k and p, scales row k by 1/w_kk and
+// eliminates column k from every other row; the eliminated column is replaced
+// by the column of the elementary transform, so that after the n steps and
+// the reverse column swaps W holds A^{-1}. Panels of kPanel columns are
+// factorised in shared memory; the rest of W gets the rank-kPanel update
+// W[:, notJ] += (M_J - I)[:, J] W[J, notJ] once per panel.
+// Returns 0, or 1 if a pivot is zero or not finite. *logabsdet (thread 0
+// accumulates; broadcast at the end) = sum log|pivot| = log|det A|.
+// ---------------------------------------------------------------------------
+__device__ int gj_inverse_block(double* __restrict__ W, int n, double* logabsdet, BlockSmem& S) {
+  const int tid = threadIdx.x;
+  double* P = S.u.gj.P;
+  double* R = S.u.gj.R;
+  int* piv = S.piv;
+  double ld = 0.0;  // meaningful in thread 0
+  int status = 0;
+  for (int kb = 0; kb < n && !status; kb += kPanel) {
+    const int jb = min(kPanel, n - kb);
+    // panel -> shared (column-major)
+    for (int e = tid; e < jb * n; e += kThreads) {
+      const int c = e / n, i = e % n;
+      P[c * kMaxN + i] = W[i * n + kb + c];
+    }
+    __syncthreads();
+    for (int c = 0; c < jb; ++c) {
+      const int k = kb + c;
+      double cand = -1.0;
+      int cidx = n;
+      for (int i = tid; i < n; i += kThreads) {
+        if (i >= k) {
+          double v = fabs(P[c * kMaxN + i]);
+          if (v != v) v = INFINITY;  // NaN pivots are taken (and rejected below)
+          if (v > cand || (v == cand && i < cidx)) {
+            cand = v;
+            cidx = i;
+          }
+        }
+      }
+      double pv;
+      int p;
+      block_argmax(cand, cidx, S.red, &pv, &p);
+      if (!(pv > 0.0) || !(pv < INFINITY)) {
+        status = 1;
+        break;
+      }
+      if (tid < jb && p != k) {
+        double t0 = P[tid * kMaxN + k];
+        P[tid * kMaxN + k] = P[tid * kMaxN + p];
+        P[tid * kMaxN + p] = t0;
+      }
+      if (tid == 0) piv[k] = p;
+      __syncthreads();
+      if (tid == 0) {
+        const double d = P[c * kMaxN + k];
+        ld += log(fabs(d));
+        S.bc[0] = 1.0 / d;
+      }
+      __syncthreads();
+      const double inv = S.bc[0];
+      if (tid < jb) {
+        double* pk = &P[tid * kMaxN + k];
+        *pk = (tid == c) ? inv : (*pk) * inv;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += kThreads) {
+        if (i == k) continue;
+        const double f = P[c * kMaxN + i];
+        if (f == 0.0) continue;
+        P[c * kMaxN + i] = 0.0;
+        for (int cc = 0; cc < jb; ++cc) P[cc * kMaxN + i] = fma(-f, P[cc * kMaxN + k], P[cc * kMaxN + i]);
+      }
+      __syncthreads();
+    }
+    if (status) break;
+    // panel -> W, row swaps of the panel on the other columns, copy of the pivot rows
+    for (int e = tid; e < jb * n; e += kThreads) {
+      const int c = e / n, i = e % n;
+      W[i * n + kb + c] = P[c * kMaxN + i];
+    }
+    for (int j = tid; j < n; j += kThreads) {
+      if (j >= kb && j < kb + jb) continue;
+      for (int c = 0; c < jb; ++c) {
+        const int k = kb + c, p = piv[k];
+        if (p != k) {
+          double t0 = W[k * n + j];
+          W[k * n + j] = W[p * n + j];
+          W[p * n + j] = t0;
+        }
+      }
+      for (int c = 0; c < jb; ++c) R[c * kMaxN + j] = W[(kb + c) * n + j];
+    }
+    __syncthreads();
+    // W[:, notJ] += (P - I_J) R, 4 x 4 register blocks
+    const int ngrp = (n + 3) / 4;
+    for (int blk = tid; blk < ngrp * ngrp; blk += kThreads) {
+      const int i0 = (blk / ngrp) * 4, j0 = (blk % ngrp) * 4;
+      // (P - I_J) R = P R - R on the rows of J: start those rows from -R.
+      double acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = i0 + a;
+        const bool inJ = i >= kb && i < kb + jb;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          acc[a][b] = (inJ && j0 + b < n) ? -R[(i - kb) * kMaxN + j0 + b] : 0.0;
+      }
+      for (int c = 0; c < jb; ++c) {
+        double d[4], rr[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int i = i0 + a;
+          d[a] = (i < n) ? P[c * kMaxN + i] : 0.0;
+        }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) rr[b] = (j0 + b < n) ? R[c * kMaxN + j0 + b] : 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(d[a], rr[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int i = i0 + a, j = j0 + b;
+          if (i < n && j < n && (j < kb || j >= kb + jb)) W[i * n + j] += acc[a][b];
+        }
+    }
+    __syncthreads();
+  }
+  if (!status) {
+    // undo the pivoting on the columns, last step first
+    for (int i = tid; i < n; i += kThreads)
+      for (int k = n - 1; k >= 0; --k) {
+        const int p = piv[k];
+        if (p != k) {
+          double t0 = W[i * n + k];
+          W[i * n + k] = W[i * n + p];
+          W[i * n + p] = t0;
+        }
+      }
+  }
+  if (tid == 0) S.bc[1] = ld;
+  __syncthreads();
+  *logabsdet = S.bc[1];
+  __syncthreads();
+  return status;
+}
+
+}  // namespace lg

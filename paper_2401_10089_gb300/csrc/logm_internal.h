@@ -1,0 +1,58 @@
+// logm_internal.h -- host-side interface between the C ABI (logm_api.cu) and
+// the kernel launchers. Not installed; the public surface is include/logm.h.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lg {
+
+enum Mode : int { kModeExecute = 0, kModePlan = 1, kModeSqrt = 2, kModeGraph = 3 };
+
+// Everything one launch of the one-block-per-matrix kernel needs. Device
+// pointers unless noted.
+struct SmallParams {
+  // batch
+  int count, dtype, n_uniform, n_max;
+  const int32_t* n_dev;
+  const int64_t* off_dev;
+  // options
+  int k_max, max_sqrt, max_db;
+  double theta[3];
+  // inputs / outputs (NULL when unused by the mode)
+  const void* A;       // execute, plan, sqrt (sqrt: in/out)
+  void* A_inout;       // sqrt
+  void* L;             // execute: L; graph: Z
+  const void* AI2_in;  // plan
+  void* A2_out;        // sqrt
+  void* AI2_out;       // sqrt
+  const void* X;       // graph
+  const void* P3;      // graph
+  const int32_t* k_in; // graph
+  const int32_t* active;
+  int32_t* s_out;
+  int32_t* k_out;
+  int32_t* info;
+  int32_t* finish;
+  double* alpha;
+  int32_t* iters;
+  int32_t* stats;      // execute: [4 * count] DB iterations, inverses, products, matvecs
+  double* ctx;         // execute: per-level checkpoints (NULL = none)
+  int ctx_levels;
+  // workspace
+  double* slots;       // n_slots * kSlotMats * n_max^2 doubles
+  int32_t* queue;      // one counter, zeroed before the launch
+  int n_slots;
+  int precision;       // graph products (FP64 in this kernel family)
+};
+
+constexpr int kSlotMats = 7;
+constexpr int kCtxLevels = 12;
+constexpr int kSmallMaxN = 256;  // largest n of the one-block-per-matrix kernels
+
+int small_kernel_slots(int count);
+size_t small_workspace_bytes(int count, int n_max);
+cudaError_t launch_small(Mode mode, const SmallParams& p, cudaStream_t stream);
+
+}  // namespace lg

@@ -1,0 +1,53 @@
+"""The CUDA library builds, loads and exports every symbol include/logm.h
+declares (no compute calls: runs without a GPU)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "logm.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(logm_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2401_10089_gb300 import _build, _lib
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 8
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) <= set(_lib.EXPORTS) | set(names)
+    assert set(_lib.EXPORTS) == set(names)
+
+
+def test_workspace_queries_without_gpu():
+    from paper_2401_10089_gb300 import _lib
+    L = _lib.load()
+    b = _lib.LogmBatch()
+    b.count, b.dtype, b.n_uniform, b.n_max = 4, 0, 32, 32
+    o = _lib.LogmOptions()
+    o.k_max, o.precision, o.max_sqrt, o.max_db_iter = 5, 0, 40, 50
+    assert L.logm_context_size(ctypes.byref(b), ctypes.byref(o)) > 4 * 32 * 32 * 8
+    bad = _lib.LogmBatch()
+    bad.count, bad.dtype, bad.n_uniform, bad.n_max = 4, 7, 32, 32
+    assert L.logm_context_size(ctypes.byref(bad), ctypes.byref(o)) == 0
+
+
+def test_invalid_arguments_rejected_before_launch():
+    from paper_2401_10089_gb300 import _lib
+    L = _lib.load()
+    b = _lib.LogmBatch()
+    b.count, b.dtype, b.n_uniform, b.n_max = 1, 0, 8, 8
+    o = _lib.LogmOptions()
+    o.k_max, o.precision, o.max_sqrt, o.max_db_iter = 3, 0, 40, 50  # k_max = 3 has no coefficients
+    rc = L.logm_execute(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, None, None, 0, None)
+    assert rc == _lib.ERR_INVALID_ARG
+    o.k_max = 5
+    rc = L.logm_execute(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, None, None, 0, None)
+    assert rc == _lib.ERR_INVALID_ARG
