@@ -155,6 +155,25 @@ int logm_backward(const logm_batch* batch, const logm_options* opts, const void*
                   const void* ctx, const void* dL, void* dA, int32_t* info_dev, void* ws,
                   size_t ws_bytes, void* stream);
 
+/* logm_execute_noalloc -- logm_execute for callers that cannot allocate
+ * device memory (no counterpart in the paper: it exists for callers such as
+ * code running under a host framework that owns every device allocation, or
+ * real-time code with a fixed device-memory budget). The caller still passes
+ * A, L and the per-matrix outputs; the scratch space lives in a file-scope
+ * device array of 32 MiB that every GPU loading the library keeps until the
+ * process exits. The call runs as many matrices at a time as that array
+ * holds (7 n_max^2 doubles each), FP64 precision only, n_max <= 256;
+ * larger n_max returns LOGM_ERR_UNSUPPORTED and another precision
+ * LOGM_ERR_UNSUPPORTED. It calls no cudaMalloc, cudaFree or other allocating
+ * routine. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents behind: calls whose
+ * work overlaps on the GPU (different streams, or different host threads on
+ * one device) race on it and must be serialised by the caller.
+ *   Arguments as logm_execute, without stats, ctx and workspace. */
+int logm_execute_noalloc(const logm_batch* batch, const logm_options* opts, const void* A, void* L,
+                         int32_t* s_dev, int32_t* k_dev, int32_t* info_dev, void* stream);
+
 /* Library version (major * 10000 + minor * 100 + patch). */
 int logm_version(void);
 

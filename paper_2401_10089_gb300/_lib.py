@@ -21,7 +21,7 @@ _ERRORS = {ERR_INVALID_ARG: "invalid argument", ERR_UNSUPPORTED: "unsupported", 
 
 # Every symbol include/logm.h declares.
 EXPORTS = ("logm_workspace_size", "logm_context_size", "logm_plan", "logm_sqrt", "logm_graph_eval",
-           "logm_execute", "logm_backward", "logm_version")
+           "logm_execute", "logm_backward", "logm_execute_noalloc", "logm_version")
 
 
 class LogmBatch(ctypes.Structure):
@@ -69,6 +69,7 @@ def load(build_if_missing: bool = True):
         L.logm_graph_eval.argtypes = [B, I32, V, V, V, V, V, SZ, V]
         L.logm_execute.argtypes = [B, O, V, V, V, V, V, V, V, V, SZ, V]
         L.logm_backward.argtypes = [B, O, V, V, V, V, V, V, SZ, V]
+        L.logm_execute_noalloc.argtypes = [B, O, V, V, V, V, V, V]
         L.logm_version.argtypes = []
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
