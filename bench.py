@@ -257,7 +257,7 @@ def main():
                          "flops_per_launch": flops},
             "e2e": {"value": count * world / (e2e_ms * 1e-3) if not args.no_e2e else None, "unit": UNIT,
                     "h2d_bytes_per_step": int(A_host.numel() * 8), "d2h_bytes_per_step": int(A_host.numel() * 8)},
-            "gpu_launches": args.steps,
+            "gpu_launches": 4 * args.steps,  # per step: 3 queue-order kernels + the persistent logm kernel
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:

@@ -53,7 +53,10 @@ void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o,
   }
   char* w = static_cast<char*>(ws);
   p.queue = reinterpret_cast<int32_t*>(w);
-  p.slots = reinterpret_cast<double*>(w + 256);
+  const size_t ob = lg::small_order_bytes(b->count);
+  p.order = reinterpret_cast<int32_t*>(w + 256);
+  p.order_aux = p.order + b->count;
+  p.slots = reinterpret_cast<double*>(w + 256 + ob);
   p.n_slots = lg::small_kernel_slots(b->count);
 }
 

@@ -43,16 +43,20 @@ struct SmallParams {
   // workspace
   double* slots;       // n_slots * kSlotMats * n_max^2 doubles
   int32_t* queue;      // one counter, zeroed before the launch
+  int32_t* order;      // execute: [count] queue position -> matrix, most expensive first (NULL: index order)
+  int32_t* order_aux;  // [2 * kOrderBuckets + count]: bucket counts, bucket cursors, bucket per matrix
   int n_slots;
   int precision;       // graph products (FP64 in this kernel family)
 };
 
 constexpr int kSlotMats = 7;
+constexpr int kOrderBuckets = 256;
 constexpr int kCtxLevels = 12;
 constexpr int kSmallMaxN = 256;  // largest n of the one-block-per-matrix kernels
 
 int small_kernel_slots(int count);
 size_t small_workspace_bytes(int count, int n_max);
+size_t small_order_bytes(int count);
 cudaError_t launch_small(Mode mode, const SmallParams& p, cudaStream_t stream);
 
 }  // namespace lg

@@ -649,6 +649,70 @@ __device__ void run_graph(const SmallParams& p, int b, Slot& M, BlockSmem& S) {
   if (threadIdx.x == 0 && p.info) p.info[b] = 0;
 }
 
+// ---------------------------------------------------------------------------
+// Queue order for execute: longest work first. The cost of a matrix grows
+// with n^3 and with the number of square roots, which grows with
+// log(||A - I||_1 / Theta); a counting sort over log-scale buckets of
+// n^3 (1 + log2(1 + ||A - I||_1 / Theta)) puts the expensive matrices at the
+// head of the queue so the tail of the persistent grid holds only cheap ones.
+// Scheduling only: every matrix's arithmetic is the same in any order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_order_keys(SmallParams p) {
+  __shared__ Reduce red;
+  int* hist = p.order_aux;
+  int* bucket_of = p.order_aux + 2 * kOrderBuckets;
+  const double th = p.theta[theta_slot(p.k_max)];
+  for (int b = blockIdx.x; b < p.count; b += gridDim.x) {
+    int n;
+    int64_t off;
+    matrix_geometry(p, b, &n, &off);
+    double best = 0.0;
+    if (n >= 1 && n <= p.n_max) {
+      for (int j = threadIdx.x; j < n; j += kThreads) {
+        double sum = 0.0;
+        for (int i = 0; i < n; ++i) {
+          double v = load_elem(p.A, p.dtype, off + (int64_t)i * n + j);
+          if (i == j) v -= 1.0;
+          sum += fabs(v);
+        }
+        best = nanmax(best, sum);
+      }
+    }
+    const double nu = block_max(best, red);
+    if (threadIdx.x == 0) {
+      const double n3 = (n >= 1 ? (double)n * n * n : 1.0);
+      double key = n3 * (1.0 + log2(1.0 + (nu == nu ? nu : 1e30) / th));
+      int bk = (int)(4.0 * log2(key + 1.0));
+      bk = bk < 0 ? 0 : (bk >= kOrderBuckets ? kOrderBuckets - 1 : bk);
+      bucket_of[b] = bk;
+      atomicAdd(&hist[bk], 1);
+    }
+    __syncthreads();
+  }
+}
+
+// Exclusive scan with the largest bucket first: cursor[bk] = first queue slot of bucket bk.
+__global__ void k_order_scan(SmallParams p) {
+  if (threadIdx.x == 0) {
+    int* hist = p.order_aux;
+    int* cursor = p.order_aux + kOrderBuckets;
+    int acc = 0;
+    for (int bk = kOrderBuckets - 1; bk >= 0; --bk) {
+      cursor[bk] = acc;
+      acc += hist[bk];
+    }
+  }
+}
+
+__global__ void k_order_scatter(SmallParams p) {
+  int* cursor = p.order_aux + kOrderBuckets;
+  const int* bucket_of = p.order_aux + 2 * kOrderBuckets;
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < p.count; b += gridDim.x * blockDim.x) {
+    const int pos = atomicAdd(&cursor[bucket_of[b]], 1);
+    p.order[pos] = b;
+  }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2) k_logm_small(SmallParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -660,9 +724,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_logm_small(SmallParams p) {
   for (;;) {
     if (threadIdx.x == 0) S.ibc[0] = atomicAdd(p.queue, 1);
     __syncthreads();
-    const int b = S.ibc[0];
+    const int q = S.ibc[0];
     __syncthreads();
-    if (b >= p.count) break;
+    if (q >= p.count) break;
+    const int b = p.order ? p.order[q] : q;
     if (threadIdx.x == 0) S.work[0] = S.work[1] = S.work[2] = S.work[3] = 0;
     if (MODE == kModeExecute) run_execute(p, b, M, S);
     if (MODE == kModePlan) run_plan(p, b, M, S);
@@ -693,9 +758,14 @@ int small_kernel_slots(int count) {
   return count < cap ? (count > 0 ? count : 1) : cap;
 }
 
+size_t small_order_bytes(int count) {
+  const size_t raw = sizeof(int32_t) * ((size_t)count + 2 * kOrderBuckets + (size_t)count);
+  return (raw + 255) / 256 * 256;
+}
+
 size_t small_workspace_bytes(int count, int n_max) {
   const size_t slots = (size_t)small_kernel_slots(count);
-  return 256 + slots * kSlotMats * (size_t)n_max * n_max * sizeof(double);
+  return 256 + small_order_bytes(count) + slots * kSlotMats * (size_t)n_max * n_max * sizeof(double);
 }
 
 template <int MODE>
@@ -710,7 +780,17 @@ static cudaError_t launch_mode(const SmallParams& p, cudaStream_t st) {
   }
   cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  k_logm_small<MODE><<<p.n_slots, kThreads, smem, st>>>(p);
+  if (MODE == kModeExecute && p.order && p.order_aux && p.count > 1) {
+    e = cudaMemsetAsync(p.order_aux, 0, sizeof(int32_t) * 2 * kOrderBuckets, st);
+    if (e != cudaSuccess) return e;
+    const int kb = p.count < 4 * sm_count() ? p.count : 4 * sm_count();
+    k_order_keys<<<kb, kThreads, 0, st>>>(p);
+    k_order_scan<<<1, 32, 0, st>>>(p);
+    k_order_scatter<<<(p.count + kThreads - 1) / kThreads, kThreads, 0, st>>>(p);
+  }
+  SmallParams q = p;
+  if (!(MODE == kModeExecute && p.count > 1)) q.order = nullptr;
+  k_logm_small<MODE><<<q.n_slots, kThreads, smem, st>>>(q);
   return cudaGetLastError();
 }
 
