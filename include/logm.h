@@ -52,6 +52,7 @@ extern "C" {
 #define LOGM_INFO_NO_CONVERGENCE 2 /* Denman-Beavers iteration hit max_db_iter */
 #define LOGM_INFO_MAX_SQRT 3       /* square-root count hit max_sqrt (maxiter of Algorithm 1) */
 #define LOGM_INFO_NONFINITE 4      /* NaN or Inf in the input */
+#define LOGM_INFO_TIMEOUT 5        /* a grid barrier of the whole-GPU (large n) kernel timed out; result invalid */
 
 /* Storage type of A, L, X, Z (arithmetic is FP64 except where `precision` says). */
 #define LOGM_DTYPE_F64 0

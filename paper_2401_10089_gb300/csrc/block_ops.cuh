@@ -1,0 +1,65 @@
+// block_ops.cuh -- the one-thread-block-per-matrix ops layer (n <= kMaxN):
+// vectors in shared memory, reductions through shared memory, matrices in the
+// block's workspace slot.
+#pragma once
+
+#include "cta_linalg.cuh"
+
+namespace lg {
+
+struct BlockOps {
+  BlockSmem& S;
+
+  __device__ int tid() const { return threadIdx.x; }
+  __device__ int nthreads() const { return kThreads; }
+  __device__ void sync() { __syncthreads(); }
+  __device__ bool leader() const { return threadIdx.x == 0; }
+
+  __device__ double sum(double v) { return block_sum(v, S.red); }
+  __device__ double max(double v) { return block_max(v, S.red); }
+  __device__ int all(int v) { return block_and(v, S.red); }
+  __device__ void argmax(double v, int i, double* ov, int* oi) { block_argmax(v, i, S.red, ov, oi); }
+
+  // A scalar as thread 0 computed it, for every thread of the block.
+  __device__ double bcast0(double v) {
+    if (threadIdx.x == 0) S.bc[0] = v;
+    __syncthreads();
+    const double r = S.bc[0];
+    __syncthreads();
+    return r;
+  }
+
+  __device__ double* vec(int i) {
+    return i == 0 ? S.vec.x : (i == 1 ? S.vec.y : (i == 2 ? S.vec.t : S.vec.z));
+  }
+
+  __device__ double norm1(const double* M, int n, double shift) { return mat_norm1(M, n, shift, S.red); }
+
+  __device__ void matvec(const double* M, int n, double shift, const double* x, double* y, int trans) {
+    mat_vec(M, n, shift, x, y, trans);
+  }
+
+  __device__ void gemm(int n, const double* A, double as, const double* B, double bs, double alpha,
+                       const EpiTerms& e, OutView out) {
+    gemm_block(n, A, as, B, bs, alpha, e, out, S.u.gemm);
+  }
+
+  __device__ void lincomb(int n, const EpiTerms& e, double* out) { lincomb_block(n, e, out); }
+
+  // dst <- src^{-1}; returns 0, or 1 for a zero / non-finite pivot.
+  __device__ int inverse(const double* src, double* dst, int n, double* logabsdet) {
+    mat_copy(dst, src, n);
+    __syncthreads();
+    return gj_inverse_block(dst, n, logabsdet, S);
+  }
+
+  __device__ void tally_reset() {
+    if (threadIdx.x == 0) S.work[0] = S.work[1] = S.work[2] = S.work[3] = 0;
+  }
+  __device__ void tally(int i, int c) {
+    if (threadIdx.x == 0) S.work[i] += c;
+  }
+  __device__ int tally_get(int i) const { return S.work[i]; }
+};
+
+}  // namespace lg

@@ -60,17 +60,17 @@ struct BlockSmem {
 // ---------------------------------------------------------------------------
 // Block reductions (all threads get the result).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v) {
+static __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-__device__ __forceinline__ double nanmax(double a, double b) {
+static __device__ __forceinline__ double nanmax(double a, double b) {
   return (a > b || a != a) ? a : b;
 }
 
-__device__ double block_sum(double v, Reduce& r) {
+static __device__ double block_sum(double v, Reduce& r) {
   v = warp_sum(v);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) r.v[w] = v;
@@ -82,7 +82,7 @@ __device__ double block_sum(double v, Reduce& r) {
   return s;
 }
 
-__device__ double block_max(double v, Reduce& r) {
+static __device__ double block_max(double v, Reduce& r) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -96,7 +96,7 @@ __device__ double block_max(double v, Reduce& r) {
 }
 
 // max of v with the smallest index among ties; v < 0 marks "not a candidate".
-__device__ void block_argmax(double v, int idx, Reduce& r, double* out_v, int* out_i) {
+static __device__ void block_argmax(double v, int idx, Reduce& r, double* out_v, int* out_i) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     double v2 = __shfl_xor_sync(0xffffffffu, v, o);
@@ -125,7 +125,7 @@ __device__ void block_argmax(double v, int idx, Reduce& r, double* out_v, int* o
   *out_i = bi;
 }
 
-__device__ int block_and(int pred, Reduce& r) {
+static __device__ int block_and(int pred, Reduce& r) {
   int w_all = __all_sync(0xffffffffu, pred);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) r.i[w] = w_all;
@@ -140,18 +140,18 @@ __device__ int block_and(int pred, Reduce& r) {
 // ---------------------------------------------------------------------------
 // Elementwise helpers over an n x n matrix (ld = n).
 // ---------------------------------------------------------------------------
-__device__ void mat_copy(double* __restrict__ dst, const double* __restrict__ src, int n) {
+static __device__ void mat_copy(double* __restrict__ dst, const double* __restrict__ src, int n) {
   const int nn = n * n;
   for (int t = threadIdx.x; t < nn; t += kThreads) dst[t] = src[t];
 }
 
-__device__ void mat_identity(double* __restrict__ dst, int n) {
+static __device__ void mat_identity(double* __restrict__ dst, int n) {
   const int nn = n * n;
   for (int t = threadIdx.x; t < nn; t += kThreads) dst[t] = (t / n == t % n) ? 1.0 : 0.0;
 }
 
 // ||M - shift I||_1 = max_j sum_i |m_ij - shift delta_ij|. NaN propagates.
-__device__ double mat_norm1(const double* __restrict__ M, int n, double shift, Reduce& r) {
+static __device__ double mat_norm1(const double* __restrict__ M, int n, double shift, Reduce& r) {
   double best = 0.0;
   for (int j = threadIdx.x; j < n; j += kThreads) {
     double s = 0.0;
@@ -167,7 +167,7 @@ __device__ double mat_norm1(const double* __restrict__ M, int n, double shift, R
 
 // y = (M - shift I) x (trans = 0) or y = (M - shift I)^T x (trans = 1);
 // x, y in shared memory (distinct).
-__device__ void mat_vec(const double* __restrict__ M, int n, double shift, const double* x,
+static __device__ void mat_vec(const double* __restrict__ M, int n, double shift, const double* x,
                         double* y, int trans) {
   if (!trans) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -202,92 +202,100 @@ struct OutView {
   int dtype;   // 0: F64, 1: F32
 };
 
-__device__ __forceinline__ void store_out(const OutView& o, int idx, double v) {
+static __device__ __forceinline__ void store_out(const OutView& o, size_t idx, double v) {
   if (o.dtype == 0)
     static_cast<double*>(o.p)[idx] = v;
   else
     static_cast<float*>(o.p)[idx] = static_cast<float>(v);
 }
 
-__device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double a, double b) {
+static __device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double a, double b) {
   asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
                : "+d"(d0), "+d"(d1)
                : "d"(a), "d"(b));
 }
 
-__device__ void gemm_block(int n, const double* __restrict__ A, double a_shift,
-                           const double* __restrict__ B, double b_shift, double alpha,
-                           const EpiTerms& epi, OutView out, GemmSmem& sm) {
+// One 64 x 64 output tile (rows r0.., cols c0..) of
+// out = alpha * (A - a_shift I)(B - b_shift I) + sum_t c_t E_t, by DMMA with
+// the block's 8 warps (each a 16 x 32 sub-tile). A, B, E, out: n x n, ld n.
+// Columns with colmask_lo <= c < colmask_hi are left unwritten.
+static __device__ void gemm_tile(int n, int r0, int c0, const double* __restrict__ A, double a_shift,
+                          const double* __restrict__ B, double b_shift, double alpha,
+                          const EpiTerms& epi, OutView out, GemmSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 1, wn = warp & 1;
   const int g = lane >> 2, q = lane & 3;
-  const int tiles = (n + kTileM - 1) / kTileM;
-  for (int tile = 0; tile < tiles * tiles; ++tile) {
-    const int r0 = (tile / tiles) * kTileM, c0 = (tile % tiles) * kTileN;
-    double acc[2][4][2];
+  double acc[2][4][2];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
-    for (int k0 = 0; k0 < n; k0 += kTileK) {
+    for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+  for (int k0 = 0; k0 < n; k0 += kTileK) {
 #pragma unroll
-      for (int e = tid; e < kTileM * kTileK; e += kThreads) {
-        const int rr = e / kTileK, kk = e % kTileK;
-        const int gr = r0 + rr, gk = k0 + kk;
-        double v = 0.0;
-        if (gr < n && gk < n) {
-          v = A[gr * n + gk];
-          if (gr == gk) v -= a_shift;
-        }
-        sm.As[rr * kAsStride + kk] = v;
+    for (int e = tid; e < kTileM * kTileK; e += kThreads) {
+      const int rr = e / kTileK, kk = e % kTileK;
+      const int gr = r0 + rr, gk = k0 + kk;
+      double v = 0.0;
+      if (gr < n && gk < n) {
+        v = A[(size_t)gr * n + gk];
+        if (gr == gk) v -= a_shift;
       }
-#pragma unroll
-      for (int e = tid; e < kTileK * kTileN; e += kThreads) {
-        const int kk = e / kTileN, cc = e % kTileN;
-        const int gk = k0 + kk, gc = c0 + cc;
-        double v = 0.0;
-        if (gk < n && gc < n) {
-          v = B[gk * n + gc];
-          if (gk == gc) v -= b_shift;
-        }
-        sm.Bs[kk * kBsStride + cc] = v;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int ks = 0; ks < kTileK; ks += 4) {
-        double af[2], bf[4];
-#pragma unroll
-        for (int mb = 0; mb < 2; ++mb) af[mb] = sm.As[(wm * 16 + mb * 8 + g) * kAsStride + ks + q];
-#pragma unroll
-        for (int nb = 0; nb < 4; ++nb) bf[nb] = sm.Bs[(ks + q) * kBsStride + wn * 32 + nb * 8 + g];
-#pragma unroll
-        for (int mb = 0; mb < 2; ++mb)
-#pragma unroll
-          for (int nb = 0; nb < 4; ++nb) dmma_8x8x4(acc[mb][nb][0], acc[mb][nb][1], af[mb], bf[nb]);
-      }
-      __syncthreads();
+      sm.As[rr * kAsStride + kk] = v;
     }
 #pragma unroll
-    for (int mb = 0; mb < 2; ++mb)
+    for (int e = tid; e < kTileK * kTileN; e += kThreads) {
+      const int kk = e / kTileN, cc = e % kTileN;
+      const int gk = k0 + kk, gc = c0 + cc;
+      double v = 0.0;
+      if (gk < n && gc < n) {
+        v = B[(size_t)gk * n + gc];
+        if (gk == gc) v -= b_shift;
+      }
+      sm.Bs[kk * kBsStride + cc] = v;
+    }
+    __syncthreads();
 #pragma unroll
-      for (int nb = 0; nb < 4; ++nb)
+    for (int ks = 0; ks < kTileK; ks += 4) {
+      double af[2], bf[4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int gr = r0 + wm * 16 + mb * 8 + g;
-          const int gc = c0 + wn * 32 + nb * 8 + 2 * q + h;
-          if (gr < n && gc < n) {
-            const int idx = gr * n + gc;
-            double v = alpha * acc[mb][nb][h];
-            for (int t = 0; t < epi.count; ++t) v = fma(epi.c[t], epi.M[t][idx], v);
-            store_out(out, idx, v);
-          }
-        }
+      for (int mb = 0; mb < 2; ++mb) af[mb] = sm.As[(wm * 16 + mb * 8 + g) * kAsStride + ks + q];
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb) bf[nb] = sm.Bs[(ks + q) * kBsStride + wn * 32 + nb * 8 + g];
+#pragma unroll
+      for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+        for (int nb = 0; nb < 4; ++nb) dmma_8x8x4(acc[mb][nb][0], acc[mb][nb][1], af[mb], bf[nb]);
+    }
+    __syncthreads();
   }
+#pragma unroll
+  for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+    for (int nb = 0; nb < 4; ++nb)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gr = r0 + wm * 16 + mb * 8 + g;
+        const int gc = c0 + wn * 32 + nb * 8 + 2 * q + h;
+        if (gr < n && gc < n) {
+          const size_t idx = (size_t)gr * n + gc;
+          double v = alpha * acc[mb][nb][h];
+          for (int t = 0; t < epi.count; ++t) v = fma(epi.c[t], epi.M[t][idx], v);
+          store_out(out, idx, v);
+        }
+      }
+}
+
+static __device__ void gemm_block(int n, const double* __restrict__ A, double a_shift,
+                           const double* __restrict__ B, double b_shift, double alpha,
+                           const EpiTerms& epi, OutView out, GemmSmem& sm) {
+  const int tiles = (n + kTileM - 1) / kTileM;
+  for (int tile = 0; tile < tiles * tiles; ++tile)
+    gemm_tile(n, (tile / tiles) * kTileM, (tile % tiles) * kTileN, A, a_shift, B, b_shift, alpha, epi, out, sm);
   __syncthreads();
 }
 
 // out = sum_t c_t E_t elementwise (lin-comb node of the computation graph).
-__device__ void lincomb_block(int n, const EpiTerms& e, double* __restrict__ out) {
+static __device__ void lincomb_block(int n, const EpiTerms& e, double* __restrict__ out) {
   const int nn = n * n;
   for (int t = threadIdx.x; t < nn; t += kThreads) {
     double v = 0.0;
@@ -309,7 +317,7 @@ __device__ void lincomb_block(int n, const EpiTerms& e, double* __restrict__ out
 // Returns 0, or 1 if a pivot is zero or not finite. *logabsdet (thread 0
 // accumulates; broadcast at the end) = sum log|pivot| = log|det A|.
 // ---------------------------------------------------------------------------
-__device__ int gj_inverse_block(double* __restrict__ W, int n, double* logabsdet, BlockSmem& S) {
+static __device__ int gj_inverse_block(double* __restrict__ W, int n, double* logabsdet, BlockSmem& S) {
   const int tid = threadIdx.x;
   double* P = S.u.gj.P;
   double* R = S.u.gj.R;

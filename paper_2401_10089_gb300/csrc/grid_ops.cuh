@@ -1,0 +1,431 @@
+// grid_ops.cuh -- the whole-GPU ops layer for one large matrix at a time.
+//
+// One cooperative launch (every block resident) runs Algorithm 1 with all
+// blocks working on the same matrix; phases are separated by a grid barrier.
+// The barrier is bounded: a block that waits longer than kBarrierTimeoutNs
+// sets an error flag, and from then on every barrier returns at once, so the
+// kernel always finishes (with LOGM_INFO error status) instead of hanging.
+//
+// Reductions are deterministic and identical in every block: each block
+// writes its partial result, and after the barrier every block reduces the
+// same array in the same order. That keeps every branch of Algorithm 1
+// uniform across the grid.
+#pragma once
+
+#include <cstdint>
+
+#include "cta_linalg.cuh"
+
+namespace lg {
+
+constexpr int kGridPanel = 32;          // Gauss-Jordan panel width for large n
+constexpr int kMaxGrid = 1024;          // upper bound on co-resident blocks
+constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s
+
+struct GridWs {
+  unsigned* bar;     // [0] arrivals, [1] generation (zeroed before the launch)
+  int* err;          // set when a barrier wait timed out (zeroed before the launch)
+  double* partial;   // [2][kMaxGrid] partial results of sum / max
+  int* ipartial;     // [2][kMaxGrid] partial results of all / argmax indices
+  double* cand_v;    // [2][kMaxGrid] pivot candidates (value)
+  int* cand_i;       // [2][kMaxGrid] pivot candidates (row)
+  double* vec;       // [4][n_max] estimator vectors
+  double* panel;     // [2][kGridPanel][n_max] panel, column-major, double-buffered
+  double* R;         // [kGridPanel][n_max] pivot rows of the panel
+  int* piv;          // [n_max] pivot rows of the Gauss-Jordan steps
+  int* perm;         // [n_max] composite column permutation
+  double* misc;      // [8] broadcast slots
+  double* work;      // [n_max^2] Gauss-Jordan working matrix
+  int n_max;
+};
+
+struct GridSmem {
+  GemmSmem gemm;
+  Reduce red;
+  double rowk[kGridPanel];
+  double rowp[kGridPanel];
+  double bc[4];
+  int work[4];
+};
+
+static __device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+static __device__ void grid_barrier(GridWs& w) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = w.bar + 1;
+    volatile int* verr = w.err;
+    if (*verr == 0) {
+      const unsigned g = *vgen;
+      __threadfence();
+      const unsigned arrived = atomicAdd(w.bar, 1u);
+      if (arrived == gridDim.x - 1) {
+        atomicExch(w.bar, 0u);
+        __threadfence();
+        atomicAdd(w.bar + 1, 1u);
+      } else {
+        const unsigned long long t0 = global_ns();
+        while (*vgen == g && *verr == 0) {
+          __nanosleep(64);
+          if (global_ns() - t0 > kBarrierTimeoutNs) {
+            atomicExch(w.err, 1);
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+struct GridOps {
+  GridWs& w;
+  GridSmem& S;
+  int rbuf;  // alternating partial buffer of the generic reductions
+
+  __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+  __device__ int nthreads() const { return gridDim.x * blockDim.x; }
+  __device__ void sync() { grid_barrier(w); }
+  __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
+
+  __device__ double sum(double v) {
+    const double bs = block_sum(v, S.red);
+    double* part = w.partial + rbuf * kMaxGrid;
+    rbuf ^= 1;
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    sync();
+    double t = 0.0;
+    for (int g = threadIdx.x; g < (int)gridDim.x; g += kThreads) t += part[g];
+    return block_sum(t, S.red);
+  }
+
+  __device__ double max(double v) {
+    const double bm = block_max(v, S.red);
+    double* part = w.partial + rbuf * kMaxGrid;
+    rbuf ^= 1;
+    if (threadIdx.x == 0) part[blockIdx.x] = bm;
+    sync();
+    double t = 0.0;
+    for (int g = threadIdx.x; g < (int)gridDim.x; g += kThreads) t = nanmax(t, part[g]);
+    return block_max(t, S.red);
+  }
+
+  __device__ int all(int v) {
+    const int ba = block_and(v, S.red);
+    int* part = w.ipartial + rbuf * kMaxGrid;
+    rbuf ^= 1;
+    if (threadIdx.x == 0) part[blockIdx.x] = ba;
+    sync();
+    int t = 1;
+    for (int g = threadIdx.x; g < (int)gridDim.x; g += kThreads) t &= part[g];
+    return block_and(t, S.red);
+  }
+
+  __device__ void argmax(double v, int i, double* ov, int* oi) {
+    double bv;
+    int bi;
+    block_argmax(v, i, S.red, &bv, &bi);
+    double* pv = w.partial + rbuf * kMaxGrid;
+    int* pi = w.ipartial + rbuf * kMaxGrid;
+    rbuf ^= 1;
+    if (threadIdx.x == 0) {
+      pv[blockIdx.x] = bv;
+      pi[blockIdx.x] = bi;
+    }
+    sync();
+    double cv = -1.0;
+    int ci = 0x7fffffff;
+    for (int g = threadIdx.x; g < (int)gridDim.x; g += kThreads)
+      if (pv[g] > cv || (pv[g] == cv && pi[g] < ci)) {
+        cv = pv[g];
+        ci = pi[g];
+      }
+    block_argmax(cv, ci, S.red, ov, oi);
+  }
+
+  __device__ double bcast0(double v) {
+    if (threadIdx.x == 0) S.bc[0] = v;
+    __syncthreads();
+    const double r = S.bc[0];
+    __syncthreads();
+    return r;
+  }
+
+  __device__ double* vec(int i) { return w.vec + (int64_t)i * w.n_max; }
+
+  __device__ double norm1(const double* M, int n, double shift) {
+    double best = 0.0;
+    for (int j = tid(); j < n; j += nthreads()) {
+      double s = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double v = M[(int64_t)i * n + j];
+        if (i == j) v -= shift;
+        s += fabs(v);
+      }
+      best = nanmax(best, s);
+    }
+    return max(best);
+  }
+
+  __device__ void matvec(const double* M, int n, double shift, const double* x, double* y, int trans) {
+    if (!trans) {
+      const int lane = threadIdx.x & 31;
+      const int gw = tid() >> 5, nw = nthreads() >> 5;
+      for (int i = gw; i < n; i += nw) {
+        double s = 0.0;
+        const double* row = M + (int64_t)i * n;
+        for (int c = lane; c < n; c += 32) s = fma(row[c], x[c], s);
+        s = warp_sum(s);
+        if (lane == 0) y[i] = s - shift * x[i];
+      }
+    } else {
+      for (int j = tid(); j < n; j += nthreads()) {
+        double s0 = 0.0, s1 = 0.0;
+        int i = 0;
+        for (; i + 1 < n; i += 2) {
+          s0 = fma(M[(int64_t)i * n + j], x[i], s0);
+          s1 = fma(M[(int64_t)(i + 1) * n + j], x[i + 1], s1);
+        }
+        if (i < n) s0 = fma(M[(int64_t)i * n + j], x[i], s0);
+        y[j] = (s0 + s1) - shift * x[j];
+      }
+    }
+    sync();
+  }
+
+  __device__ void gemm(int n, const double* A, double as, const double* B, double bs, double alpha,
+                       const EpiTerms& e, OutView out) {
+    const int tiles = (n + kTileM - 1) / kTileM;
+    for (int t = blockIdx.x; t < tiles * tiles; t += gridDim.x)
+      gemm_tile(n, (t / tiles) * kTileM, (t % tiles) * kTileN, A, as, B, bs, alpha, e, out, S.gemm);
+    sync();
+  }
+
+  __device__ void lincomb(int n, const EpiTerms& e, double* out) {
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t t = tid(); t < nn; t += nthreads()) {
+      double v = 0.0;
+      for (int s = 0; s < e.count; ++s) v = fma(e.c[s], e.M[s][t], v);
+      out[t] = v;
+    }
+    sync();
+  }
+
+  // W[r0.., c0..] (64 x 64 tile) += (Pf - I_J)[r0.., 0..jb) R[0..jb), c0..], columns of J skipped.
+  __device__ void rank_update_tile(double* W, int n, int kb, int jb, const double* Pf, int r0, int c0) {
+    GemmSmem& sm = S.gemm;
+    const int tid_ = threadIdx.x, lane = tid_ & 31, warp = tid_ >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int g = lane >> 2, q = lane & 3;
+    double acc[2][4][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+    for (int k0 = 0; k0 < jb; k0 += kTileK) {
+      for (int e = tid_; e < kTileM * kTileK; e += kThreads) {
+        const int kk = e / kTileM, rr = e % kTileM;
+        const int gr = r0 + rr, gk = k0 + kk;
+        sm.As[rr * kAsStride + kk] = (gr < n && gk < jb) ? Pf[(int64_t)gk * n + gr] : 0.0;
+      }
+      for (int e = tid_; e < kTileK * kTileN; e += kThreads) {
+        const int kk = e / kTileN, cc = e % kTileN;
+        const int gk = k0 + kk, gc = c0 + cc;
+        sm.Bs[kk * kBsStride + cc] = (gk < jb && gc < n) ? w.R[(int64_t)gk * n + gc] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int ks = 0; ks < kTileK; ks += 4) {
+        double af[2], bf[4];
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb) af[mb] = sm.As[(wm * 16 + mb * 8 + g) * kAsStride + ks + q];
+#pragma unroll
+        for (int nb = 0; nb < 4; ++nb) bf[nb] = sm.Bs[(ks + q) * kBsStride + wn * 32 + nb * 8 + g];
+#pragma unroll
+        for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+          for (int nb = 0; nb < 4; ++nb) dmma_8x8x4(acc[mb][nb][0], acc[mb][nb][1], af[mb], bf[nb]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int gr = r0 + wm * 16 + mb * 8 + g;
+          const int gc = c0 + wn * 32 + nb * 8 + 2 * q + h;
+          if (gr < n && gc < n && (gc < kb || gc >= kb + jb)) {
+            double v = acc[mb][nb][h];
+            if (gr >= kb && gr < kb + jb) v -= w.R[(int64_t)(gr - kb) * n + gc];  // the -I_J part
+            W[(int64_t)gr * n + gc] += v;
+          }
+        }
+  }
+
+  // dst <- src^{-1} by Gauss-Jordan with partial pivoting (same steps as
+  // gj_inverse_block), panels of kGridPanel columns. The panel is spread over
+  // the blocks by rows; each column step is one grid barrier: the owners of
+  // every row apply the step and publish the next column's pivot candidates.
+  // Returns 0, or 1 for a zero / non-finite pivot.
+  __device__ int inverse(const double* src, double* dst, int n, double* logabsdet) {
+    double* W = w.work;
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t t = tid(); t < nn; t += nthreads()) W[t] = src[t];
+    const int G = gridDim.x;
+    const int rows_per = (n + G - 1) / G;
+    const int r_lo = blockIdx.x * rows_per;
+    const int r_hi = min(n, r_lo + rows_per);
+    const int my_rows = r_hi > r_lo ? r_hi - r_lo : 0;
+    double* P0 = w.panel;
+    double* P1 = w.panel + (int64_t)kGridPanel * w.n_max;
+    double ld = 0.0;  // block 0, thread 0
+    int status = 0;
+    sync();
+    for (int kb = 0; kb < n && !status; kb += kGridPanel) {
+      const int jb = min(kGridPanel, n - kb);
+      // own rows of W[:, J] -> P0, and the candidates of column kb
+      {
+        double cv = -1.0;
+        int ci = 0x7fffffff;
+        for (int e = threadIdx.x; e < my_rows * jb; e += kThreads) {
+          const int r = r_lo + e / jb, c = e % jb;
+          const double v = W[(int64_t)r * n + kb + c];
+          P0[(int64_t)c * n + r] = v;
+          if (c == 0 && r >= kb) {
+            double a = fabs(v);
+            if (a != a) a = INFINITY;
+            if (a > cv || (a == cv && r < ci)) { cv = a; ci = r; }
+          }
+        }
+        double bv;
+        int bi;
+        block_argmax(cv, ci, S.red, &bv, &bi);
+        if (threadIdx.x == 0) {
+          w.cand_v[blockIdx.x] = bv;
+          w.cand_i[blockIdx.x] = bi;
+        }
+      }
+      sync();
+      for (int c = 0; c < jb; ++c) {
+        const int k = kb + c;
+        const double* Pin = (c & 1) ? P1 : P0;
+        double* Pout = (c & 1) ? P0 : P1;
+        const double* cvv = w.cand_v + (c & 1) * kMaxGrid;
+        const int* cii = w.cand_i + (c & 1) * kMaxGrid;
+        double pv;
+        int p;
+        {
+          double cv = -1.0;
+          int ci = 0x7fffffff;
+          for (int g = threadIdx.x; g < G; g += kThreads)
+            if (cvv[g] > cv || (cvv[g] == cv && cii[g] < ci)) { cv = cvv[g]; ci = cii[g]; }
+          block_argmax(cv, ci, S.red, &pv, &p);
+        }
+        if (!(pv > 0.0) || !(pv < INFINITY) || p < k || p >= n) { status = 1; break; }
+        if (threadIdx.x < jb) {
+          S.rowk[threadIdx.x] = Pin[(int64_t)threadIdx.x * n + k];
+          S.rowp[threadIdx.x] = Pin[(int64_t)threadIdx.x * n + p];
+        }
+        __syncthreads();
+        const double d = S.rowp[c];
+        const double inv = bcast0(1.0 / d);
+        if (leader()) {
+          ld += log(fabs(d));
+          w.piv[k] = p;
+        }
+        double cv = -1.0;
+        int ci = 0x7fffffff;
+        for (int e = threadIdx.x; e < my_rows * jb; e += kThreads) {
+          const int r = r_lo + e / jb, cc = e % jb;
+          const double prow = (cc == c) ? inv : S.rowp[cc] * inv;
+          double val;
+          if (r == k) {
+            val = prow;
+          } else {
+            const double srcv = (r == p) ? S.rowk[cc] : Pin[(int64_t)cc * n + r];
+            const double f = (r == p) ? S.rowk[c] : Pin[(int64_t)c * n + r];
+            val = (cc == c) ? -f * inv : fma(-f, prow, srcv);
+          }
+          Pout[(int64_t)cc * n + r] = val;
+          if (cc == c + 1 && r > k) {
+            double a = fabs(val);
+            if (a != a) a = INFINITY;
+            if (a > cv || (a == cv && r < ci)) { cv = a; ci = r; }
+          }
+        }
+        if (c + 1 < jb) {
+          double bv;
+          int bi;
+          block_argmax(cv, ci, S.red, &bv, &bi);
+          if (threadIdx.x == 0) {
+            w.cand_v[((c + 1) & 1) * kMaxGrid + blockIdx.x] = bv;
+            w.cand_i[((c + 1) & 1) * kMaxGrid + blockIdx.x] = bi;
+          }
+        }
+        sync();
+      }
+      if (status) break;
+      const double* Pf = (jb & 1) ? P1 : P0;
+      // panel -> W, the panel's row swaps on the other columns, pivot rows -> R
+      for (int e = threadIdx.x; e < my_rows * jb; e += kThreads) {
+        const int r = r_lo + e / jb, c = e % jb;
+        W[(int64_t)r * n + kb + c] = Pf[(int64_t)c * n + r];
+      }
+      for (int j = tid(); j < n; j += nthreads()) {
+        if (j >= kb && j < kb + jb) continue;
+        for (int c = 0; c < jb; ++c) {
+          const int k = kb + c, p = w.piv[k];
+          if (p != k) {
+            const double t0 = W[(int64_t)k * n + j];
+            W[(int64_t)k * n + j] = W[(int64_t)p * n + j];
+            W[(int64_t)p * n + j] = t0;
+          }
+        }
+        for (int c = 0; c < jb; ++c) w.R[(int64_t)c * n + j] = W[(int64_t)(kb + c) * n + j];
+      }
+      sync();
+      const int tiles = (n + kTileM - 1) / kTileM;
+      for (int t = blockIdx.x; t < tiles * tiles; t += G)
+        rank_update_tile(W, n, kb, jb, Pf, (t / tiles) * kTileM, (t % tiles) * kTileN);
+      sync();
+    }
+    if (leader()) w.misc[0] = ld;
+    if (!status) {
+      if (leader()) {
+        for (int j = 0; j < n; ++j) w.perm[j] = j;
+        for (int k = n - 1; k >= 0; --k) {
+          const int p = w.piv[k];
+          const int t0 = w.perm[k];
+          w.perm[k] = w.perm[p];
+          w.perm[p] = t0;
+        }
+      }
+      sync();
+      for (int64_t t = tid(); t < nn; t += nthreads()) {
+        const int64_t i = t / n, j = t % n;
+        dst[t] = W[i * n + w.perm[j]];
+      }
+    }
+    sync();
+    *logabsdet = w.misc[0];
+    sync();
+    return status;
+  }
+
+  __device__ void tally_reset() {
+    if (threadIdx.x == 0) S.work[0] = S.work[1] = S.work[2] = S.work[3] = 0;
+  }
+  __device__ void tally(int i, int c) {
+    if (threadIdx.x == 0) S.work[i] += c;
+  }
+  __device__ int tally_get(int i) const { return S.work[i]; }
+};
+
+}  // namespace lg

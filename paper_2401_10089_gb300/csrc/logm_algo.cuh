@@ -1,0 +1,635 @@
+// logm_algo.cuh -- Algorithm 1 of arXiv 2401.10089 (Sec. 6), written once
+// against an "ops" layer so that the same plan logic, square-root iteration
+// and graph evaluation run on one thread block per matrix (BlockOps, n <= 256)
+// and on the whole GPU per matrix (GridOps, large n).
+//
+// An Ops type provides: tid()/nthreads() for strided loops over the
+// participating threads, sync(), block-or-grid reductions sum/max/all/argmax
+// whose results are bitwise identical in every participating thread,
+// bcast0() (a scalar computed by thread 0 of each block), n-vectors vec(i),
+// norm1, matvec, gemm, lincomb and an in-place inverse, plus leader() and
+// tally() for the per-matrix outputs.
+//
+// Every branch below depends only on such uniform values, so all threads
+// (and, in the grid version, all blocks) take the same path.
+#pragma once
+
+#include <cstdint>
+
+#include "cta_linalg.cuh"
+#include "logm_internal.h"
+
+namespace lg {
+
+// Table table_simple_experiment (Sec. 3): the k = 5 scheme fitted to
+// -log(1 - x). h_{j,i}, g_{j,i} for j = 2..5, i = 2..j+1 in that order.
+static __constant__ double c_h5[14] = {
+    7.363757032799957e-02, -1.050281301619960e+00, 8.897468955192446e-02,
+    -1.599651928992725e-01, 9.577281350989334e-01, 5.394999133948797e-01,
+    6.700731102561937e-02, -5.158769100223212e-02, 1.094308587350110e+00,
+    1.027072285939197e-01, -8.964023050065877e-03, -2.100705663612491e-01,
+    1.949655359168707e-01, 1.117368056772713e+00};
+static __constant__ double c_g5[14] = {
+    -9.666134174379001e-01, -4.395519034717933e-01, 1.048664069004776e-01,
+    1.585606124033259e-01, 1.668066506920988e-01, -8.025600931705978e-02,
+    -1.159854366397558e-01, 1.066554944706011e-01, 1.127094008297975e+00,
+    2.702180425508705e-01, 4.137541209720699e-02, 4.857347452405025e-01,
+    -6.000256005636980e-01, 1.063393233943084e+00};
+// y_1 .. y_7 (y_1 = 0: no identity term)
+static __constant__ double c_y5[7] = {0.0, 1.0, 5.065546620208965e-01, 3.832512052972577e-01,
+                               1.088307723749078e+00, 2.787461897212877e-01,
+                               8.157421998489228e-01};
+
+constexpr double kUnitRoundoff = 0x1p-53;
+
+struct Slot {
+  double *Acur, *A2, *Y, *W1, *W2, *T1, *T2;
+};
+
+static __device__ __forceinline__ int m_of_k(int k) { return k == 1 ? 2 : (k == 2 ? 4 : 14); }
+static __device__ __forceinline__ int theta_slot(int k) { return k == 1 ? 0 : (k == 2 ? 1 : 2); }
+
+// x^m by repeated multiplication, so that "x^{1/m} <= Theta" is decided as
+// "x <= Theta^m" exactly the same way in every implementation.
+static __device__ __forceinline__ double ipow(double x, int m) {
+  double r = 1.0;
+  for (int i = 0; i < m; ++i) r *= x;
+  return r;
+}
+
+static __device__ __forceinline__ double load_elem(const void* base, int dtype, int64_t idx) {
+  return dtype == 0 ? static_cast<const double*>(base)[idx]
+                    : static_cast<double>(static_cast<const float*>(base)[idx]);
+}
+
+static __device__ __forceinline__ OutView out_view(void* base, int dtype, int64_t off) {
+  return OutView{dtype == 0 ? static_cast<void*>(static_cast<double*>(base) + off)
+                            : static_cast<void*>(static_cast<float*>(base) + off),
+                 dtype};
+}
+
+static __device__ __forceinline__ void matrix_geometry(const SmallParams& p, int b, int* n, int64_t* off) {
+  if (p.n_uniform > 0) {
+    *n = p.n_uniform;
+    *off = (int64_t)b * p.n_uniform * p.n_uniform;
+  } else {
+    *n = p.n_dev[b];
+    *off = p.off_dev[b];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise steps
+// ---------------------------------------------------------------------------
+template <class Ops>
+static __device__ int load_matrix(Ops& ops, const void* src, int dtype, int64_t off, int n, double* dst) {
+  int ok = 1;
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = ops.tid(); t < nn; t += ops.nthreads()) {
+    const double v = load_elem(src, dtype, off + t);
+    ok &= isfinite(v) ? 1 : 0;
+    dst[t] = v;
+  }
+  return ops.all(ok);  // also orders the stores before later reads
+}
+
+template <class Ops>
+static __device__ void store_matrix(Ops& ops, void* dst, int dtype, int64_t off, int n, const double* src) {
+  const OutView o = out_view(dst, dtype, off);
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = ops.tid(); t < nn; t += ops.nthreads()) store_out(o, t, src[t]);
+  ops.sync();
+}
+
+template <class Ops>
+static __device__ void fill_nan(Ops& ops, void* dst, int dtype, int64_t off, int n) {
+  const OutView o = out_view(dst, dtype, off);
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = ops.tid(); t < nn; t += ops.nthreads())
+    store_out(o, t, __longlong_as_double(0x7ff8000000000000ll));
+  ops.sync();
+}
+
+template <class Ops>
+static __device__ void copy_matrix(Ops& ops, double* dst, const double* src, int n) {
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = ops.tid(); t < nn; t += ops.nthreads()) dst[t] = src[t];
+  ops.sync();
+}
+
+template <class Ops>
+static __device__ void identity_matrix(Ops& ops, double* dst, int n) {
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = ops.tid(); t < nn; t += ops.nthreads()) dst[t] = (t / n == t % n) ? 1.0 : 0.0;
+  ops.sync();
+}
+
+// A_I2 = A_2 - 2A + I (eq. AI2), written over A_2.
+template <class Ops>
+static __device__ void ai2_from(Ops& ops, Slot& M, int n) {
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = ops.tid(); t < nn; t += ops.nthreads()) {
+    double v = M.A2[t] - 2.0 * M.Acur[t];
+    if (t / n == t % n) v += 1.0;
+    M.A2[t] = v;
+  }
+  ops.sync();
+}
+
+// X = -(A - I), in place.
+template <class Ops>
+static __device__ void to_x(Ops& ops, double* A, int n) {
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = ops.tid(); t < nn; t += ops.nthreads()) {
+    double v = A[t];
+    if (t / n == t % n) v -= 1.0;
+    A[t] = -v;
+  }
+  ops.sync();
+}
+
+// ---------------------------------------------------------------------------
+// 1-norm estimate of ||B^p||_1, B = Acur - I (Higham 1988, the estimator the
+// paper cites in Sec. 6). With A_I2 = B^2 (eq. AI2) the power is applied as
+// B^{p mod 2} A_I2^{p div 2} (Sec. 6, item 2). One vector, at most 5 sweeps,
+// ties to the smallest index, sign(0) = +1, then the alternating-sign test.
+// ---------------------------------------------------------------------------
+template <class Ops>
+static __device__ void apply_power(Ops& ops, const double* Acur, const double* AI2, int n, int p, double* v,
+                            double* tmp, int trans) {
+  const int q = AI2 ? (p & 1) : p;
+  const int r = AI2 ? (p >> 1) : 0;
+  ops.tally(3, q + r);
+  double* cur = v;
+  double* oth = tmp;
+  if (!trans) {
+    for (int t = 0; t < r; ++t) {
+      ops.matvec(AI2, n, 0.0, cur, oth, 0);
+      double* s = cur; cur = oth; oth = s;
+    }
+    for (int t = 0; t < q; ++t) {
+      ops.matvec(Acur, n, 1.0, cur, oth, 0);
+      double* s = cur; cur = oth; oth = s;
+    }
+  } else {
+    for (int t = 0; t < q; ++t) {
+      ops.matvec(Acur, n, 1.0, cur, oth, 1);
+      double* s = cur; cur = oth; oth = s;
+    }
+    for (int t = 0; t < r; ++t) {
+      ops.matvec(AI2, n, 0.0, cur, oth, 1);
+      double* s = cur; cur = oth; oth = s;
+    }
+  }
+  if (cur != v) {
+    for (int i = ops.tid(); i < n; i += ops.nthreads()) v[i] = cur[i];
+    ops.sync();
+  }
+}
+
+template <class Ops>
+static __device__ void argmax_abs(Ops& ops, const double* x, int n, double* bv, int* j) {
+  double cv = -1.0;
+  int ci = n;
+  for (int i = ops.tid(); i < n; i += ops.nthreads()) {
+    const double a = fabs(x[i]);
+    if (a > cv) { cv = a; ci = i; }
+  }
+  ops.argmax(cv, ci, bv, j);
+}
+
+template <class Ops>
+static __device__ double normest_pow(Ops& ops, const double* Acur, const double* AI2, int n, int p) {
+  double* x = ops.vec(0);
+  double* tmp = ops.vec(1);
+  double* xi = ops.vec(2);
+  for (int i = ops.tid(); i < n; i += ops.nthreads()) x[i] = 1.0 / n;
+  ops.sync();
+  apply_power(ops, Acur, AI2, n, p, x, tmp, 0);
+  double s0 = 0.0;
+  for (int i = ops.tid(); i < n; i += ops.nthreads()) s0 += fabs(x[i]);
+  double est = ops.sum(s0);
+  if (n > 1) {
+    for (int i = ops.tid(); i < n; i += ops.nthreads()) {
+      xi[i] = (x[i] >= 0.0) ? 1.0 : -1.0;
+      x[i] = xi[i];
+    }
+    ops.sync();
+    apply_power(ops, Acur, AI2, n, p, x, tmp, 1);
+    double bv;
+    int j;
+    argmax_abs(ops, x, n, &bv, &j);
+    for (int sweep = 2; sweep <= 5; ++sweep) {
+      ops.sync();  // everyone has read x before it is overwritten
+      for (int i = ops.tid(); i < n; i += ops.nthreads()) x[i] = (i == j) ? 1.0 : 0.0;
+      ops.sync();
+      apply_power(ops, Acur, AI2, n, p, x, tmp, 0);
+      double sn = 0.0;
+      int same = 1;
+      for (int i = ops.tid(); i < n; i += ops.nthreads()) {
+        sn += fabs(x[i]);
+        same &= (((x[i] >= 0.0) ? 1.0 : -1.0) == xi[i]);
+      }
+      const double est_new = ops.sum(sn);
+      same = ops.all(same);
+      if (same || est_new <= est) {
+        if (est_new > est) est = est_new;
+        break;
+      }
+      est = est_new;
+      for (int i = ops.tid(); i < n; i += ops.nthreads()) {
+        xi[i] = (x[i] >= 0.0) ? 1.0 : -1.0;
+        x[i] = xi[i];
+      }
+      ops.sync();
+      apply_power(ops, Acur, AI2, n, p, x, tmp, 1);
+      const int jlast = j;
+      argmax_abs(ops, x, n, &bv, &j);
+      const double zlast = fabs(x[jlast]);
+      if (zlast == bv) break;
+    }
+    ops.sync();
+    for (int i = ops.tid(); i < n; i += ops.nthreads())
+      x[i] = ((i & 1) ? -1.0 : 1.0) * (1.0 + (double)i / (double)(n - 1));
+    ops.sync();
+    apply_power(ops, Acur, AI2, n, p, x, tmp, 0);
+    double sa = 0.0;
+    for (int i = ops.tid(); i < n; i += ops.nthreads()) sa += fabs(x[i]);
+    const double alt = 2.0 * ops.sum(sa) / (3.0 * n);
+    if (alt > est) est = alt;
+  }
+  ops.sync();
+  return est;
+}
+
+// ---------------------------------------------------------------------------
+// alpha_m <= Theta by eqs. (alphaapprox), (normAm9), (alpha2term1),
+// (normAm9plus1) of Sec. 6. AI2 == nullptr means s = 0 (powers of B itself).
+// ---------------------------------------------------------------------------
+struct EstState {
+  double t_m, t_m1;
+  int m, n_est;
+};
+
+template <class Ops>
+static __device__ int alpha_test(Ops& ops, const double* Acur, const double* AI2, int n, double nB, double nI2,
+                          int m, double theta, EstState& st, double* alpha) {
+  const double th_m = ipow(theta, m), th_m1 = ipow(theta, m + 1);
+  double t1, t2;
+  int have_est1 = 0;
+  st.m = m;
+  st.t_m = -1.0;
+  st.t_m1 = -1.0;
+  if (AI2 && m == 2) {
+    t1 = nI2;
+  } else if (AI2 && ipow(nI2, m / 2) <= th_m) {
+    t1 = ipow(nI2, m / 2);
+  } else {
+    t1 = normest_pow(ops, Acur, AI2, n, m);
+    st.n_est++;
+    st.t_m = t1;
+    have_est1 = 1;
+  }
+  if (!(t1 <= th_m)) {
+    *alpha = pow(t1, 1.0 / m);
+    return 0;
+  }
+  const double base = have_est1 ? t1 : (AI2 ? ipow(nI2, m / 2) : t1);
+  if (base * nB <= th_m1) {
+    t2 = base * nB;
+  } else {
+    t2 = normest_pow(ops, Acur, AI2, n, m + 1);
+    st.n_est++;
+    st.t_m1 = t2;
+  }
+  const double a1 = pow(t1, 1.0 / m), a2 = pow(t2, 1.0 / (m + 1));
+  *alpha = a1 > a2 ? a1 : a2;
+  return t2 <= th_m1;
+}
+
+// Order search (Step 'StepFinminm' of Algorithm 1, Sec. 6): min_im from the
+// loop's estimates (eqs. min_in, min_inp), max_in from the rough bound (eq.
+// roughmax_even; every available m_k is even), then an increasing scan that
+// takes k+1 at once when alpha_{m_k} is above Theta_k but not above Theta_{k+1}.
+template <class Ops>
+static __device__ int order_search(Ops& ops, const double* Acur, const double* AI2, int n, double nB, double nI2,
+                            int k_max, const double* theta, const EstState* loop_est) {
+  int cands[3], nc = 0;
+  const int all[3] = {1, 2, 5};
+  for (int t = 0; t < 3; ++t)
+    if (all[t] <= k_max) cands[nc++] = all[t];
+  if (nc == 0) return k_max;
+  int lo = 0;
+  if (loop_est && loop_est->t_m >= 0.0) {
+    const int mm = loop_est->m;
+    while (lo < nc - 1) {
+      const double th = theta[theta_slot(cands[lo])];
+      int ok = loop_est->t_m <= ipow(th, mm);
+      if (ok && loop_est->t_m1 >= 0.0) ok = loop_est->t_m1 <= ipow(th, mm + 1);
+      if (ok) break;
+      ++lo;
+    }
+  }
+  int hi = nc - 1;
+  for (int t = 0; t < nc; ++t) {
+    const int m = m_of_k(cands[t]);
+    const double th = theta[theta_slot(cands[t])];
+    if (ipow(nI2, m / 2) * nB <= ipow(th, m + 1)) {
+      hi = t;
+      break;
+    }
+  }
+  if (lo >= hi) return cands[hi];
+  for (int t = lo; t < hi; ++t) {
+    const int m = m_of_k(cands[t]);
+    const double th = theta[theta_slot(cands[t])];
+    EstState st{-1.0, -1.0, m, 0};
+    double a;
+    if (alpha_test(ops, Acur, AI2, n, nB, nI2, m, th, st, &a)) return cands[t];
+    const double thn = theta[theta_slot(cands[t + 1])];
+    const double t1 = (st.t_m >= 0.0) ? st.t_m : (m == 2 ? nI2 : ipow(nI2, m / 2));
+    if (t1 <= ipow(thn, m)) {
+      double t2 = st.t_m1;
+      if (t2 < 0.0) {
+        if (t1 * nB <= ipow(thn, m + 1))
+          t2 = t1 * nB;
+        else
+          t2 = normest_pow(ops, Acur, AI2, n, m + 1);
+      }
+      if (t2 <= ipow(thn, m + 1)) return cands[t + 1];
+    }
+  }
+  return cands[hi];
+}
+
+// ---------------------------------------------------------------------------
+// Scaled Denman-Beavers square root, eq. (ScalDB): X_0 = A (in Acur, in
+// place), Y_0 = I, mu_k = |det X_k det Y_k|^{-1/(2n)} from the pivots of the
+// two inverses. Stop when the relative 1-norm change of X is <= 10 sqrt(n) u,
+// or, once scaling is off and the change has reached 1e-7, when it no longer
+// halves; scaling is switched off below 1e-2.
+// Returns 0 (converged), 1 (singular) or 2 (no convergence).
+// ---------------------------------------------------------------------------
+template <class Ops>
+static __device__ int db_sqrt(Ops& ops, Slot& M, int n, int max_db, int* iters_out) {
+  double* X = M.Acur;
+  double* Y = M.Y;
+  identity_matrix(ops, Y, n);
+  const double tol = 10.0 * sqrt((double)n) * kUnitRoundoff;
+  int scale = 1, status = 2, it;
+  double dprev = INFINITY;
+  for (it = 1; it <= max_db; ++it) {
+    double ldx, ldy;
+    ops.tally(0, 1);
+    ops.tally(1, (it == 1) ? 1 : 2);
+    if (ops.inverse(X, M.W1, n, &ldx)) { status = 1; break; }
+    if (it == 1) {
+      // Y_0 = I: its inverse is I and log|det Y_0| = 0 exactly.
+      identity_matrix(ops, M.W2, n);
+      ldy = 0.0;
+    } else {
+      if (ops.inverse(Y, M.W2, n, &ldy)) { status = 1; break; }
+    }
+    const double mu = ops.bcast0(scale ? exp(-(ldx + ldy) / (2.0 * n)) : 1.0);
+    const double imu = ops.bcast0(1.0 / mu);
+    double sd = 0.0, sx = 0.0;
+    for (int j = ops.tid(); j < n; j += ops.nthreads()) {
+      double cd = 0.0, cx = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const int64_t t = (int64_t)i * n + j;
+        const double xo = X[t];
+        const double xn = 0.5 * fma(mu, xo, M.W2[t] * imu);
+        Y[t] = 0.5 * fma(mu, Y[t], M.W1[t] * imu);
+        X[t] = xn;
+        cd += fabs(xn - xo);
+        cx += fabs(xn);
+      }
+      sd = nanmax(sd, cd);
+      sx = nanmax(sx, cx);
+    }
+    const double nd = ops.max(sd);
+    const double nx = ops.max(sx);
+    const double delta = nd / nx;
+    if (!(delta == delta)) { status = 2; break; }
+    if (delta <= tol) { status = 0; break; }
+    if (!scale && dprev <= 1e-7 && delta > 0.5 * dprev) { status = 0; break; }
+    if (delta < 1e-2) scale = 0;
+    dprev = delta;
+  }
+  *iters_out = it > max_db ? max_db : it;
+  return status;
+}
+
+// ---------------------------------------------------------------------------
+// Graph evaluation, eq. (five_mult_degopt): out = scale * z(X) with P_2 = X
+// (Acur), P_3 = X^2 (A2) given. For Algorithm 1, scale = -2^s (eq. logipASTM
+// and the final squaring step): a power of two, so it changes no rounding.
+// ---------------------------------------------------------------------------
+template <class Ops>
+static __device__ void graph_eval(Ops& ops, int k, int n, Slot& M, double scale, OutView out) {
+  double* P2 = M.Acur;
+  double* P3 = M.A2;
+  if (k == 1) {  // z = X + X^2/2 (Taylor T_2)
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t t = ops.tid(); t < nn; t += ops.nthreads()) store_out(out, t, scale * fma(0.5, P3[t], P2[t]));
+    ops.sync();
+    return;
+  }
+  if (k == 2) {  // P_4 = X^2 (X/3 + X^2/4); z = X + X^2/2 + P_4 (Taylor T_4)
+    EpiTerms r{{P2, P3}, {1.0 / 3.0, 0.25}, 2};
+    ops.lincomb(n, r, M.T2);
+    EpiTerms e{{P2, P3}, {scale, 0.5 * scale}, 2};
+    ops.tally(2, 1);
+    ops.gemm(n, P3, 0.0, M.T2, 0.0, scale, e, out);
+    return;
+  }
+  // k = 5: P_4 .. P_7 from Table table_simple_experiment
+  double* P[8] = {nullptr, nullptr, P2, P3, M.Y, M.W1, M.W2, nullptr};
+  int t = 0;
+  for (int j = 2; j <= 5; ++j) {
+    EpiTerms hl, gl;
+    hl.count = gl.count = j;
+    for (int i = 2; i <= j + 1; ++i, ++t) {
+      hl.M[i - 2] = P[i];
+      hl.c[i - 2] = c_h5[t];
+      gl.M[i - 2] = P[i];
+      gl.c[i - 2] = c_g5[t];
+    }
+    ops.lincomb(n, hl, M.T1);
+    ops.lincomb(n, gl, M.T2);
+    ops.tally(2, 1);
+    if (j < 5) {
+      EpiTerms none;
+      none.count = 0;
+      ops.gemm(n, M.T1, 0.0, M.T2, 0.0, 1.0, none, OutView{P[j + 2], 0});
+    } else {
+      EpiTerms e;
+      e.count = 5;
+      for (int i = 2; i <= 6; ++i) {
+        e.M[i - 2] = P[i];
+        e.c[i - 2] = scale * c_y5[i - 1];
+      }
+      ops.gemm(n, M.T1, 0.0, M.T2, 0.0, scale * c_y5[6], e, out);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One matrix, per entry point.
+// ---------------------------------------------------------------------------
+template <class Ops>
+static __device__ void run_execute(Ops& ops, const SmallParams& p, int b, int n, int64_t off, Slot& M) {
+  const int km = p.k_max;
+  ops.tally_reset();
+  const int finite = load_matrix(ops, p.A, p.dtype, off, n, M.Acur);
+  if (!finite) {
+    fill_nan(ops, p.L, p.dtype, off, n);
+    if (ops.leader()) {
+      if (p.stats)
+        for (int t = 0; t < 4; ++t) p.stats[4 * b + t] = 0;
+      p.info[b] = 4;
+      if (p.s_out) p.s_out[b] = 0;
+      if (p.k_out) p.k_out[b] = km;
+    }
+    return;
+  }
+  const int m = m_of_k(km);
+  const double th = p.theta[theta_slot(km)];
+  double nB = ops.norm1(M.Acur, n, 1.0), nI2 = 0.0;
+  int s = 0, have_ai2 = 0, info = 0, finish = nB <= th;
+  double alpha = nB;
+  EstState last{-1.0, -1.0, m, 0};
+  while (!finish && s < p.max_sqrt) {
+    EstState st{-1.0, -1.0, m, 0};
+    finish = alpha_test(ops, M.Acur, have_ai2 ? M.A2 : nullptr, n, nB, nI2, m, th, st, &alpha);
+    last = st;
+    if (finish) break;
+    if (p.ctx && s < p.ctx_levels) {
+      double* ck = p.ctx + ((int64_t)b * p.ctx_levels + s) * (int64_t)p.ctx_nmax * p.ctx_nmax;
+      copy_matrix(ops, ck, M.Acur, n);
+    }
+    copy_matrix(ops, M.A2, M.Acur, n);
+    int it;
+    const int r = db_sqrt(ops, M, n, p.max_db, &it);
+    if (r == 1) { info = 1; break; }
+    if (r == 2 && info == 0) info = 2;
+    ai2_from(ops, M, n);
+    nB = ops.norm1(M.Acur, n, 1.0);
+    nI2 = ops.norm1(M.A2, n, 0.0);
+    have_ai2 = 1;
+    ++s;
+  }
+  int k = km;
+  if (info == 1) {
+    fill_nan(ops, p.L, p.dtype, off, n);
+  } else {
+    if (!finish && info == 0) info = 3;
+    if (!have_ai2) {
+      EpiTerms none;
+      none.count = 0;
+      ops.tally(2, 1);
+      ops.gemm(n, M.Acur, 1.0, M.Acur, 1.0, 1.0, none, OutView{M.A2, 0});
+      nI2 = ops.norm1(M.A2, n, 0.0);
+    }
+    if (finish) k = order_search(ops, M.Acur, M.A2, n, nB, nI2, km, p.theta, last.t_m >= 0.0 ? &last : nullptr);
+    to_x(ops, M.Acur, n);  // P_2 = X = -(A - I)
+    graph_eval(ops, k, n, M, -ldexp(1.0, s), out_view(p.L, p.dtype, off));
+  }
+  if (ops.leader()) {
+    p.info[b] = info;
+    if (p.s_out) p.s_out[b] = s;
+    if (p.k_out) p.k_out[b] = k;
+    if (p.alpha) p.alpha[b] = alpha;
+    if (p.stats)
+      for (int t = 0; t < 4; ++t) p.stats[4 * b + t] = ops.tally_get(t);
+  }
+}
+
+template <class Ops>
+static __device__ void run_plan(Ops& ops, const SmallParams& p, int b, int n, int64_t off, Slot& M) {
+  const int km = p.k_max;
+  const int finite = load_matrix(ops, p.A, p.dtype, off, n, M.Acur);
+  int fin2 = 1;
+  if (p.AI2_in) fin2 = load_matrix(ops, p.AI2_in, p.dtype, off, n, M.A2);
+  if (!finite || !fin2) {
+    if (ops.leader()) {
+      p.info[b] = 4;
+      p.finish[b] = 0;
+      p.k_out[b] = km;
+      p.alpha[b] = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    return;
+  }
+  const int m = m_of_k(km);
+  const double th = p.theta[theta_slot(km)];
+  const double nB = ops.norm1(M.Acur, n, 1.0);
+  EstState st{-1.0, -1.0, m, 0};
+  int fin;
+  double a;
+  double nI2 = p.AI2_in ? ops.norm1(M.A2, n, 0.0) : 0.0;
+  if (!p.AI2_in && nB <= th) {
+    fin = 1;
+    a = nB;
+  } else {
+    fin = alpha_test(ops, M.Acur, p.AI2_in ? M.A2 : nullptr, n, nB, nI2, m, th, st, &a);
+  }
+  if (!p.AI2_in) {
+    EpiTerms none;
+    none.count = 0;
+    ops.gemm(n, M.Acur, 1.0, M.Acur, 1.0, 1.0, none, OutView{M.A2, 0});
+    nI2 = ops.norm1(M.A2, n, 0.0);
+  }
+  const int k = fin ? order_search(ops, M.Acur, M.A2, n, nB, nI2, km, p.theta, &st) : km;
+  if (ops.leader()) {
+    p.info[b] = 0;
+    p.finish[b] = fin;
+    p.k_out[b] = k;
+    p.alpha[b] = a;
+  }
+}
+
+template <class Ops>
+static __device__ void run_sqrt(Ops& ops, const SmallParams& p, int b, int n, int64_t off, Slot& M) {
+  const int finite = load_matrix(ops, p.A_inout, p.dtype, off, n, M.Acur);
+  if (!finite) {
+    if (ops.leader()) {
+      p.info[b] = 4;
+      if (p.iters) p.iters[b] = 0;
+    }
+    return;
+  }
+  copy_matrix(ops, M.A2, M.Acur, n);
+  if (p.A2_out) store_matrix(ops, p.A2_out, p.dtype, off, n, M.A2);
+  int it;
+  const int r = db_sqrt(ops, M, n, p.max_db, &it);
+  store_matrix(ops, p.A_inout, p.dtype, off, n, M.Acur);
+  if (p.AI2_out) {
+    ai2_from(ops, M, n);
+    store_matrix(ops, p.AI2_out, p.dtype, off, n, M.A2);
+  }
+  if (ops.leader()) {
+    p.info[b] = r;
+    if (p.iters) p.iters[b] = it;
+  }
+}
+
+template <class Ops>
+static __device__ void run_graph(Ops& ops, const SmallParams& p, int b, int n, int64_t off, Slot& M) {
+  const int k = p.k_in[b];
+  if (!(k == 1 || k == 2 || k == 5)) {
+    if (ops.leader() && p.info) p.info[b] = -1;
+    return;
+  }
+  load_matrix(ops, p.X, p.dtype, off, n, M.Acur);
+  if (p.P3) {
+    load_matrix(ops, p.P3, p.dtype, off, n, M.A2);
+  } else {
+    EpiTerms none;
+    none.count = 0;
+    ops.gemm(n, M.Acur, 0.0, M.Acur, 0.0, 1.0, none, OutView{M.A2, 0});
+  }
+  graph_eval(ops, k, n, M, 1.0, out_view(p.L, p.dtype, off));
+  if (ops.leader() && p.info) p.info[b] = 0;
+}
+
+}  // namespace lg

@@ -31,7 +31,33 @@ int opts_ok(const logm_options* o) {
   return 1;
 }
 
-void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o, void* ws) {
+// Workspace: [small part | large part]. The small part (queue, order, one
+// slot of kSlotMats matrices per resident block) serves matrices with
+// n <= kSmallMaxN; the large part (one whole-GPU slot) serves n > kSmallMaxN.
+struct WsLayout {
+  int small_nmax;   // 0: no small pass
+  int large_nmax;   // 0: no large pass
+  size_t small_bytes, large_off, total;
+};
+
+WsLayout ws_layout(const logm_batch* b) {
+  WsLayout L{};
+  const int n_max = batch_n_max(b);
+  if (n_max <= 0) return L;
+  const bool ragged = b->n_uniform <= 0;
+  if (n_max <= lg::kSmallMaxN) {
+    L.small_nmax = n_max;
+  } else {
+    L.large_nmax = n_max;
+    if (ragged) L.small_nmax = lg::kSmallMaxN;
+  }
+  L.small_bytes = L.small_nmax ? lg::small_workspace_bytes(b->count, L.small_nmax) : 0;
+  L.large_off = (L.small_bytes + 255) / 256 * 256;
+  L.total = L.large_off + (L.large_nmax ? lg::large_workspace_bytes(L.large_nmax) : 0);
+  return L;
+}
+
+void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o) {
   std::memset(&p, 0, sizeof(p));
   p.count = b->count;
   p.dtype = b->dtype;
@@ -51,23 +77,40 @@ void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o,
     p.max_db = 50;
     for (int t = 0; t < 3; ++t) p.theta[t] = kThetaPaper[t];
   }
-  char* w = static_cast<char*>(ws);
-  p.queue = reinterpret_cast<int32_t*>(w);
-  const size_t ob = lg::small_order_bytes(b->count);
-  p.order = reinterpret_cast<int32_t*>(w + 256);
-  p.order_aux = p.order + b->count;
-  p.slots = reinterpret_cast<double*>(w + 256 + ob);
-  p.n_slots = lg::small_kernel_slots(b->count);
+  p.ctx_nmax = p.n_max;
 }
 
-int check_ws(const logm_batch* b, const logm_options* o, void* ws, size_t ws_bytes) {
-  if (!ws) return LOGM_ERR_WORKSPACE;
-  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return LOGM_ERR_WORKSPACE;
-  if (ws_bytes < logm_workspace_size(b, o)) return LOGM_ERR_WORKSPACE;
+// Launch the small pass and/or the large pass for this batch.
+int run_passes(lg::Mode mode, lg::SmallParams& p, const logm_batch* b, void* ws, cudaStream_t st) {
+  const WsLayout L = ws_layout(b);
+  char* w = static_cast<char*>(ws);
+  if (L.small_nmax) {
+    lg::SmallParams q = p;
+    q.n_max = L.small_nmax;
+    q.large_pass = L.large_nmax ? 1 : 0;
+    q.queue = reinterpret_cast<int32_t*>(w);
+    const size_t ob = lg::small_order_bytes(b->count);
+    q.order = reinterpret_cast<int32_t*>(w + 256);
+    q.order_aux = q.order + b->count;
+    q.slots = reinterpret_cast<double*>(w + 256 + ob);
+    q.n_slots = lg::small_kernel_slots(b->count);
+    if (lg::launch_small(mode, q, st) != cudaSuccess) return LOGM_ERR_CUDA;
+  }
+  if (L.large_nmax) {
+    lg::SmallParams q = p;
+    q.n_max = L.large_nmax;
+    q.large_pass = L.small_nmax ? 1 : 0;
+    if (lg::launch_large(mode, q, w + L.large_off, st) != cudaSuccess) return LOGM_ERR_CUDA;
+  }
   return LOGM_SUCCESS;
 }
 
-int finish_launch(cudaError_t e) { return e == cudaSuccess ? LOGM_SUCCESS : LOGM_ERR_CUDA; }
+int check_ws(const logm_batch* b, void* ws, size_t ws_bytes) {
+  if (!ws) return LOGM_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return LOGM_ERR_WORKSPACE;
+  if (ws_bytes < ws_layout(b).total) return LOGM_ERR_WORKSPACE;
+  return LOGM_SUCCESS;
+}
 
 }  // namespace
 
@@ -77,10 +120,8 @@ int logm_version(void) { return 100; }
 
 size_t logm_workspace_size(const logm_batch* batch, const logm_options* opts) {
   (void)opts;
-  const int n_max = batch_n_max(batch);
-  if (n_max <= 0) return 0;
-  if (n_max > lg::kSmallMaxN) return 0;
-  return lg::small_workspace_bytes(batch->count, n_max);
+  if (batch_n_max(batch) <= 0) return 0;
+  return ws_layout(batch).total;
 }
 
 size_t logm_context_size(const logm_batch* batch, const logm_options* opts) {
@@ -97,17 +138,16 @@ int logm_plan(const logm_batch* batch, const logm_options* opts, const void* A, 
   if (n_max <= 0 || !opts_ok(opts)) return LOGM_ERR_INVALID_ARG;
   if (batch->count == 0) return LOGM_SUCCESS;
   if (!A || !finish_dev || !k_dev || !alpha_dev || !info_dev) return LOGM_ERR_INVALID_ARG;
-  if (n_max > lg::kSmallMaxN) return LOGM_ERR_UNSUPPORTED;
-  if (int r = check_ws(batch, opts, ws, ws_bytes)) return r;
+  if (int r = check_ws(batch, ws, ws_bytes)) return r;
   lg::SmallParams p;
-  fill_common(p, batch, opts, ws);
+  fill_common(p, batch, opts);
   p.A = A;
   p.AI2_in = AI2;
   p.finish = finish_dev;
   p.k_out = k_dev;
   p.alpha = alpha_dev;
   p.info = info_dev;
-  return finish_launch(lg::launch_small(lg::kModePlan, p, static_cast<cudaStream_t>(stream)));
+  return run_passes(lg::kModePlan, p, batch, ws, static_cast<cudaStream_t>(stream));
 }
 
 int logm_sqrt(const logm_batch* batch, const logm_options* opts, void* A, void* A2_out,
@@ -117,17 +157,16 @@ int logm_sqrt(const logm_batch* batch, const logm_options* opts, void* A, void* 
   if (n_max <= 0 || !opts_ok(opts)) return LOGM_ERR_INVALID_ARG;
   if (batch->count == 0) return LOGM_SUCCESS;
   if (!A || !info_dev) return LOGM_ERR_INVALID_ARG;
-  if (n_max > lg::kSmallMaxN) return LOGM_ERR_UNSUPPORTED;
-  if (int r = check_ws(batch, opts, ws, ws_bytes)) return r;
+  if (int r = check_ws(batch, ws, ws_bytes)) return r;
   lg::SmallParams p;
-  fill_common(p, batch, opts, ws);
+  fill_common(p, batch, opts);
   p.A_inout = A;
   p.A2_out = A2_out;
   p.AI2_out = AI2_out;
   p.active = active_dev;
   p.iters = iters_dev;
   p.info = info_dev;
-  return finish_launch(lg::launch_small(lg::kModeSqrt, p, static_cast<cudaStream_t>(stream)));
+  return run_passes(lg::kModeSqrt, p, batch, ws, static_cast<cudaStream_t>(stream));
 }
 
 int logm_graph_eval(const logm_batch* batch, int32_t precision, const void* X, const void* P3,
@@ -137,17 +176,16 @@ int logm_graph_eval(const logm_batch* batch, int32_t precision, const void* X, c
   if (precision < LOGM_PREC_FP64 || precision > LOGM_PREC_BF16X3) return LOGM_ERR_INVALID_ARG;
   if (batch->count == 0) return LOGM_SUCCESS;
   if (!X || !k_dev || !Z) return LOGM_ERR_INVALID_ARG;
-  if (n_max > lg::kSmallMaxN) return LOGM_ERR_UNSUPPORTED;
   if (precision != LOGM_PREC_FP64) return LOGM_ERR_UNSUPPORTED;
-  if (int r = check_ws(batch, nullptr, ws, ws_bytes)) return r;
+  if (int r = check_ws(batch, ws, ws_bytes)) return r;
   lg::SmallParams p;
-  fill_common(p, batch, nullptr, ws);
+  fill_common(p, batch, nullptr);
   p.X = X;
   p.P3 = P3;
   p.k_in = k_dev;
   p.L = Z;
   p.precision = precision;
-  return finish_launch(lg::launch_small(lg::kModeGraph, p, static_cast<cudaStream_t>(stream)));
+  return run_passes(lg::kModeGraph, p, batch, ws, static_cast<cudaStream_t>(stream));
 }
 
 int logm_execute(const logm_batch* batch, const logm_options* opts, const void* A, void* L,
@@ -157,11 +195,10 @@ int logm_execute(const logm_batch* batch, const logm_options* opts, const void* 
   if (n_max <= 0 || !opts_ok(opts)) return LOGM_ERR_INVALID_ARG;
   if (batch->count == 0) return LOGM_SUCCESS;
   if (!A || !L || !info_dev) return LOGM_ERR_INVALID_ARG;
-  if (n_max > lg::kSmallMaxN) return LOGM_ERR_UNSUPPORTED;
   if (opts->precision != LOGM_PREC_FP64) return LOGM_ERR_UNSUPPORTED;
-  if (int r = check_ws(batch, opts, ws, ws_bytes)) return r;
+  if (int r = check_ws(batch, ws, ws_bytes)) return r;
   lg::SmallParams p;
-  fill_common(p, batch, opts, ws);
+  fill_common(p, batch, opts);
   p.A = A;
   p.L = L;
   p.s_out = s_dev;
@@ -170,7 +207,7 @@ int logm_execute(const logm_batch* batch, const logm_options* opts, const void* 
   p.stats = stats_dev;
   p.ctx = static_cast<double*>(ctx);
   p.ctx_levels = lg::kCtxLevels;
-  return finish_launch(lg::launch_small(lg::kModeExecute, p, static_cast<cudaStream_t>(stream)));
+  return run_passes(lg::kModeExecute, p, batch, ws, static_cast<cudaStream_t>(stream));
 }
 
 int logm_backward(const logm_batch* batch, const logm_options* opts, const void* A, const void* ctx,

@@ -40,6 +40,7 @@ struct SmallParams {
   int32_t* stats;      // execute: [4 * count] DB iterations, inverses, products, matvecs
   double* ctx;         // execute: per-level checkpoints (NULL = none)
   int ctx_levels;
+  int ctx_nmax;        // n stride of the checkpoint layout (the batch's n_max)
   // workspace
   double* slots;       // n_slots * kSlotMats * n_max^2 doubles
   int32_t* queue;      // one counter, zeroed before the launch
@@ -47,6 +48,7 @@ struct SmallParams {
   int32_t* order_aux;  // [2 * kOrderBuckets + count]: bucket counts, bucket cursors, bucket per matrix
   int n_slots;
   int precision;       // graph products (FP64 in this kernel family)
+  int large_pass;      // 1: matrices with n > kSmallMaxN are left to the whole-GPU kernel
 };
 
 constexpr int kSlotMats = 7;
@@ -55,6 +57,9 @@ constexpr int kCtxLevels = 12;
 constexpr int kSmallMaxN = 256;  // largest n of the one-block-per-matrix kernels
 
 int small_kernel_slots(int count);
+size_t large_workspace_bytes(int n_max);
+int large_grid_size();
+cudaError_t launch_large(Mode mode, const SmallParams& p, void* ws, cudaStream_t stream);
 size_t small_workspace_bytes(int count, int n_max);
 size_t small_order_bytes(int count);
 cudaError_t launch_small(Mode mode, const SmallParams& p, cudaStream_t stream);

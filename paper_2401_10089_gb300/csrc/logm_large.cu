@@ -1,0 +1,138 @@
+// logm_large.cu -- Algorithm 1 of arXiv 2401.10089 (Sec. 6) with the whole
+// GPU on one matrix at a time, for n > kSmallMaxN (e.g. one 4096 x 4096
+// matrix). A single cooperative launch (all blocks resident) walks the batch;
+// the plan, the Denman-Beavers square roots (Gauss-Jordan inverses spread over
+// all SMs) and the graph products all run inside it, separated by bounded
+// grid barriers, with no host round trip.
+#include <cmath>
+
+#include "grid_ops.cuh"
+#include "logm_algo.cuh"
+#include "logm_internal.h"
+
+namespace lg {
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 2) k_logm_large(SmallParams p, GridWs w, Slot M) {
+  __shared__ GridSmem S;
+  GridOps ops{w, S, 0};
+  for (int b = 0; b < p.count; ++b) {
+    int n;
+    int64_t off;
+    matrix_geometry(p, b, &n, &off);
+    if (n <= kSmallMaxN && p.large_pass) continue;  // handled by the one-block-per-matrix kernel
+    if (n < 1 || n > p.n_max) {
+      if (ops.leader()) {
+        if (p.info) p.info[b] = -1;
+        if (p.s_out) p.s_out[b] = 0;
+        if (p.k_out) p.k_out[b] = p.k_max;
+      }
+      continue;
+    }
+    if (MODE == kModeSqrt && p.active && p.active[b] == 0) {
+      if (ops.leader()) {
+        p.info[b] = 0;
+        if (p.iters) p.iters[b] = 0;
+      }
+      continue;
+    }
+    if (MODE == kModeExecute) run_execute(ops, p, b, n, off, M);
+    if (MODE == kModePlan) run_plan(ops, p, b, n, off, M);
+    if (MODE == kModeSqrt) run_sqrt(ops, p, b, n, off, M);
+    if (MODE == kModeGraph) run_graph(ops, p, b, n, off, M);
+    ops.sync();
+    if (ops.leader() && *(volatile int*)w.err && p.info) p.info[b] = 5;  // barrier timed out
+  }
+}
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+struct LargeLayout {
+  size_t bar, partial, ipartial, cand_v, cand_i, vec, panel, R, piv, perm, misc, work, slot, total;
+};
+
+LargeLayout large_layout(int n_max) {
+  LargeLayout L{};
+  size_t o = 0;
+  const size_t nm = (size_t)n_max;
+  L.bar = o;      o = align256(o + 16);
+  L.partial = o;  o = align256(o + sizeof(double) * 2 * kMaxGrid);
+  L.ipartial = o; o = align256(o + sizeof(int) * 2 * kMaxGrid);
+  L.cand_v = o;   o = align256(o + sizeof(double) * 2 * kMaxGrid);
+  L.cand_i = o;   o = align256(o + sizeof(int) * 2 * kMaxGrid);
+  L.vec = o;      o = align256(o + sizeof(double) * 4 * nm);
+  L.panel = o;    o = align256(o + sizeof(double) * 2 * kGridPanel * nm);
+  L.R = o;        o = align256(o + sizeof(double) * kGridPanel * nm);
+  L.piv = o;      o = align256(o + sizeof(int) * nm);
+  L.perm = o;     o = align256(o + sizeof(int) * nm);
+  L.misc = o;     o = align256(o + sizeof(double) * 8);
+  L.work = o;     o = align256(o + sizeof(double) * nm * nm);
+  L.slot = o;     o = align256(o + sizeof(double) * kSlotMats * nm * nm);
+  L.total = o;
+  return L;
+}
+
+int g_large_grid = 0;
+
+template <int MODE>
+cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
+  const LargeLayout L = large_layout(p.n_max);
+  GridWs w{};
+  w.bar = reinterpret_cast<unsigned*>(ws + L.bar);
+  w.err = reinterpret_cast<int*>(ws + L.bar + 8);
+  w.partial = reinterpret_cast<double*>(ws + L.partial);
+  w.ipartial = reinterpret_cast<int*>(ws + L.ipartial);
+  w.cand_v = reinterpret_cast<double*>(ws + L.cand_v);
+  w.cand_i = reinterpret_cast<int*>(ws + L.cand_i);
+  w.vec = reinterpret_cast<double*>(ws + L.vec);
+  w.panel = reinterpret_cast<double*>(ws + L.panel);
+  w.R = reinterpret_cast<double*>(ws + L.R);
+  w.piv = reinterpret_cast<int*>(ws + L.piv);
+  w.perm = reinterpret_cast<int*>(ws + L.perm);
+  w.misc = reinterpret_cast<double*>(ws + L.misc);
+  w.work = reinterpret_cast<double*>(ws + L.work);
+  w.n_max = p.n_max;
+  const int64_t nn = (int64_t)p.n_max * p.n_max;
+  double* base = reinterpret_cast<double*>(ws + L.slot);
+  Slot M{base, base + nn, base + 2 * nn, base + 3 * nn, base + 4 * nn, base + 5 * nn, base + 6 * nn};
+
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_logm_large<MODE>, kThreads, 0);
+  if (e != cudaSuccess) return e;
+  int grid = sms * (per_sm < 2 ? per_sm : 2);
+  if (grid > kMaxGrid) grid = kMaxGrid;
+  if (grid < 1) return cudaErrorLaunchOutOfResources;
+  g_large_grid = grid;
+
+  e = cudaMemsetAsync(ws + L.bar, 0, 16, st);
+  if (e != cudaSuccess) return e;
+  SmallParams pp = p;
+  void* args[] = {&pp, &w, &M};
+  return cudaLaunchCooperativeKernel((const void*)k_logm_large<MODE>, dim3(grid), dim3(kThreads), args, 0, st);
+}
+
+}  // namespace
+
+size_t large_workspace_bytes(int n_max) { return large_layout(n_max).total; }
+
+int large_grid_size() { return g_large_grid; }
+
+cudaError_t launch_large(Mode mode, const SmallParams& p, void* ws, cudaStream_t st) {
+  if (p.count <= 0) return cudaSuccess;
+  char* w = static_cast<char*>(ws);
+  switch (mode) {
+    case kModeExecute: return launch_large_mode<kModeExecute>(p, w, st);
+    case kModePlan: return launch_large_mode<kModePlan>(p, w, st);
+    case kModeSqrt: return launch_large_mode<kModeSqrt>(p, w, st);
+    case kModeGraph: return launch_large_mode<kModeGraph>(p, w, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace lg
