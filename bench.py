@@ -1,9 +1,12 @@
 """Benchmark: matrix logarithms per second (and TFLOP/s) on GB300.
 
-Default workload: a batch of 512 real 256 x 256 matrices A = I + E, E seeded
-Gaussian rescaled so ||E||_1 is uniform in [0.2, 5] (synthetic stand-in for
-the paper's test sets, which are not available). One step = Algorithm 1 on the
-whole batch (plan, square roots, graph polynomial, 2^s scaling), FP64 path.
+Default workload (synthetic stand-in for the paper's test sets, which are not
+available): a batch of 512 real 256 x 256 matrices A = I + E, E seeded
+Gaussian rescaled so ||E||_1 is uniform in [0.2, 5], plus one 4096 x 4096
+A = Q T Q^T (T upper triangular, diag log-uniform in [1e-2, 1e2], off-diagonal
+Gaussian of standard deviation 0.1/n; with 0.1 literally T is numerically
+singular). One step = Algorithm 1 (plan, square roots, graph polynomial, 2^s
+scaling) on all 513 matrices, FP64 path.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -29,9 +32,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "logm matrices/s and TFLOP/s at stated rel. error: mixed/batched vs plain FP64"
-UNIT = "matrices/s"
+UNIT = "TFLOP/s"  # algorithmic FP64-equivalent work of the executed plan per second
 COUNT, N = 512, 256
-WORKLOAD = "batch of 512 real 256x256 A = I + E, ||E||_1 ~ U[0.2, 5] (seeded), FP64 path"
+NBIG = 4096
+WORKLOAD = ("512 x 256x256 A = I + E (||E||_1 ~ U[0.2, 5]) + one 4096x4096 A = Q T Q^T "
+            "(diag T log-uniform [1e-2, 1e2], off-diag N(0, (0.1/n)^2)), seeded, FP64 path")
 
 
 def measured_peaks():
@@ -42,12 +47,15 @@ def measured_peaks():
         return {}
 
 
-def fp64_peak_tflops():
-    """FP64 dense peak = measured BF16 dense peak x nominal FP64/BF16 ratio (1.25 / 2250)."""
+def fp64_peak_tflops(sustained: bool = False):
+    """FP64 dense peak = measured BF16 dense peak x nominal FP64/BF16 ratio (1.25 / 2250);
+    the sustained BF16 figure for a kernel that runs for seconds."""
     pk = measured_peaks()
-    if "bf16_tflops" in pk:
-        return pk["bf16_tflops"] * 1.25 / 2250.0, "of measured (bf16 burst x nominal fp64/bf16 ratio)"
-    return 1900.0 * 1.25 / 2250.0, "of fallback (1.9 PFLOP/s bf16 x nominal fp64/bf16 ratio)"
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+    if key in pk:
+        what = "sustained" if sustained else "burst"
+        return pk[key] * 1.25 / 2250.0, f"of measured (bf16 {what} x nominal fp64/bf16 ratio)"
+    return (1700.0 if sustained else 1900.0) * 1.25 / 2250.0, "of fallback (bf16 x nominal fp64/bf16 ratio)"
 
 
 class Clocks:
@@ -111,6 +119,18 @@ def algorithmic_flops(stats: np.ndarray, n: int) -> float:
     return float(((st[:, 1] + st[:, 2]) * 2.0 * n ** 3 + st[:, 3] * 2.0 * n ** 2).sum())
 
 
+def oracle_flops(diags, n: int) -> float:
+    """Algorithmic work of the oracle's executed plans, counted like the GPU's:
+    2n^3 per inverse (Y_0 = I needs none) and per graph product; the
+    estimator's 2n^2 matrix-vector products are left out (negligible)."""
+    tot = 0.0
+    for d in diags:
+        inverses = 2 * d["db_iters"] - d["s"]
+        products = (d["k"] - 1) + (1 if d["s"] == 0 else 0)
+        tot += 2.0 * n ** 3 * (inverses + products)
+    return tot
+
+
 def cpu_baseline(A_np, sample: int):
     """The oracle as it stands, on the host cores, on `sample` matrices of the workload."""
     import oracle
@@ -120,8 +140,9 @@ def cpu_baseline(A_np, sample: int):
     t0 = time.perf_counter()
     Ls, ds = oracle.logm_batch(mats, nthreads=cores)
     dt = time.perf_counter() - t0
-    return {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} of the {COUNT} matrices (same seed), one OpenMP thread per matrix",
+    return {"value": oracle_flops(ds, A_np.shape[1]) / dt / 1e12, "unit": UNIT, "matrices_per_s": sample / dt,
+            "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} of the {COUNT} 256x256 matrices (same seed), one OpenMP thread per matrix",
             "seconds": dt}, Ls, ds
 
 
@@ -137,17 +158,21 @@ def run_reference(args, rank, world):
     cores = cb["cores"]
     for _ in range(args.warmup):
         oracle.logm_batch([A[0]], nthreads=cores)
-    times = []
+    times, flops = [], 0.0
     for s in range(args.steps):
         t0 = time.perf_counter()
-        oracle.logm_batch([A[(s * sample + i) % COUNT] for i in range(sample)], nthreads=cores)
+        _, ds_s = oracle.logm_batch([A[(s * sample + i) % COUNT] for i in range(sample)], nthreads=cores)
         times.append(time.perf_counter() - t0)
-    value = sample * len(times) / sum(times)
+        flops += oracle_flops(ds_s, N)
+    value = flops / sum(times) / 1e12
     cb["value"] = value
+    cb["matrices_per_s"] = sample * len(times) / sum(times)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD + f"; oracle on {sample} matrices per step"},
+           "data": "synthetic", "matrices_per_s": cb["matrices_per_s"],
+           "config": {"workload": WORKLOAD + f"; oracle on a bounded sample: {sample} of the 256x256 matrices per "
+                      "step (the 4096 matrix would take the oracle hours)"},
            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -155,13 +180,15 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-sample", type=int, default=COUNT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--count", type=int, default=COUNT, help="matrices per rank (smaller for profiling)")
+    ap.add_argument("--no-big", action="store_true", help="leave out the 4096 x 4096 matrix")
+    ap.add_argument("--big-n", type=int, default=NBIG, help="size of the large matrix (smaller for profiling)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -186,6 +213,12 @@ def main():
     A_np = workloads.identity_plus(count, N, seed=1 + rank)
     A_host = torch.from_numpy(A_np).pin_memory()
     A_dev = A_host.to(dev)
+    big = not args.no_big
+    if big:
+        nbig = args.big_n
+        B_host = torch.from_numpy(workloads.triangular_similar(nbig, seed=2 + rank)[None]).pin_memory()
+        B_dev = B_host.to(dev)
+        stats_b = torch.zeros(4, dtype=torch.int32, device=dev)
     stats = torch.zeros(4 * count, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -194,77 +227,111 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    def step():
+        out = lg.logm_execute(A_dev, stats=stats)
+        outb = lg.logm_execute(B_dev, stats=stats_b) if big else None
+        return out, outb
+
     for _ in range(args.warmup):
-        lg.logm_execute(A_dev, stats=stats)
+        step()
     barrier()
 
-    # device-timed region: inputs resident in HBM (268 MB > 129 MB L2)
+    # device-timed region: inputs resident in HBM (268 MB + 134 MB > 129 MB L2)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         barrier()
         e0.record(stream)
-        for _ in range(args.steps):
+        for i in range(args.steps):
+            ev[3 * i].record(stream)
             L, s, k, info = lg.logm_execute(A_dev, stats=stats)
+            ev[3 * i + 1].record(stream)
+            if big:
+                Lb, sb, kb, infob = lg.logm_execute(B_dev, stats=stats_b)
+            ev[3 * i + 2].record(stream)
         e1.record(stream)
         barrier()
     ms = e0.elapsed_time(e1) / args.steps
+    ms_a = sum(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(args.steps)) / args.steps
+    ms_b = sum(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(args.steps)) / args.steps
     clocks = clk.summary()
     ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
     ms_max = float(ms_t.item())
 
-    st = stats.cpu().numpy()
-    flops = algorithmic_flops(st, N)
+    flops_a = algorithmic_flops(stats.cpu().numpy(), N)
+    flops_b = algorithmic_flops(stats_b.cpu().numpy(), args.big_n) if big else 0.0
     info_np = info.cpu().numpy()
     s_np, k_np = s.cpu().numpy(), k.cpu().numpy()
+    n_mats = count + (1 if big else 0)
 
     # end to end through the public call with host buffers: H2D + execute + D2H
+    e2e_steps = 0 if args.no_e2e else min(args.steps, 2)
     L_host = torch.empty_like(A_host).pin_memory()
-    for _ in range(0 if args.no_e2e else 1):
+    LB_host = torch.empty_like(B_host).pin_memory() if big else None
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
         Ad = A_host.to(dev, non_blocking=True)
         Lo, _, _, _ = lg.logm_execute(Ad)
         L_host.copy_(Lo, non_blocking=True)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(0 if args.no_e2e else args.steps):
-        Ad = A_host.to(dev, non_blocking=True)
-        Lo, _, _, inf2 = lg.logm_execute(Ad)
-        L_host.copy_(Lo, non_blocking=True)
+        if big:
+            Bd = B_host.to(dev, non_blocking=True)
+            Lbo, _, _, _ = lg.logm_execute(Bd)
+            LB_host.copy_(Lbo, non_blocking=True)
         torch.cuda.synchronize(dev)
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps if not args.no_e2e else float("nan")
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps if e2e_steps else float("nan")
     e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_ms = float(e2e_t.item())
+    h2d = A_host.numel() * 8 + (B_host.numel() * 8 if big else 0)
 
     if rank == 0:
-        peak, peak_note = fp64_peak_tflops()
-        achieved = flops / (ms * 1e-3) / 1e12
+        # dominant kernel: the whole-GPU 4096 kernel (seconds long -> sustained peak)
+        if big:
+            peak, peak_note = fp64_peak_tflops(sustained=True)
+            ach = flops_b / (ms_b * 1e-3) / 1e12
+            kname, fpl = "k_logm_large<execute> (cooperative, whole GPU on the 4096 matrix)", flops_b
+        else:
+            peak, peak_note = fp64_peak_tflops()
+            ach = flops_a / (ms_a * 1e-3) / 1e12
+            kname, fpl = "k_logm_small<execute> (persistent, one block per matrix)", flops_a
+        pk_a, note_a = fp64_peak_tflops()
+        parts = {"batch256": {"ms": ms_a, "matrices_per_s": count / (ms_a * 1e-3),
+                              "tflops": flops_a / (ms_a * 1e-3) / 1e12,
+                              "frac": flops_a / (ms_a * 1e-3) / 1e12 / pk_a, "peak_note": "FP64 " + note_a,
+                              "s_hist": np.bincount(s_np).tolist(), "k_hist": np.bincount(k_np, minlength=6).tolist(),
+                              "info_nonzero": int((info_np != 0).sum())}}
+        if big:
+            parts["n4096"] = {"ms": ms_b, "tflops": ach, "frac": ach / peak, "s": int(sb[0]), "k": int(kb[0]),
+                              "info": int(infob[0]), "work": stats_b.cpu().numpy().tolist()}
         out = {
-            "metric": METRIC, "value": count * world / (ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": (flops_a + flops_b) * world / (ms_max * 1e-3) / 1e12, "unit": UNIT,
+            "matrices_per_s": n_mats * world / (ms_max * 1e-3), "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if count == COUNT else WORKLOAD.replace(str(COUNT), str(count), 1),
-                       "count": count, "n": N, "precision": "fp64",
-                       "l2": f"inputs ({count * N * N * 8 / 1e6:.0f} MB) vs 129 MB L2; no flush", "parallelism": f"batch-sharded x{world}"},
-            "tflops": achieved * world * ms / ms_max,
-            "plan": {"s_hist": np.bincount(s_np).tolist(), "k_hist": np.bincount(k_np, minlength=6).tolist(),
-                     "info_nonzero": int((info_np != 0).sum())},
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "peak_note": "FP64 dense " + peak_note,
-                         "kernel": "k_logm_small<execute> (persistent, one block per matrix)",
-                         "flops_per_launch": flops},
-            "e2e": {"value": count * world / (e2e_ms * 1e-3) if not args.no_e2e else None, "unit": UNIT,
-                    "h2d_bytes_per_step": int(A_host.numel() * 8), "d2h_bytes_per_step": int(A_host.numel() * 8)},
-            "gpu_launches": 4 * args.steps,  # per step: 3 queue-order kernels + the persistent logm kernel
+            "config": {"workload": WORKLOAD if (count == COUNT and big and args.big_n == NBIG) else
+                       f"{count} x 256x256 A = I + E" + (f" + one {args.big_n}^2 Q T Q^T" if big else "") + ", FP64 path",
+                       "count": count, "n": N, "n_big": args.big_n if big else None, "precision": "fp64",
+                       "l2": "inputs larger than the 129 MB L2; no flush", "parallelism": f"batch-sharded x{world}"},
+            "parts": parts,
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "traffic": None, "peak_note": "FP64 dense " + peak_note,
+                         "kernel": kname, "flops_per_launch": fpl},
+            "e2e": {"value": (flops_a + flops_b) * world / (e2e_ms * 1e-3) / 1e12 if e2e_steps else None,
+                    "unit": UNIT, "matrices_per_s": n_mats * world / (e2e_ms * 1e-3) if e2e_steps else None,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)},
+            "gpu_launches": (4 + (1 if big else 0)) * args.steps,  # 3 queue-order kernels + persistent + cooperative
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:
-            cb, Ls, ds = cpu_baseline(A_np, args.ref_sample)
+            cb, Ls, ds = cpu_baseline(A_np, min(args.ref_sample, count))
             Lg = L.cpu().numpy()
             errs = [np.linalg.norm(Lg[i] - Ls[i]) / np.linalg.norm(Ls[i]) for i in range(len(Ls))
                     if (ds[i]["s"], ds[i]["k"]) == (int(s_np[i]), int(k_np[i]))]
+            cb["sample"] += "; the 4096 matrix is not in the sample (the oracle would need hours for it)"
             out["cpu_baseline"] = cb
             out["rel_err_vs_oracle"] = {"max": float(max(errs)) if errs else None, "matrices": len(errs)}
         print(json.dumps(out), flush=True)
