@@ -186,6 +186,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=COUNT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the split-precision forms")
     ap.add_argument("--count", type=int, default=COUNT, help="matrices per rank (smaller for profiling)")
     ap.add_argument("--no-big", action="store_true", help="leave out the 4096 x 4096 matrix")
     ap.add_argument("--big-n", type=int, default=NBIG, help="size of the large matrix (smaller for profiling)")
@@ -288,6 +289,40 @@ def main():
     e2e_ms = float(e2e_t.item())
     h2d = A_host.numel() * 8 + (B_host.numel() * 8 if big else 0)
 
+    # precision forms: the same step with the graph products in split precision
+    # on the tensor cores (square roots and plan stay FP64); error vs the FP64 result
+    forms = {}
+    for prec in ([] if args.no_forms else ["tf32x3", "bf16x3"]):
+        lg.logm_execute(A_dev, precision=prec)
+        if big:
+            lg.logm_execute(B_dev, precision=prec)
+        barrier()
+        fa0, fa1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fb1 = torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(args.steps, 2))
+        fa0.record(stream)
+        for _ in range(reps):
+            Lp, sp, kp, ip = lg.logm_execute(A_dev, precision=prec)
+        fa1.record(stream)
+        if big:
+            for _ in range(reps):
+                Lpb, _, _, _ = lg.logm_execute(B_dev, precision=prec)
+        fb1.record(stream)
+        barrier()
+        ms_fa = fa0.elapsed_time(fa1) / reps
+        ms_fb = fa1.elapsed_time(fb1) / reps if big else 0.0
+        errs_a = ((Lp - L).flatten(1).norm(dim=1) / L.flatten(1).norm(dim=1)).cpu().numpy()
+        ent = {"batch256": {"ms": ms_fa, "matrices_per_s": count / (ms_fa * 1e-3),
+                            "tflops": flops_a / (ms_fa * 1e-3) / 1e12, "speedup_vs_fp64": ms_a / ms_fa,
+                            "rel_err_vs_fp64": {"max": float(errs_a.max()), "median": float(np.median(errs_a))}}}
+        if big:
+            eb = float(((Lpb - Lb).norm() / Lb.norm()).item())
+            ent["n4096"] = {"ms": ms_fb, "tflops": flops_b / (ms_fb * 1e-3) / 1e12, "speedup_vs_fp64": ms_b / ms_fb,
+                            "rel_err_vs_fp64": eb}
+            ent["step"] = {"ms": ms_fa + ms_fb, "tflops": (flops_a + flops_b) / ((ms_fa + ms_fb) * 1e-3) / 1e12,
+                           "speedup_vs_fp64": ms / (ms_fa + ms_fb)}
+        forms[prec] = ent
+
     if rank == 0:
         # dominant kernel: the whole-GPU 4096 kernel (seconds long -> sustained peak)
         if big:
@@ -317,6 +352,7 @@ def main():
                        "count": count, "n": N, "n_big": args.big_n if big else None, "precision": "fp64",
                        "l2": "inputs larger than the 129 MB L2; no flush", "parallelism": f"batch-sharded x{world}"},
             "parts": parts,
+            "forms": forms,
             "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach / peak, "traffic": None, "peak_note": "FP64 dense " + peak_note,
                          "kernel": kname, "flops_per_launch": fpl},

@@ -174,7 +174,7 @@ def logm_graph_eval(X, k, P3=None, precision="fp64"):
         k = torch.full((b.count,), int(k), dtype=torch.int32, device=dev)
     Z = torch.empty_like(v)
     prec = _PREC[precision] if isinstance(precision, str) else int(precision)
-    o = _options()
+    o = _options(precision=prec)
     w, nb = _workspace(X, b, o, L)
     rc = L.logm_graph_eval(ctypes.byref(b), prec, _ptr(v), _ptr(None if P3 is None else _values(P3)),
                            _ptr(k), _ptr(Z), _ptr(w), nb, _stream(dev))

@@ -533,7 +533,19 @@ static __device__ void run_execute(Ops& ops, const SmallParams& p, int b, int n,
     }
     if (finish) k = order_search(ops, M.Acur, M.A2, n, nB, nI2, km, p.theta, last.t_m >= 0.0 ? &last : nullptr);
     to_x(ops, M.Acur, n);  // P_2 = X = -(A - I)
-    graph_eval(ops, k, n, M, -ldexp(1.0, s), out_view(p.L, p.dtype, off));
+    if (p.gbuf) {
+      // precision form: P_2 and P_3 go to the tensor-core graph stage in FP32
+      float* g = p.gbuf + (int64_t)b * 5 * (int64_t)p.gbuf_nmax * p.gbuf_nmax;
+      float* g3 = g + (int64_t)p.gbuf_nmax * p.gbuf_nmax;
+      const int64_t nn = (int64_t)n * n;
+      for (int64_t t = ops.tid(); t < nn; t += ops.nthreads()) {
+        g[t] = static_cast<float>(M.Acur[t]);
+        g3[t] = static_cast<float>(M.A2[t]);
+      }
+      ops.sync();
+    } else {
+      graph_eval(ops, k, n, M, -ldexp(1.0, s), out_view(p.L, p.dtype, off));
+    }
   }
   if (ops.leader()) {
     p.info[b] = info;

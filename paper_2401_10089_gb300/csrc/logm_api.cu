@@ -37,10 +37,19 @@ int opts_ok(const logm_options* o) {
 struct WsLayout {
   int small_nmax;   // 0: no small pass
   int large_nmax;   // 0: no large pass
-  size_t small_bytes, large_off, total;
+  size_t small_bytes, large_off, graph_off, total;
 };
 
-WsLayout ws_layout(const logm_batch* b) {
+size_t round256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Tensor-core graph stage region: FP32 slots P_2 .. P_6 per matrix, then k, s
+// (when the caller passes none) and an error word.
+size_t graph_region_bytes(const logm_batch* b, int n_max) {
+  return round256(sizeof(float) * 5 * (size_t)b->count * n_max * n_max) +
+         2 * round256(sizeof(int32_t) * (size_t)b->count) + 256;
+}
+
+WsLayout ws_layout(const logm_batch* b, int precision) {
   WsLayout L{};
   const int n_max = batch_n_max(b);
   if (n_max <= 0) return L;
@@ -52,9 +61,31 @@ WsLayout ws_layout(const logm_batch* b) {
     if (ragged) L.small_nmax = lg::kSmallMaxN;
   }
   L.small_bytes = L.small_nmax ? lg::small_workspace_bytes(b->count, L.small_nmax) : 0;
-  L.large_off = (L.small_bytes + 255) / 256 * 256;
-  L.total = L.large_off + (L.large_nmax ? lg::large_workspace_bytes(L.large_nmax) : 0);
+  L.large_off = round256(L.small_bytes);
+  L.graph_off = round256(L.large_off + (L.large_nmax ? lg::large_workspace_bytes(L.large_nmax) : 0));
+  L.total = L.graph_off + (precision != LOGM_PREC_FP64 ? graph_region_bytes(b, n_max) : 0);
   return L;
+}
+
+struct GraphRegion {
+  float* gbuf;
+  int32_t* k;
+  int32_t* s;
+  int32_t* err;
+};
+
+GraphRegion graph_region(const logm_batch* b, const WsLayout& L, void* ws) {
+  char* w = static_cast<char*>(ws) + L.graph_off;
+  const int n_max = batch_n_max(b);
+  GraphRegion g;
+  g.gbuf = reinterpret_cast<float*>(w);
+  w += round256(sizeof(float) * 5 * (size_t)b->count * n_max * n_max);
+  g.k = reinterpret_cast<int32_t*>(w);
+  w += round256(sizeof(int32_t) * (size_t)b->count);
+  g.s = reinterpret_cast<int32_t*>(w);
+  w += round256(sizeof(int32_t) * (size_t)b->count);
+  g.err = reinterpret_cast<int32_t*>(w);
+  return g;
 }
 
 void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o) {
@@ -82,7 +113,7 @@ void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o)
 
 // Launch the small pass and/or the large pass for this batch.
 int run_passes(lg::Mode mode, lg::SmallParams& p, const logm_batch* b, void* ws, cudaStream_t st) {
-  const WsLayout L = ws_layout(b);
+  const WsLayout L = ws_layout(b, LOGM_PREC_FP64);
   char* w = static_cast<char*>(ws);
   if (L.small_nmax) {
     lg::SmallParams q = p;
@@ -105,10 +136,10 @@ int run_passes(lg::Mode mode, lg::SmallParams& p, const logm_batch* b, void* ws,
   return LOGM_SUCCESS;
 }
 
-int check_ws(const logm_batch* b, void* ws, size_t ws_bytes) {
+int check_ws(const logm_batch* b, void* ws, size_t ws_bytes, int precision = LOGM_PREC_FP64) {
   if (!ws) return LOGM_ERR_WORKSPACE;
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return LOGM_ERR_WORKSPACE;
-  if (ws_bytes < ws_layout(b).total) return LOGM_ERR_WORKSPACE;
+  if (ws_bytes < ws_layout(b, precision).total) return LOGM_ERR_WORKSPACE;
   return LOGM_SUCCESS;
 }
 
@@ -119,9 +150,8 @@ extern "C" {
 int logm_version(void) { return 100; }
 
 size_t logm_workspace_size(const logm_batch* batch, const logm_options* opts) {
-  (void)opts;
   if (batch_n_max(batch) <= 0) return 0;
-  return ws_layout(batch).total;
+  return ws_layout(batch, opts ? opts->precision : LOGM_PREC_TF32X3).total;
 }
 
 size_t logm_context_size(const logm_batch* batch, const logm_options* opts) {
@@ -176,8 +206,30 @@ int logm_graph_eval(const logm_batch* batch, int32_t precision, const void* X, c
   if (precision < LOGM_PREC_FP64 || precision > LOGM_PREC_BF16X3) return LOGM_ERR_INVALID_ARG;
   if (batch->count == 0) return LOGM_SUCCESS;
   if (!X || !k_dev || !Z) return LOGM_ERR_INVALID_ARG;
-  if (precision != LOGM_PREC_FP64) return LOGM_ERR_UNSUPPORTED;
-  if (int r = check_ws(batch, ws, ws_bytes)) return r;
+  if (int r = check_ws(batch, ws, ws_bytes, precision)) return r;
+  if (precision != LOGM_PREC_FP64) {
+    const WsLayout L = ws_layout(batch, precision);
+    const GraphRegion g = graph_region(batch, L, ws);
+    lg::GraphParams gp{};
+    gp.count = batch->count;
+    gp.n_uniform = batch->n_uniform > 0 ? batch->n_uniform : 0;
+    gp.n_max = n_max;
+    gp.n_dev = batch->n;
+    gp.off_dev = batch->offset;
+    gp.k_dev = k_dev;
+    gp.s_dev = nullptr;
+    gp.info_dev = nullptr;
+    gp.gbuf = g.gbuf;
+    gp.L = Z;
+    gp.out_dtype = batch->dtype;
+    gp.precision = precision;
+    gp.p3_given = P3 ? 1 : 0;
+    gp.err = g.err;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(g.err, 0, sizeof(int32_t), st) != cudaSuccess) return LOGM_ERR_CUDA;
+    if (lg::launch_graph_prep(gp, X, P3, batch->dtype, st) != cudaSuccess) return LOGM_ERR_CUDA;
+    return lg::launch_graph_tc(gp, st) == cudaSuccess ? LOGM_SUCCESS : LOGM_ERR_CUDA;
+  }
   lg::SmallParams p;
   fill_common(p, batch, nullptr);
   p.X = X;
@@ -195,8 +247,7 @@ int logm_execute(const logm_batch* batch, const logm_options* opts, const void* 
   if (n_max <= 0 || !opts_ok(opts)) return LOGM_ERR_INVALID_ARG;
   if (batch->count == 0) return LOGM_SUCCESS;
   if (!A || !L || !info_dev) return LOGM_ERR_INVALID_ARG;
-  if (opts->precision != LOGM_PREC_FP64) return LOGM_ERR_UNSUPPORTED;
-  if (int r = check_ws(batch, ws, ws_bytes)) return r;
+  if (int r = check_ws(batch, ws, ws_bytes, opts->precision)) return r;
   lg::SmallParams p;
   fill_common(p, batch, opts);
   p.A = A;
@@ -207,7 +258,33 @@ int logm_execute(const logm_batch* batch, const logm_options* opts, const void* 
   p.stats = stats_dev;
   p.ctx = static_cast<double*>(ctx);
   p.ctx_levels = lg::kCtxLevels;
-  return run_passes(lg::kModeExecute, p, batch, ws, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (opts->precision == LOGM_PREC_FP64) return run_passes(lg::kModeExecute, p, batch, ws, st);
+  // precision form: FP64 plan and square roots, then the graph products on the tensor cores
+  const WsLayout L2 = ws_layout(batch, opts->precision);
+  const GraphRegion g = graph_region(batch, L2, ws);
+  p.gbuf = g.gbuf;
+  p.gbuf_nmax = n_max;
+  if (!p.k_out) p.k_out = g.k;
+  if (!p.s_out) p.s_out = g.s;
+  if (int r = run_passes(lg::kModeExecute, p, batch, ws, st)) return r;
+  lg::GraphParams gp{};
+  gp.count = batch->count;
+  gp.n_uniform = batch->n_uniform > 0 ? batch->n_uniform : 0;
+  gp.n_max = n_max;
+  gp.n_dev = batch->n;
+  gp.off_dev = batch->offset;
+  gp.k_dev = p.k_out;
+  gp.s_dev = p.s_out;
+  gp.info_dev = info_dev;
+  gp.gbuf = g.gbuf;
+  gp.L = L;
+  gp.out_dtype = batch->dtype;
+  gp.precision = opts->precision;
+  gp.p3_given = 1;
+  gp.err = g.err;
+  if (cudaMemsetAsync(g.err, 0, sizeof(int32_t), st) != cudaSuccess) return LOGM_ERR_CUDA;
+  return lg::launch_graph_tc(gp, st) == cudaSuccess ? LOGM_SUCCESS : LOGM_ERR_CUDA;
 }
 
 int logm_backward(const logm_batch* batch, const logm_options* opts, const void* A, const void* ctx,

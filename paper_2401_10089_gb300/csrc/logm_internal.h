@@ -49,7 +49,30 @@ struct SmallParams {
   int n_slots;
   int precision;       // graph products (FP64 in this kernel family)
   int large_pass;      // 1: matrices with n > kSmallMaxN are left to the whole-GPU kernel
+  float* gbuf;         // precision form: hand P_2, P_3 over in FP32 here and stop before the graph
+  int gbuf_nmax;       // n stride of gbuf
 };
+
+// Parameters of the tensor-core graph stage (graph_tc.cu).
+struct GraphParams {
+  int count, n_uniform, n_max;
+  const int32_t* n_dev;
+  const int64_t* off_dev;
+  const int32_t* k_dev;     // products per matrix (1, 2, 5)
+  const int32_t* s_dev;     // square roots per matrix (scale -2^s), NULL: scale 1
+  const int32_t* info_dev;  // matrices with info 1 or 4 are skipped; may be NULL
+  float* gbuf;              // per matrix 5 slots of n_max^2 floats: P_2 .. P_6
+  void* L;                  // output (dtype out_dtype) at the batch's offsets
+  int out_dtype;
+  int precision;            // LOGM_PREC_TF32X3 or LOGM_PREC_BF16X3
+  int j;                    // product of this launch (1: P_3 = X X, 2..5)
+  int p3_given;             // 1: slot 1 already holds P_3
+  int32_t* err;             // set when a tensor-core wait timed out
+};
+
+size_t graph_tc_smem_bytes();
+cudaError_t launch_graph_tc(const GraphParams& p, cudaStream_t st);
+cudaError_t launch_graph_prep(const GraphParams& p, const void* X, const void* P3, int in_dtype, cudaStream_t st);
 
 constexpr int kSlotMats = 7;
 constexpr int kOrderBuckets = 256;

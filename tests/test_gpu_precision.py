@@ -1,0 +1,47 @@
+"""Precision form: the graph products on the tensor cores (tcgen05) in split
+TF32x3 / BF16x3 with FP32 accumulation, square roots and plan in FP64.
+
+Tolerances: the products see FP32 operands (24-bit), split into slices whose
+cross terms reach about 2^-22 (TF32x3) or 2^-24 (BF16x3) relative, accumulated
+in FP32 over n terms; the lin-combs run in FP32. Per product that is a few
+times 1e-7 relative, so z(X) and L = -2^s z(X) carry about 1e-6 relative error.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_10089_gb300 import workloads
+from tests.test_gpu_parity import dev, lg, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PREC_TOL = {"tf32x3": 5e-6, "bf16x3": 5e-6}
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+@pytest.mark.parametrize("k", [1, 2, 5])
+@pytest.mark.parametrize("n", [8, 64, 100, 256, 300])
+def test_graph_eval_split_precision(precision, k, n):
+    rng = np.random.default_rng(70 + n + k)
+    X = rng.standard_normal((3, n, n))
+    X *= 0.2 / np.abs(X).sum(axis=1).max(axis=1)[:, None, None]
+    Z = lg().logm_graph_eval(dev(X), k, precision=precision).cpu().numpy()
+    Zp = lg().logm_graph_eval(dev(X), k, P3=dev(X @ X), precision=precision).cpu().numpy()
+    for b in range(3):
+        Zr = oracle.graph_eval(X[b], k)
+        assert rel(Z[b], Zr) <= PREC_TOL[precision], rel(Z[b], Zr)
+        assert rel(Zp[b], Zr) <= PREC_TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+def test_execute_split_precision(precision):
+    A = workloads.identity_plus(16, 128, seed=71)
+    L, s, k, info = lg().logm_execute(dev(A), precision=precision)
+    L64, s64, k64, info64 = lg().logm_execute(dev(A))
+    assert torch.equal(s.cpu(), s64.cpu()) and torch.equal(k.cpu(), k64.cpu())
+    L = L.cpu().numpy()
+    for b in range(16):
+        Lr, d = oracle.logm(A[b])
+        assert int(info[b]) == 0
+        assert rel(L[b], Lr) <= PREC_TOL[precision], rel(L[b], Lr)
