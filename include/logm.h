@@ -53,6 +53,7 @@ extern "C" {
 #define LOGM_INFO_MAX_SQRT 3       /* square-root count hit max_sqrt (maxiter of Algorithm 1) */
 #define LOGM_INFO_NONFINITE 4      /* NaN or Inf in the input */
 #define LOGM_INFO_TIMEOUT 5        /* a grid barrier of the whole-GPU (large n) kernel timed out; result invalid */
+#define LOGM_INFO_BACKWARD_LIMIT 6 /* logm_backward: the forward's levels or iterations exceed what it records */
 
 /* Storage type of A, L, X, Z (arithmetic is FP64 except where `precision` says). */
 #define LOGM_DTYPE_F64 0
@@ -146,12 +147,24 @@ int logm_execute(const logm_batch* batch, const logm_options* opts, const void* 
                  int32_t* s_dev, int32_t* k_dev, int32_t* info_dev, int32_t* stats_dev, void* ctx,
                  void* ws, size_t ws_bytes, void* stream);
 
+/* Bytes of device workspace logm_backward needs (one slot per resident block
+ * of 49 n_max^2 doubles: forward recompute, adjoints and the recorded
+ * inverses of up to 16 Denman-Beavers iterations). Returns 0 for an invalid
+ * batch or n_max > 256. */
+size_t logm_backward_workspace_size(const logm_batch* batch, const logm_options* opts);
+
 /* logm_backward -- dA = adjoint of the computed map A -> L at the forward's
  * plan, applied to dL (i.e. the gradient of sum(dL o L) with respect to A):
- * the graph products and the Denman-Beavers iterations of every level are
- * reversed; the iterates of a level are recomputed from its checkpoint in ctx.
- * The plan (s, k) and the scaling mu are held fixed.
- *   A   : the forward's input.  ctx: the forward's context.  dL, dA: device. */
+ * the graph products (Sec. 3, eq. five_mult_degopt) and the Denman-Beavers
+ * iterations (eq. ScalDB) of every level are reversed; the iterates of a level
+ * are recomputed from the level's input, which logm_execute checkpointed in
+ * ctx. The plan (s, k) and the scalings mu_k are held fixed (they do not
+ * change the converged root).
+ *   A   : the forward's input.  ctx: the forward's context (logm_context_size
+ *         bytes, filled by logm_execute).  dL, dA: device, dtype per batch.
+ *   ws  : logm_backward_workspace_size bytes.  n_max <= 256.
+ *   info_dev: 0, 1 (the forward had no result), 6 (a level needed more than 16
+ *         Denman-Beavers iterations or s exceeded the 12 checkpointed levels). */
 int logm_backward(const logm_batch* batch, const logm_options* opts, const void* A,
                   const void* ctx, const void* dL, void* dA, int32_t* info_dev, void* ws,
                   size_t ws_bytes, void* stream);

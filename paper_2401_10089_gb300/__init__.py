@@ -5,8 +5,8 @@ with computation-graph polynomials (Jarlebring, Sastre, Ibanez, arXiv
 The compute path is the CUDA library built from ``csrc/`` (C ABI in
 ``include/logm.h``); this package is its thin Python binding.
 """
-from .api import (Ragged, logm_backward, logm_context_size, logm_execute, logm_graph_eval, logm_plan,
-                  logm_sqrt, logm_version, logm_workspace_size)
+from .api import (LogmFunction, Ragged, logm, logm_backward, logm_backward_workspace_size, logm_context_size,
+                  logm_execute, logm_graph_eval, logm_plan, logm_sqrt, logm_version, logm_workspace_size)
 
-__all__ = ["Ragged", "logm_backward", "logm_context_size", "logm_execute", "logm_graph_eval", "logm_plan",
-           "logm_sqrt", "logm_version", "logm_workspace_size"]
+__all__ = ["LogmFunction", "Ragged", "logm", "logm_backward", "logm_backward_workspace_size", "logm_context_size",
+           "logm_execute", "logm_graph_eval", "logm_plan", "logm_sqrt", "logm_version", "logm_workspace_size"]

@@ -20,8 +20,8 @@ _ERRORS = {ERR_INVALID_ARG: "invalid argument", ERR_UNSUPPORTED: "unsupported", 
            ERR_CUDA: "CUDA launch error"}
 
 # Every symbol include/logm.h declares.
-EXPORTS = ("logm_workspace_size", "logm_context_size", "logm_plan", "logm_sqrt", "logm_graph_eval",
-           "logm_execute", "logm_backward", "logm_execute_noalloc", "logm_version")
+EXPORTS = ("logm_workspace_size", "logm_context_size", "logm_backward_workspace_size", "logm_plan", "logm_sqrt",
+           "logm_graph_eval", "logm_execute", "logm_backward", "logm_execute_noalloc", "logm_version")
 
 
 class LogmBatch(ctypes.Structure):
@@ -64,6 +64,8 @@ def load(build_if_missing: bool = True):
         L.logm_workspace_size.argtypes = [B, O]
         L.logm_context_size.restype = SZ
         L.logm_context_size.argtypes = [B, O]
+        L.logm_backward_workspace_size.restype = SZ
+        L.logm_backward_workspace_size.argtypes = [B, O]
         L.logm_plan.argtypes = [B, O, V, V, V, V, V, V, V, SZ, V]
         L.logm_sqrt.argtypes = [B, O, V, V, V, V, V, V, V, SZ, V]
         L.logm_graph_eval.argtypes = [B, I32, V, V, V, V, V, SZ, V]
@@ -75,6 +77,7 @@ def load(build_if_missing: bool = True):
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         L.logm_workspace_size.restype = SZ
         L.logm_context_size.restype = SZ
+        L.logm_backward_workspace_size.restype = SZ
         _lib = L
         return _lib
 

@@ -208,15 +208,29 @@ def logm_execute(A, with_ctx=False, stats=None, **opts):
     return Lout, s, k, info
 
 
+def logm_backward_workspace_size(A, **opts) -> int:
+    L = _lib.load()
+    b, o = _batch(A), _options(**opts)
+    return int(L.logm_backward_workspace_size(ctypes.byref(b), ctypes.byref(o)))
+
+
+_ws_bwd = _Workspace()
+
+
 def logm_backward(A, ctx, dL, **opts):
-    """dA = gradient of sum(dL * log(A)) with respect to A at the forward's plan."""
+    """dA = gradient of sum(dL * log(A)) with respect to A at the forward's plan.
+
+    ``ctx`` is the context tensor ``logm_execute(A, with_ctx=True)`` returned."""
     L = _lib.load()
     b, o = _batch(A), _options(**opts)
     v = _values(A)
     dev = v.device
     dA = torch.empty_like(v)
     info = _i32(b.count, dev)
-    w, nb = _workspace(A, b, o, L)
+    nb = int(L.logm_backward_workspace_size(ctypes.byref(b), ctypes.byref(o)))
+    if nb == 0:
+        raise _lib.LogmError("logm_backward: unsupported batch (n_max > 256?)")
+    w = _ws_bwd.get(dev, nb)
     rc = L.logm_backward(ctypes.byref(b), ctypes.byref(o), _ptr(v), _ptr(ctx), _ptr(_values(dL)), _ptr(dA),
                          _ptr(info), _ptr(w), nb, _stream(dev))
     _lib.check(rc, "logm_backward")
@@ -225,3 +239,29 @@ def logm_backward(A, ctx, dL, **opts):
 
 def logm_version() -> int:
     return int(_lib.load().logm_version())
+
+
+class LogmFunction(torch.autograd.Function):
+    """L = log(A) with the hand-written adjoint (logm_backward) as its backward."""
+
+    @staticmethod
+    def forward(ctx, A, k_max=5, max_sqrt=40, max_db_iter=50):
+        opts = dict(k_max=k_max, max_sqrt=max_sqrt, max_db_iter=max_db_iter)
+        Ac = A.contiguous()
+        L, s, k, info, cbuf = logm_execute(Ac, with_ctx=True, **opts)
+        ctx.save_for_backward(Ac, cbuf)
+        ctx.opts = opts
+        ctx.mark_non_differentiable(s, k, info)
+        return L, s, k, info
+
+    @staticmethod
+    def backward(ctx, dL, ds, dk, dinfo):
+        A, cbuf = ctx.saved_tensors
+        dA, info = logm_backward(A, cbuf, dL.contiguous(), **ctx.opts)
+        return dA, None, None, None
+
+
+def logm(A, k_max=5, max_sqrt=40, max_db_iter=50):
+    """Differentiable matrix logarithm of a (count, n, n) or (n, n) CUDA tensor."""
+    L, s, k, info = LogmFunction.apply(A, k_max, max_sqrt, max_db_iter)
+    return L

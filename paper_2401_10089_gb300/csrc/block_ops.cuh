@@ -40,8 +40,8 @@ struct BlockOps {
   }
 
   __device__ void gemm(int n, const double* A, double as, const double* B, double bs, double alpha,
-                       const EpiTerms& e, OutView out) {
-    gemm_block(n, A, as, B, bs, alpha, e, out, S.u.gemm);
+                       const EpiTerms& e, OutView out, bool ta = false, bool tb = false) {
+    gemm_block(n, A, as, B, bs, alpha, e, out, S.u.gemm, ta, tb);
   }
 
   __device__ void lincomb(int n, const EpiTerms& e, double* out) { lincomb_block(n, e, out); }

@@ -216,12 +216,13 @@ static __device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double
 }
 
 // One 64 x 64 output tile (rows r0.., cols c0..) of
-// out = alpha * (A - a_shift I)(B - b_shift I) + sum_t c_t E_t, by DMMA with
-// the block's 8 warps (each a 16 x 32 sub-tile). A, B, E, out: n x n, ld n.
-// Columns with colmask_lo <= c < colmask_hi are left unwritten.
+// out = alpha * op(A - a_shift I) op(B - b_shift I) + sum_t c_t E_t, by DMMA
+// with the block's 8 warps (each a 16 x 32 sub-tile); op(M) = M^T when the
+// transpose flag is set. A, B, E, out: n x n, ld n. `out` may be one of the
+// E_t (each element is read before it is written by the same thread).
 static __device__ void gemm_tile(int n, int r0, int c0, const double* __restrict__ A, double a_shift,
                           const double* __restrict__ B, double b_shift, double alpha,
-                          const EpiTerms& epi, OutView out, GemmSmem& sm) {
+                          const EpiTerms& epi, OutView out, GemmSmem& sm, bool ta = false, bool tb = false) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 1, wn = warp & 1;
   const int g = lane >> 2, q = lane & 3;
@@ -237,7 +238,7 @@ static __device__ void gemm_tile(int n, int r0, int c0, const double* __restrict
       const int gr = r0 + rr, gk = k0 + kk;
       double v = 0.0;
       if (gr < n && gk < n) {
-        v = A[(size_t)gr * n + gk];
+        v = ta ? A[(size_t)gk * n + gr] : A[(size_t)gr * n + gk];
         if (gr == gk) v -= a_shift;
       }
       sm.As[rr * kAsStride + kk] = v;
@@ -248,7 +249,7 @@ static __device__ void gemm_tile(int n, int r0, int c0, const double* __restrict
       const int gk = k0 + kk, gc = c0 + cc;
       double v = 0.0;
       if (gk < n && gc < n) {
-        v = B[(size_t)gk * n + gc];
+        v = tb ? B[(size_t)gc * n + gk] : B[(size_t)gk * n + gc];
         if (gk == gc) v -= b_shift;
       }
       sm.Bs[kk * kBsStride + cc] = v;
@@ -287,10 +288,11 @@ static __device__ void gemm_tile(int n, int r0, int c0, const double* __restrict
 
 static __device__ void gemm_block(int n, const double* __restrict__ A, double a_shift,
                            const double* __restrict__ B, double b_shift, double alpha,
-                           const EpiTerms& epi, OutView out, GemmSmem& sm) {
+                           const EpiTerms& epi, OutView out, GemmSmem& sm, bool ta = false, bool tb = false) {
   const int tiles = (n + kTileM - 1) / kTileM;
   for (int tile = 0; tile < tiles * tiles; ++tile)
-    gemm_tile(n, (tile / tiles) * kTileM, (tile % tiles) * kTileN, A, a_shift, B, b_shift, alpha, epi, out, sm);
+    gemm_tile(n, (tile / tiles) * kTileM, (tile % tiles) * kTileN, A, a_shift, B, b_shift, alpha, epi, out, sm,
+              ta, tb);
   __syncthreads();
 }
 

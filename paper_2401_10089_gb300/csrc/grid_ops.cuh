@@ -199,10 +199,10 @@ struct GridOps {
   }
 
   __device__ void gemm(int n, const double* A, double as, const double* B, double bs, double alpha,
-                       const EpiTerms& e, OutView out) {
+                       const EpiTerms& e, OutView out, bool ta = false, bool tb = false) {
     const int tiles = (n + kTileM - 1) / kTileM;
     for (int t = blockIdx.x; t < tiles * tiles; t += gridDim.x)
-      gemm_tile(n, (t / tiles) * kTileM, (t % tiles) * kTileN, A, as, B, bs, alpha, e, out, S.gemm);
+      gemm_tile(n, (t / tiles) * kTileM, (t % tiles) * kTileN, A, as, B, bs, alpha, e, out, S.gemm, ta, tb);
     sync();
   }
 

@@ -370,8 +370,17 @@ static __device__ int order_search(Ops& ops, const double* Acur, const double* A
 // halves; scaling is switched off below 1e-2.
 // Returns 0 (converged), 1 (singular) or 2 (no convergence).
 // ---------------------------------------------------------------------------
+// Optional record of one square root for the adjoint: X_i^{-1}, Y_i^{-1} and
+// mu_i of every iteration i (the inverses are written straight into the tape).
+struct DbTape {
+  double* inv;     // [cap][2][stride]
+  double* mu;      // [cap]
+  int64_t stride;  // n_max^2
+  int cap;
+};
+
 template <class Ops>
-static __device__ int db_sqrt(Ops& ops, Slot& M, int n, int max_db, int* iters_out) {
+static __device__ int db_sqrt(Ops& ops, Slot& M, int n, int max_db, int* iters_out, const DbTape* tape = nullptr) {
   double* X = M.Acur;
   double* Y = M.Y;
   identity_matrix(ops, Y, n);
@@ -382,24 +391,28 @@ static __device__ int db_sqrt(Ops& ops, Slot& M, int n, int max_db, int* iters_o
     double ldx, ldy;
     ops.tally(0, 1);
     ops.tally(1, (it == 1) ? 1 : 2);
-    if (ops.inverse(X, M.W1, n, &ldx)) { status = 1; break; }
+    const bool taped = tape && it - 1 < tape->cap;
+    double* Xi = taped ? tape->inv + (int64_t)(2 * (it - 1)) * tape->stride : M.W1;
+    double* Yi = taped ? tape->inv + (int64_t)(2 * (it - 1) + 1) * tape->stride : M.W2;
+    if (ops.inverse(X, Xi, n, &ldx)) { status = 1; break; }
     if (it == 1) {
       // Y_0 = I: its inverse is I and log|det Y_0| = 0 exactly.
-      identity_matrix(ops, M.W2, n);
+      identity_matrix(ops, Yi, n);
       ldy = 0.0;
     } else {
-      if (ops.inverse(Y, M.W2, n, &ldy)) { status = 1; break; }
+      if (ops.inverse(Y, Yi, n, &ldy)) { status = 1; break; }
     }
     const double mu = ops.bcast0(scale ? exp(-(ldx + ldy) / (2.0 * n)) : 1.0);
     const double imu = ops.bcast0(1.0 / mu);
+    if (taped && ops.leader()) tape->mu[it - 1] = mu;
     double sd = 0.0, sx = 0.0;
     for (int j = ops.tid(); j < n; j += ops.nthreads()) {
       double cd = 0.0, cx = 0.0;
       for (int i = 0; i < n; ++i) {
         const int64_t t = (int64_t)i * n + j;
         const double xo = X[t];
-        const double xn = 0.5 * fma(mu, xo, M.W2[t] * imu);
-        Y[t] = 0.5 * fma(mu, Y[t], M.W1[t] * imu);
+        const double xn = 0.5 * fma(mu, xo, Yi[t] * imu);
+        Y[t] = 0.5 * fma(mu, Y[t], Xi[t] * imu);
         X[t] = xn;
         cd += fabs(xn - xo);
         cx += fabs(xn);
@@ -551,6 +564,10 @@ static __device__ void run_execute(Ops& ops, const SmallParams& p, int b, int n,
     p.info[b] = info;
     if (p.s_out) p.s_out[b] = s;
     if (p.k_out) p.k_out[b] = k;
+    if (p.ctx_hdr) {
+      p.ctx_hdr[2 * b] = s;
+      p.ctx_hdr[2 * b + 1] = (info == 0 || info == 2 || info == 3) ? k : -1;
+    }
     if (p.alpha) p.alpha[b] = alpha;
     if (p.stats)
       for (int t = 0; t < 4; ++t) p.stats[4 * b + t] = ops.tally_get(t);
@@ -642,6 +659,176 @@ static __device__ void run_graph(Ops& ops, const SmallParams& p, int b, int n, i
   }
   graph_eval(ops, k, n, M, 1.0, out_view(p.L, p.dtype, off));
   if (ops.leader() && p.info) p.info[b] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint (differentiation form): dA = gradient of sum(dL o L) for the map
+// A -> L that the forward computed, at the forward's plan (s, k). Reverse
+// mode through the graph products (P = L_j R_j gives Lbar = Pbar R_j^T and
+// Rbar = L_j^T Pbar, scattered to the P_i by h_{j,i} and g_{j,i}), through
+// A_I2 = A_2 - 2A + I, X = I - A, and through every Denman-Beavers iteration
+// (Xbar_i = mu/2 Xbar_{i+1} - 1/(2 mu) X_i^{-T} Ybar_{i+1} X_i^{-T}, and the
+// same with X, Y exchanged) with mu_i held fixed: its derivative does not
+// change the converged root. A level's iterates are recomputed from the
+// level's input, which the forward checkpointed.
+// ---------------------------------------------------------------------------
+struct BwdSlot {
+  Slot F;          // forward recompute: Acur/P_2, A2/P_3, Y/P_4, W1/P_5, W2/P_6, T1, T2
+  double* Pb[6];   // adjoints of P_2 .. P_7
+  double *Lb, *Rb, *Ab, *Yb;
+  DbTape tape;
+};
+
+// Factor coefficients h_{j,i}, g_{j,i} of P_i (i = 2..j+1) in product j >= 2.
+static __device__ __forceinline__ void scheme64(int k, int j, int i, double* h, double* g) {
+  *h = 0.0;
+  *g = 0.0;
+  if (k == 2) {
+    if (j == 2) {
+      *h = (i == 3) ? 1.0 : 0.0;
+      *g = (i == 2) ? 1.0 / 3.0 : (i == 3 ? 0.25 : 0.0);
+    }
+    return;
+  }
+  int t = 0;
+  for (int jj = 2; jj < j; ++jj) t += jj;
+  *h = c_h5[t + i - 2];
+  *g = c_g5[t + i - 2];
+}
+
+static __device__ __forceinline__ double y64(int k, int i) {  // y_i, i = 2..k+2
+  if (k == 1) return i == 2 ? 1.0 : 0.5;
+  if (k == 2) return i == 2 ? 1.0 : (i == 3 ? 0.5 : 1.0);
+  return c_y5[i - 1];
+}
+
+template <class Ops>
+static __device__ void factor_terms(int k, int j, double* const* P, EpiTerms& hl, EpiTerms& gl) {
+  hl.count = gl.count = j;
+  for (int i = 2; i <= j + 1; ++i) {
+    double h, g;
+    scheme64(k, j, i, &h, &g);
+    hl.M[i - 2] = gl.M[i - 2] = P[i];
+    hl.c[i - 2] = h;
+    gl.c[i - 2] = g;
+  }
+}
+
+template <class Ops>
+static __device__ void run_backward(Ops& ops, const SmallParams& p, int b, int n, int64_t off, BwdSlot& W) {
+  const int s = p.ctx_hdr[2 * b], k = p.ctx_hdr[2 * b + 1];
+  const int64_t nn = (int64_t)n * n;
+  if (k != 1 && k != 2 && k != 5) {  // the forward produced no result
+    fill_nan(ops, p.dA, p.dtype, off, n);
+    if (ops.leader()) p.info[b] = 1;
+    return;
+  }
+  if (s > p.ctx_levels) {  // the forward could not checkpoint every level
+    fill_nan(ops, p.dA, p.dtype, off, n);
+    if (ops.leader()) p.info[b] = 6;
+    return;
+  }
+  const int64_t lstride = (int64_t)p.ctx_nmax * p.ctx_nmax;
+  Slot& F = W.F;
+  int it = 0, status = 0;
+  // 1. recompute the last level (its tape serves the first reversal) and P_3
+  if (s >= 1) {
+    copy_matrix(ops, F.Acur, p.ctx + ((int64_t)b * p.ctx_levels + (s - 1)) * lstride, n);
+    copy_matrix(ops, F.A2, F.Acur, n);
+    if (db_sqrt(ops, F, n, p.max_db, &it, &W.tape) == 1) status = 1;
+    ai2_from(ops, F, n);
+  } else {
+    load_matrix(ops, p.A, p.dtype, off, n, F.Acur);
+    EpiTerms none;
+    none.count = 0;
+    ops.gemm(n, F.Acur, 1.0, F.Acur, 1.0, 1.0, none, OutView{F.A2, 0});
+  }
+  to_x(ops, F.Acur, n);
+  double* P[7] = {nullptr, nullptr, F.Acur, F.A2, F.Y, F.W1, F.W2};
+  // 2. recompute the products that later products use as factors
+  const int last_j = (k == 5) ? 5 : (k == 2 ? 2 : 1);
+  for (int j = 2; j < last_j; ++j) {
+    EpiTerms hl, gl;
+    factor_terms<Ops>(k, j, P, hl, gl);
+    ops.lincomb(n, hl, F.T1);
+    ops.lincomb(n, gl, F.T2);
+    EpiTerms none;
+    none.count = 0;
+    ops.gemm(n, F.T1, 0.0, F.T2, 0.0, 1.0, none, OutView{P[j + 2], 0});
+  }
+  // 3. zbar = -2^s dL; Pbar_i = y_i zbar
+  load_matrix(ops, p.dL, p.dtype, off, n, W.Lb);
+  const double sc = -ldexp(1.0, s);
+  for (int i = 2; i <= k + 2; ++i) {
+    EpiTerms e{{W.Lb}, {sc * y64(k, i)}, 1};
+    ops.lincomb(n, e, W.Pb[i - 2]);
+  }
+  // 4. reverse the products, last first
+  for (int j = last_j; j >= 2; --j) {
+    EpiTerms hl, gl;
+    factor_terms<Ops>(k, j, P, hl, gl);
+    ops.lincomb(n, hl, F.T1);  // L_j
+    ops.lincomb(n, gl, F.T2);  // R_j
+    EpiTerms none;
+    none.count = 0;
+    ops.gemm(n, W.Pb[j], 0.0, F.T2, 0.0, 1.0, none, OutView{W.Lb, 0}, false, true);  // Lbar = Pbar R^T
+    ops.gemm(n, F.T1, 0.0, W.Pb[j], 0.0, 1.0, none, OutView{W.Rb, 0}, true, false);  // Rbar = L^T Pbar
+    for (int i = 2; i <= j + 1; ++i) {
+      EpiTerms u{{W.Pb[i - 2], W.Lb, W.Rb}, {1.0, hl.c[i - 2], gl.c[i - 2]}, 3};
+      ops.lincomb(n, u, W.Pb[i - 2]);
+    }
+  }
+  // 5. P_3: X X when s = 0, else A_2 - 2A + I
+  double* Xb = W.Pb[0];
+  if (s == 0) {
+    EpiTerms acc{{Xb}, {1.0}, 1};
+    ops.gemm(n, W.Pb[1], 0.0, F.Acur, 0.0, 1.0, acc, OutView{Xb, 0}, false, true);  // += P3bar X^T
+    ops.gemm(n, F.Acur, 0.0, W.Pb[1], 0.0, 1.0, acc, OutView{Xb, 0}, true, false);  // += X^T P3bar
+  }
+  {  // Abar_s = -Xbar (- 2 P3bar when P_3 = A_I2)
+    EpiTerms e{{Xb, W.Pb[1]}, {-1.0, s >= 1 ? -2.0 : 0.0}, 2};
+    ops.lincomb(n, e, W.Ab);
+  }
+  // 6. reverse the square-root levels, last first
+  for (int lev = s - 1; lev >= 0 && !status; --lev) {
+    if (lev < s - 1) {
+      copy_matrix(ops, F.Acur, p.ctx + ((int64_t)b * p.ctx_levels + lev) * lstride, n);
+      if (db_sqrt(ops, F, n, p.max_db, &it, &W.tape) == 1) status = 1;
+    }
+    if (status) break;
+    if (it > W.tape.cap) {
+      status = 2;
+      break;
+    }
+    for (int64_t t = ops.tid(); t < nn; t += ops.nthreads()) W.Yb[t] = 0.0;
+    ops.sync();
+    for (int i = it - 1; i >= 0; --i) {
+      const double* Xi = W.tape.inv + (int64_t)(2 * i) * W.tape.stride;
+      const double* Yi = W.tape.inv + (int64_t)(2 * i + 1) * W.tape.stride;
+      const double mu = W.tape.mu[i];
+      EpiTerms none;
+      none.count = 0;
+      ops.gemm(n, Xi, 0.0, W.Yb, 0.0, 1.0, none, OutView{W.Lb, 0}, true, false);  // X_i^{-T} Ybar
+      if (i > 0) ops.gemm(n, Yi, 0.0, W.Ab, 0.0, 1.0, none, OutView{W.Rb, 0}, true, false);  // Y_i^{-T} Xbar
+      EpiTerms ex{{W.Ab}, {0.5 * mu}, 1};
+      ops.gemm(n, W.Lb, 0.0, Xi, 0.0, -0.5 / mu, ex, OutView{W.Ab, 0}, false, true);
+      if (i > 0) {
+        EpiTerms ey{{W.Yb}, {0.5 * mu}, 1};
+        ops.gemm(n, W.Rb, 0.0, Yi, 0.0, -0.5 / mu, ey, OutView{W.Yb, 0}, false, true);
+      }
+    }
+    if (lev == s - 1) {  // the A_2 term of A_I2 = A_2 - 2A + I
+      EpiTerms e{{W.Ab, W.Pb[1]}, {1.0, 1.0}, 2};
+      ops.lincomb(n, e, W.Ab);
+    }
+  }
+  if (status) {
+    fill_nan(ops, p.dA, p.dtype, off, n);
+    if (ops.leader()) p.info[b] = status == 1 ? 1 : 6;
+    return;
+  }
+  store_matrix(ops, p.dA, p.dtype, off, n, W.Ab);
+  if (ops.leader()) p.info[b] = 0;
 }
 
 }  // namespace lg

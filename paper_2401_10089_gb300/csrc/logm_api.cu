@@ -154,11 +154,21 @@ size_t logm_workspace_size(const logm_batch* batch, const logm_options* opts) {
   return ws_layout(batch, opts ? opts->precision : LOGM_PREC_TF32X3).total;
 }
 
+// Context: (s, k) per matrix, then the input of every square-root level.
+size_t ctx_header_bytes(const logm_batch* b) { return round256(sizeof(int32_t) * 2 * (size_t)b->count); }
+
 size_t logm_context_size(const logm_batch* batch, const logm_options* opts) {
   (void)opts;
   const int n_max = batch_n_max(batch);
   if (n_max <= 0) return 0;
-  return (size_t)batch->count * lg::kCtxLevels * (size_t)n_max * n_max * sizeof(double) + 256;
+  return ctx_header_bytes(batch) + (size_t)batch->count * lg::kCtxLevels * (size_t)n_max * n_max * sizeof(double);
+}
+
+size_t logm_backward_workspace_size(const logm_batch* batch, const logm_options* opts) {
+  (void)opts;
+  const int n_max = batch_n_max(batch);
+  if (n_max <= 0 || n_max > lg::kSmallMaxN) return 0;
+  return lg::small_bwd_workspace_bytes(batch->count, n_max);
 }
 
 int logm_plan(const logm_batch* batch, const logm_options* opts, const void* A, const void* AI2,
@@ -256,7 +266,10 @@ int logm_execute(const logm_batch* batch, const logm_options* opts, const void* 
   p.k_out = k_dev;
   p.info = info_dev;
   p.stats = stats_dev;
-  p.ctx = static_cast<double*>(ctx);
+  if (ctx) {
+    p.ctx_hdr = static_cast<int32_t*>(ctx);
+    p.ctx = reinterpret_cast<double*>(static_cast<char*>(ctx) + ctx_header_bytes(batch));
+  }
   p.ctx_levels = lg::kCtxLevels;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (opts->precision == LOGM_PREC_FP64) return run_passes(lg::kModeExecute, p, batch, ws, st);
@@ -290,9 +303,28 @@ int logm_execute(const logm_batch* batch, const logm_options* opts, const void* 
 int logm_backward(const logm_batch* batch, const logm_options* opts, const void* A, const void* ctx,
                   const void* dL, void* dA, int32_t* info_dev, void* ws, size_t ws_bytes,
                   void* stream) {
-  (void)batch; (void)opts; (void)A; (void)ctx; (void)dL; (void)dA; (void)info_dev;
-  (void)ws; (void)ws_bytes; (void)stream;
-  return LOGM_ERR_UNSUPPORTED;
+  const int n_max = batch_n_max(batch);
+  if (n_max <= 0 || !opts_ok(opts)) return LOGM_ERR_INVALID_ARG;
+  if (batch->count == 0) return LOGM_SUCCESS;
+  if (!A || !ctx || !dL || !dA || !info_dev) return LOGM_ERR_INVALID_ARG;
+  if (n_max > lg::kSmallMaxN) return LOGM_ERR_UNSUPPORTED;
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 != 0) return LOGM_ERR_WORKSPACE;
+  if (ws_bytes < logm_backward_workspace_size(batch, opts)) return LOGM_ERR_WORKSPACE;
+  lg::SmallParams p;
+  fill_common(p, batch, opts);
+  p.A = A;
+  p.dL = dL;
+  p.dA = dA;
+  p.info = info_dev;
+  p.ctx_hdr = const_cast<int32_t*>(static_cast<const int32_t*>(ctx));
+  p.ctx = reinterpret_cast<double*>(const_cast<char*>(static_cast<const char*>(ctx)) + ctx_header_bytes(batch));
+  p.ctx_levels = lg::kCtxLevels;
+  char* w = static_cast<char*>(ws);
+  p.queue = reinterpret_cast<int32_t*>(w);
+  p.slots = reinterpret_cast<double*>(w + 256 + lg::small_order_bytes(batch->count));
+  p.n_slots = lg::small_kernel_slots(batch->count);
+  const cudaError_t e = lg::launch_small(lg::kModeBackward, p, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? LOGM_SUCCESS : LOGM_ERR_CUDA;
 }
 
 }  // extern "C"

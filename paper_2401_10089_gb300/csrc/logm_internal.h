@@ -8,7 +8,7 @@
 
 namespace lg {
 
-enum Mode : int { kModeExecute = 0, kModePlan = 1, kModeSqrt = 2, kModeGraph = 3 };
+enum Mode : int { kModeExecute = 0, kModePlan = 1, kModeSqrt = 2, kModeGraph = 3, kModeBackward = 4 };
 
 // Everything one launch of the one-block-per-matrix kernel needs. Device
 // pointers unless noted.
@@ -38,7 +38,10 @@ struct SmallParams {
   double* alpha;
   int32_t* iters;
   int32_t* stats;      // execute: [4 * count] DB iterations, inverses, products, matvecs
-  double* ctx;         // execute: per-level checkpoints (NULL = none)
+  double* ctx;         // execute: per-level checkpoints (NULL = none); backward: read
+  int32_t* ctx_hdr;    // execute: (s, k) per matrix for the backward (NULL = none)
+  const void* dL;      // backward: adjoint of L
+  void* dA;            // backward: result
   int ctx_levels;
   int ctx_nmax;        // n stride of the checkpoint layout (the batch's n_max)
   // workspace
@@ -75,6 +78,9 @@ cudaError_t launch_graph_tc(const GraphParams& p, cudaStream_t st);
 cudaError_t launch_graph_prep(const GraphParams& p, const void* X, const void* P3, int in_dtype, cudaStream_t st);
 
 constexpr int kSlotMats = 7;
+constexpr int kBwdTapeCap = 16;                       // Denman-Beavers iterations a backward level can reverse
+constexpr int kBwdSlotMats = 7 + 6 + 4 + 2 * kBwdTapeCap;  // forward recompute, adjoints, temporaries, tape
+size_t small_bwd_workspace_bytes(int count, int n_max);
 constexpr int kOrderBuckets = 256;
 constexpr int kCtxLevels = 12;
 constexpr int kSmallMaxN = 256;  // largest n of the one-block-per-matrix kernels

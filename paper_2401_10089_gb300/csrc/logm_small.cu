@@ -90,9 +90,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_logm_small(SmallParams p) {
   BlockSmem& S = *reinterpret_cast<BlockSmem*>(smem_raw);
   BlockOps ops{S};
   const int64_t nn_max = (int64_t)p.n_max * p.n_max;
-  double* base = p.slots + (int64_t)blockIdx.x * kSlotMats * nn_max;
+  const int mats = (MODE == kModeBackward) ? kBwdSlotMats : kSlotMats;
+  double* base = p.slots + (int64_t)blockIdx.x * mats * nn_max;
   Slot M{base, base + nn_max, base + 2 * nn_max, base + 3 * nn_max,
          base + 4 * nn_max, base + 5 * nn_max, base + 6 * nn_max};
+  BwdSlot W;
+  if (MODE == kModeBackward) {
+    W.F = M;
+    for (int i = 0; i < 6; ++i) W.Pb[i] = base + (7 + i) * nn_max;
+    W.Lb = base + 13 * nn_max;
+    W.Rb = base + 14 * nn_max;
+    W.Ab = base + 15 * nn_max;
+    W.Yb = base + 16 * nn_max;
+    W.tape.inv = base + 17 * nn_max;
+    W.tape.stride = nn_max;
+    W.tape.cap = kBwdTapeCap;
+    W.tape.mu = p.slots + (int64_t)p.n_slots * kBwdSlotMats * nn_max + (int64_t)blockIdx.x * kBwdTapeCap;
+  }
   for (;;) {
     if (threadIdx.x == 0) S.ibc[0] = atomicAdd(p.queue, 1);
     __syncthreads();
@@ -123,6 +137,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_logm_small(SmallParams p) {
     if (MODE == kModePlan) run_plan(ops, p, b, n, off, M);
     if (MODE == kModeSqrt) run_sqrt(ops, p, b, n, off, M);
     if (MODE == kModeGraph) run_graph(ops, p, b, n, off, M);
+    if (MODE == kModeBackward) run_backward(ops, p, b, n, off, W);
     __syncthreads();
   }
 }
@@ -151,6 +166,12 @@ int small_kernel_slots(int count) {
 size_t small_order_bytes(int count) {
   const size_t raw = sizeof(int32_t) * ((size_t)count + 2 * kOrderBuckets + (size_t)count);
   return (raw + 255) / 256 * 256;
+}
+
+size_t small_bwd_workspace_bytes(int count, int n_max) {
+  const size_t slots = (size_t)small_kernel_slots(count);
+  return 256 + small_order_bytes(count) + slots * kBwdSlotMats * (size_t)n_max * n_max * sizeof(double) +
+         slots * kBwdTapeCap * sizeof(double);
 }
 
 size_t small_workspace_bytes(int count, int n_max) {
@@ -191,6 +212,7 @@ cudaError_t launch_small(Mode mode, const SmallParams& p, cudaStream_t st) {
     case kModePlan: return launch_mode<kModePlan>(p, st);
     case kModeSqrt: return launch_mode<kModeSqrt>(p, st);
     case kModeGraph: return launch_mode<kModeGraph>(p, st);
+    case kModeBackward: return launch_mode<kModeBackward>(p, st);
   }
   return cudaErrorInvalidValue;
 }
