@@ -186,7 +186,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=COUNT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the split-precision forms")
+    ap.add_argument("--no-forms", action="store_true", help="skip the precision and differentiation forms")
+    ap.add_argument("--batching", action="store_true", help="also time the 20,000-matrix ragged batching form")
     ap.add_argument("--count", type=int, default=COUNT, help="matrices per rank (smaller for profiling)")
     ap.add_argument("--no-big", action="store_true", help="leave out the 4096 x 4096 matrix")
     ap.add_argument("--big-n", type=int, default=NBIG, help="size of the large matrix (smaller for profiling)")
@@ -322,6 +323,63 @@ def main():
             ent["step"] = {"ms": ms_fa + ms_fb, "tflops": (flops_a + flops_b) / ((ms_fa + ms_fb) * 1e-3) / 1e12,
                            "speedup_vs_fp64": ms / (ms_fa + ms_fb)}
         forms[prec] = ent
+
+    # differentiation form: 1024 SPD 64 x 64 (lambda log-uniform in [1e-2, 1e2]),
+    # loss = sum(W o log A): forward with checkpoints, then the hand-written adjoint
+    if not args.no_forms:
+        Ad = torch.from_numpy(workloads.spd(1024, 64, seed=91 + rank, lo=1e-2, hi=1e2)).to(dev)
+        Wd = torch.from_numpy(np.random.default_rng(92 + rank).standard_normal((1024, 64, 64))).to(dev)
+        st_d = torch.zeros(4 * 1024, dtype=torch.int32, device=dev)
+        for _ in range(2):
+            Ld, _, _, _, cd = lg.logm_execute(Ad, with_ctx=True, stats=st_d)
+            dAd, bi = lg.logm_backward(Ad, cd, Wd)
+        barrier()
+        d0, d1, d2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        reps = max(1, args.steps)
+        fwd_ms = bwd_ms = 0.0
+        for _ in range(reps):
+            d0.record(stream)
+            Ld, _, _, _, cd = lg.logm_execute(Ad, with_ctx=True, stats=st_d)
+            d1.record(stream)
+            dAd, bi = lg.logm_backward(Ad, cd, Wd)
+            d2.record(stream)
+            barrier()
+            fwd_ms += d0.elapsed_time(d1) / reps
+            bwd_ms += d1.elapsed_time(d2) / reps
+        forms["differentiation"] = {
+            "workload": "1024 SPD 64x64, lambda log-uniform [1e-2, 1e2], loss = sum(W o log A), FP64",
+            "forward_ms": fwd_ms, "backward_ms": bwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
+            "matrices_per_s_fwd_bwd": 1024 / ((fwd_ms + bwd_ms) * 1e-3),
+            "forward_tflops": algorithmic_flops(st_d.cpu().numpy(), 64) / (fwd_ms * 1e-3) / 1e12,
+            "backward_info_nonzero": int((bi.cpu().numpy() != 0).sum())}
+    # batching form (opt-in, input generation takes ~30 s): 20,000 SPD matrices,
+    # n uniform in {4, 8, ..., 256}, lambda log-uniform in [1e-3, 1e3], FP32 storage,
+    # TF32x3 graph products, one logm_execute call
+    if args.batching:
+        vals, ns_r, offs_r = workloads.ragged_spd(20000, seed=4 + rank)
+        R = lg.Ragged(torch.from_numpy(vals).to(dev), torch.from_numpy(ns_r).to(dev),
+                      torch.from_numpy(offs_r).to(dev), 256)
+        st_r = torch.zeros(4 * 20000, dtype=torch.int32, device=dev)
+        entry = {}
+        for prec in ("tf32x3", "fp64"):
+            lg.logm_execute(R, precision=prec, stats=st_r)
+            barrier()
+            r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            r0.record(stream)
+            Lr_, sr_, kr_, ir_ = lg.logm_execute(R, precision=prec, stats=st_r)
+            r1.record(stream)
+            barrier()
+            ms_r = r0.elapsed_time(r1)
+            w = st_r.cpu().numpy().reshape(-1, 4).astype(np.float64)
+            fl = float(((w[:, 1] + w[:, 2]) * 2.0 * ns_r.astype(np.float64) ** 3
+                        + w[:, 3] * 2.0 * ns_r.astype(np.float64) ** 2).sum())
+            entry[prec] = {"ms": ms_r, "matrices_per_s": 20000 / (ms_r * 1e-3), "tflops": fl / (ms_r * 1e-3) / 1e12,
+                           "info_nonzero": int((ir_.cpu().numpy() != 0).sum()),
+                           "s_hist": np.bincount(sr_.cpu().numpy()).tolist()}
+        entry["workload"] = ("20000 SPD, n uniform in {4..256}, lambda log-uniform [1e-3, 1e3], FP32 storage, "
+                             "one call (persistent FP64 stage + tcgen05 graph stage)")
+        entry["speedup_tf32x3_vs_fp64"] = entry["fp64"]["ms"] / entry["tf32x3"]["ms"]
+        forms["batching"] = entry
 
     if rank == 0:
         # dominant kernel: the whole-GPU 4096 kernel (seconds long -> sustained peak)

@@ -65,7 +65,7 @@ def spd(count: int, n: int, seed: int = 3, lo: float = 1e-2, hi: float = 1e2) ->
     rng = np.random.default_rng(seed)
     q = _orthogonal(rng, n, count)
     lam = _log_uniform(rng, lo, hi, (count, n))
-    a = np.einsum("bij,bj,bkj->bik", q, lam, q)
+    a = (q * lam[:, None, :]) @ np.swapaxes(q, 1, 2)
     return 0.5 * (a + np.swapaxes(a, 1, 2))
 
 

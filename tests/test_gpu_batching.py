@@ -1,0 +1,64 @@
+"""Batching form: thousands of matrices of uneven n in one call (a persistent
+launch for the FP64 stage, one tensor-core launch per graph product), FP32
+storage, split-precision products, checked against the FP64 oracle; and the
+whole call captured once in a CUDA graph and replayed.
+
+Tolerance 1e-5 relative: FP32 storage of A and L (6e-8), TF32x3 products and
+FP32 lin-combs (about 1e-7 per product), amplified by the conditioning of the
+logarithm for SPD inputs with eigenvalues in [1e-3, 1e3].
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_10089_gb300 import workloads
+from tests.test_gpu_parity import lg, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SIZES = (4, 8, 16, 32, 64, 128, 256)
+
+
+def ragged(count, seed):
+    vals, ns, offs = workloads.ragged_spd(count, SIZES, seed=seed)
+    R = lg().Ragged(torch.tensor(vals, device="cuda"), torch.tensor(ns, device="cuda"),
+                    torch.tensor(offs, device="cuda"), max(SIZES))
+    return vals, ns, offs, R
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3", "fp64"])
+def test_ragged_spd_fp32_storage(precision):
+    vals, ns, offs, R = ragged(700, seed=40)
+    L, s, k, info = lg().logm_execute(R, precision=precision)
+    out = L.values.cpu().numpy()
+    info = info.cpu().numpy()
+    assert (info == 0).all()
+    rng = np.random.default_rng(41)
+    for n in SIZES:  # two matrices of every size
+        for b in rng.choice(np.nonzero(ns == n)[0], 2, replace=False):
+            A = vals[offs[b]:offs[b] + n * n].reshape(n, n).astype(np.float64)
+            Lr, d = oracle.logm(A)
+            Lg = out[offs[b]:offs[b] + n * n].reshape(n, n).astype(np.float64)
+            assert rel(Lg, Lr) <= 1e-5, (precision, n, b, rel(Lg, Lr))
+
+
+def test_execute_captured_in_cuda_graph():
+    vals, ns, offs, R = ragged(300, seed=42)
+    L_eager, s_e, k_e, i_e = lg().logm_execute(R, precision="tf32x3")  # also sets kernel attributes
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        lg().logm_execute(R, precision="tf32x3")  # warm the workspace cache on this stream
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            L_g, s_g, k_g, i_g = lg().logm_execute(R, precision="tf32x3")
+    torch.cuda.current_stream().wait_stream(stream)
+    for _ in range(2):
+        L_g.values.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(L_g.values, L_eager.values)
+        assert torch.equal(s_g, s_e) and torch.equal(k_g, k_e) and torch.equal(i_g, i_e)
