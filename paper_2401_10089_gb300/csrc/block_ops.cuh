@@ -53,6 +53,14 @@ struct BlockOps {
     return gj_inverse_block(dst, n, logabsdet, S);
   }
 
+  // Xi <- X^{-1}, Yi <- Y^{-1} (one after the other on this block).
+  __device__ int inverse_pair(const double* X, double* Xi, const double* Y, double* Yi, int n, double* ldx,
+                              double* ldy) {
+    const int a = inverse(X, Xi, n, ldx);
+    if (a) return a;
+    return inverse(Y, Yi, n, ldy);
+  }
+
   __device__ void tally_reset() {
     if (threadIdx.x == 0) S.work[0] = S.work[1] = S.work[2] = S.work[3] = 0;
   }

@@ -22,20 +22,27 @@ constexpr int kGridPanel = 32;          // Gauss-Jordan panel width for large n
 constexpr int kMaxGrid = 1024;          // upper bound on co-resident blocks
 constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s
 
+// Buffers of one Gauss-Jordan inversion running on a group of blocks.
+struct GjGroup {
+  unsigned* bar;     // [2] arrivals, generation of the group's own barrier
+  double* cand_v;    // [2][kMaxGrid] pivot candidates (value)
+  int* cand_i;       // [2][kMaxGrid] pivot candidates (row)
+  double* panel;     // [2][kGridPanel][n_max] panel, column-major, double-buffered
+  double* R;         // [kGridPanel][n_max] pivot rows of the panel
+  int* piv;          // [n_max] pivot rows of the Gauss-Jordan steps
+  int* perm;         // [n_max] composite column permutation
+  double* work;      // [n_max^2] working matrix
+  double* result;    // [2] log|det|, status
+};
+
 struct GridWs {
   unsigned* bar;     // [0] arrivals, [1] generation (zeroed before the launch)
   int* err;          // set when a barrier wait timed out (zeroed before the launch)
   double* partial;   // [2][kMaxGrid] partial results of sum / max
   int* ipartial;     // [2][kMaxGrid] partial results of all / argmax indices
-  double* cand_v;    // [2][kMaxGrid] pivot candidates (value)
-  int* cand_i;       // [2][kMaxGrid] pivot candidates (row)
   double* vec;       // [4][n_max] estimator vectors
-  double* panel;     // [2][kGridPanel][n_max] panel, column-major, double-buffered
-  double* R;         // [kGridPanel][n_max] pivot rows of the panel
-  int* piv;          // [n_max] pivot rows of the Gauss-Jordan steps
-  int* perm;         // [n_max] composite column permutation
   double* misc;      // [8] broadcast slots
-  double* work;      // [n_max^2] Gauss-Jordan working matrix
+  GjGroup gj[2];     // the two inversion groups (gj[0] alone when one inversion uses the whole grid)
   int n_max;
 };
 
@@ -54,25 +61,26 @@ static __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-static __device__ void grid_barrier(GridWs& w) {
+// Barrier over `nblocks` blocks sharing the counter pair bar[0..1].
+static __device__ void bounded_barrier(unsigned* bar, unsigned nblocks, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = w.bar + 1;
-    volatile int* verr = w.err;
+    volatile unsigned* vgen = bar + 1;
+    volatile int* verr = err;
     if (*verr == 0) {
       const unsigned g = *vgen;
       __threadfence();
-      const unsigned arrived = atomicAdd(w.bar, 1u);
-      if (arrived == gridDim.x - 1) {
-        atomicExch(w.bar, 0u);
+      const unsigned arrived = atomicAdd(bar, 1u);
+      if (arrived == nblocks - 1) {
+        atomicExch(bar, 0u);
         __threadfence();
-        atomicAdd(w.bar + 1, 1u);
+        atomicAdd(bar + 1, 1u);
       } else {
         const unsigned long long t0 = global_ns();
         while (*vgen == g && *verr == 0) {
           __nanosleep(64);
           if (global_ns() - t0 > kBarrierTimeoutNs) {
-            atomicExch(w.err, 1);
+            atomicExch(err, 1);
             break;
           }
         }
@@ -82,6 +90,8 @@ static __device__ void grid_barrier(GridWs& w) {
   }
   __syncthreads();
 }
+
+static __device__ __forceinline__ void grid_barrier(GridWs& w) { bounded_barrier(w.bar, gridDim.x, w.err); }
 
 struct GridOps {
   GridWs& w;
@@ -217,7 +227,8 @@ struct GridOps {
   }
 
   // W[r0.., c0..] (64 x 64 tile) += (Pf - I_J)[r0.., 0..jb) R[0..jb), c0..], columns of J skipped.
-  __device__ void rank_update_tile(double* W, int n, int kb, int jb, const double* Pf, int r0, int c0) {
+  __device__ void rank_update_tile(double* W, int n, int kb, int jb, const double* Pf, const double* R, int r0,
+                                   int c0) {
     GemmSmem& sm = S.gemm;
     const int tid_ = threadIdx.x, lane = tid_ & 31, warp = tid_ >> 5;
     const int wm = warp >> 1, wn = warp & 1;
@@ -236,7 +247,7 @@ struct GridOps {
       for (int e = tid_; e < kTileK * kTileN; e += kThreads) {
         const int kk = e / kTileN, cc = e % kTileN;
         const int gk = k0 + kk, gc = c0 + cc;
-        sm.Bs[kk * kBsStride + cc] = (gk < jb && gc < n) ? w.R[(int64_t)gk * n + gc] : 0.0;
+        sm.Bs[kk * kBsStride + cc] = (gk < jb && gc < n) ? R[(int64_t)gk * n + gc] : 0.0;
       }
       __syncthreads();
 #pragma unroll
@@ -263,31 +274,36 @@ struct GridOps {
           const int gc = c0 + wn * 32 + nb * 8 + 2 * q + h;
           if (gr < n && gc < n && (gc < kb || gc >= kb + jb)) {
             double v = acc[mb][nb][h];
-            if (gr >= kb && gr < kb + jb) v -= w.R[(int64_t)(gr - kb) * n + gc];  // the -I_J part
+            if (gr >= kb && gr < kb + jb) v -= R[(int64_t)(gr - kb) * n + gc];  // the -I_J part
             W[(int64_t)gr * n + gc] += v;
           }
         }
   }
 
   // dst <- src^{-1} by Gauss-Jordan with partial pivoting (same steps as
-  // gj_inverse_block), panels of kGridPanel columns. The panel is spread over
-  // the blocks by rows; each column step is one grid barrier: the owners of
-  // every row apply the step and publish the next column's pivot candidates.
-  // Returns 0, or 1 for a zero / non-finite pivot.
-  __device__ int inverse(const double* src, double* dst, int n, double* logabsdet) {
-    double* W = w.work;
+  // gj_inverse_block), panels of kGridPanel columns, on the gn blocks
+  // starting at g0 with the group's buffers and barrier `bar`. The panel is
+  // spread over the group's blocks by rows; each column step is one group
+  // barrier: the owners of every row apply the step and publish the next
+  // column's pivot candidates. Writes log|det| and the status (0, or 1 for a
+  // zero / non-finite pivot) to g.result.
+  __device__ void inverse_group(GjGroup& g, int g0, int gn, unsigned* bar, const double* src, double* dst, int n) {
+    const int lb = blockIdx.x - g0;
+    const int gt = lb * kThreads + threadIdx.x, gnt = gn * kThreads;
+    const bool glead = lb == 0 && threadIdx.x == 0;
+    double* W = g.work;
     const int64_t nn = (int64_t)n * n;
-    for (int64_t t = tid(); t < nn; t += nthreads()) W[t] = src[t];
-    const int G = gridDim.x;
+    for (int64_t t = gt; t < nn; t += gnt) W[t] = src[t];
+    const int G = gn;
     const int rows_per = (n + G - 1) / G;
-    const int r_lo = blockIdx.x * rows_per;
+    const int r_lo = lb * rows_per;
     const int r_hi = min(n, r_lo + rows_per);
     const int my_rows = r_hi > r_lo ? r_hi - r_lo : 0;
-    double* P0 = w.panel;
-    double* P1 = w.panel + (int64_t)kGridPanel * w.n_max;
-    double ld = 0.0;  // block 0, thread 0
+    double* P0 = g.panel;
+    double* P1 = g.panel + (int64_t)kGridPanel * w.n_max;
+    double ld = 0.0;  // group leader
     int status = 0;
-    sync();
+    bounded_barrier(bar, gn, w.err);
     for (int kb = 0; kb < n && !status; kb += kGridPanel) {
       const int jb = min(kGridPanel, n - kb);
       // own rows of W[:, J] -> P0, and the candidates of column kb
@@ -308,24 +324,24 @@ struct GridOps {
         int bi;
         block_argmax(cv, ci, S.red, &bv, &bi);
         if (threadIdx.x == 0) {
-          w.cand_v[blockIdx.x] = bv;
-          w.cand_i[blockIdx.x] = bi;
+          g.cand_v[lb] = bv;
+          g.cand_i[lb] = bi;
         }
       }
-      sync();
+      bounded_barrier(bar, gn, w.err);
       for (int c = 0; c < jb; ++c) {
         const int k = kb + c;
         const double* Pin = (c & 1) ? P1 : P0;
         double* Pout = (c & 1) ? P0 : P1;
-        const double* cvv = w.cand_v + (c & 1) * kMaxGrid;
-        const int* cii = w.cand_i + (c & 1) * kMaxGrid;
+        const double* cvv = g.cand_v + (c & 1) * kMaxGrid;
+        const int* cii = g.cand_i + (c & 1) * kMaxGrid;
         double pv;
         int p;
         {
           double cv = -1.0;
           int ci = 0x7fffffff;
-          for (int g = threadIdx.x; g < G; g += kThreads)
-            if (cvv[g] > cv || (cvv[g] == cv && cii[g] < ci)) { cv = cvv[g]; ci = cii[g]; }
+          for (int q = threadIdx.x; q < G; q += kThreads)
+            if (cvv[q] > cv || (cvv[q] == cv && cii[q] < ci)) { cv = cvv[q]; ci = cii[q]; }
           block_argmax(cv, ci, S.red, &pv, &p);
         }
         if (!(pv > 0.0) || !(pv < INFINITY) || p < k || p >= n) { status = 1; break; }
@@ -336,9 +352,9 @@ struct GridOps {
         __syncthreads();
         const double d = S.rowp[c];
         const double inv = bcast0(1.0 / d);
-        if (leader()) {
+        if (glead) {
           ld += log(fabs(d));
-          w.piv[k] = p;
+          g.piv[k] = p;
         }
         double cv = -1.0;
         int ci = 0x7fffffff;
@@ -365,11 +381,11 @@ struct GridOps {
           int bi;
           block_argmax(cv, ci, S.red, &bv, &bi);
           if (threadIdx.x == 0) {
-            w.cand_v[((c + 1) & 1) * kMaxGrid + blockIdx.x] = bv;
-            w.cand_i[((c + 1) & 1) * kMaxGrid + blockIdx.x] = bi;
+            g.cand_v[((c + 1) & 1) * kMaxGrid + lb] = bv;
+            g.cand_i[((c + 1) & 1) * kMaxGrid + lb] = bi;
           }
         }
-        sync();
+        bounded_barrier(bar, gn, w.err);
       }
       if (status) break;
       const double* Pf = (jb & 1) ? P1 : P0;
@@ -378,45 +394,77 @@ struct GridOps {
         const int r = r_lo + e / jb, c = e % jb;
         W[(int64_t)r * n + kb + c] = Pf[(int64_t)c * n + r];
       }
-      for (int j = tid(); j < n; j += nthreads()) {
+      for (int j = gt; j < n; j += gnt) {
         if (j >= kb && j < kb + jb) continue;
         for (int c = 0; c < jb; ++c) {
-          const int k = kb + c, p = w.piv[k];
+          const int k = kb + c, p = g.piv[k];
           if (p != k) {
             const double t0 = W[(int64_t)k * n + j];
             W[(int64_t)k * n + j] = W[(int64_t)p * n + j];
             W[(int64_t)p * n + j] = t0;
           }
         }
-        for (int c = 0; c < jb; ++c) w.R[(int64_t)c * n + j] = W[(int64_t)(kb + c) * n + j];
+        for (int c = 0; c < jb; ++c) g.R[(int64_t)c * n + j] = W[(int64_t)(kb + c) * n + j];
       }
-      sync();
+      bounded_barrier(bar, gn, w.err);
       const int tiles = (n + kTileM - 1) / kTileM;
-      for (int t = blockIdx.x; t < tiles * tiles; t += G)
-        rank_update_tile(W, n, kb, jb, Pf, (t / tiles) * kTileM, (t % tiles) * kTileN);
-      sync();
+      for (int t = lb; t < tiles * tiles; t += G)
+        rank_update_tile(W, n, kb, jb, Pf, g.R, (t / tiles) * kTileM, (t % tiles) * kTileN);
+      bounded_barrier(bar, gn, w.err);
     }
-    if (leader()) w.misc[0] = ld;
     if (!status) {
-      if (leader()) {
-        for (int j = 0; j < n; ++j) w.perm[j] = j;
+      if (glead) {
+        for (int j = 0; j < n; ++j) g.perm[j] = j;
         for (int k = n - 1; k >= 0; --k) {
-          const int p = w.piv[k];
-          const int t0 = w.perm[k];
-          w.perm[k] = w.perm[p];
-          w.perm[p] = t0;
+          const int p = g.piv[k];
+          const int t0 = g.perm[k];
+          g.perm[k] = g.perm[p];
+          g.perm[p] = t0;
         }
       }
-      sync();
-      for (int64_t t = tid(); t < nn; t += nthreads()) {
+      bounded_barrier(bar, gn, w.err);
+      for (int64_t t = gt; t < nn; t += gnt) {
         const int64_t i = t / n, j = t % n;
-        dst[t] = W[i * n + w.perm[j]];
+        dst[t] = W[i * n + g.perm[j]];
       }
     }
+    if (glead) {
+      g.result[0] = ld;
+      g.result[1] = status;
+    }
+  }
+
+  // dst <- src^{-1} on the whole grid; returns 0, or 1 for a zero / non-finite pivot.
+  __device__ int inverse(const double* src, double* dst, int n, double* logabsdet) {
+    inverse_group(w.gj[0], 0, gridDim.x, w.bar, src, dst, n);
     sync();
-    *logabsdet = w.misc[0];
+    *logabsdet = w.gj[0].result[0];
+    const int st = w.gj[0].result[1] != 0.0;
     sync();
-    return status;
+    return st;
+  }
+
+  // Xi <- X^{-1} and Yi <- Y^{-1} at the same time, each on one half of the
+  // grid (blocks b and b + G/2 share an SM, so one group's panel steps overlap
+  // the other group's rank updates on the FP64 pipe).
+  __device__ int inverse_pair(const double* X, double* Xi, const double* Y, double* Yi, int n, double* ldx,
+                              double* ldy) {
+    const int half = gridDim.x / 2;
+    if (half < 8) {
+      const int a = inverse(X, Xi, n, ldx);
+      const int b = inverse(Y, Yi, n, ldy);
+      return a | b;
+    }
+    if ((int)blockIdx.x < half)
+      inverse_group(w.gj[0], 0, half, w.gj[0].bar, X, Xi, n);
+    else
+      inverse_group(w.gj[1], half, gridDim.x - half, w.gj[1].bar, Y, Yi, n);
+    sync();
+    *ldx = w.gj[0].result[0];
+    *ldy = w.gj[1].result[0];
+    const int st = (w.gj[0].result[1] != 0.0) || (w.gj[1].result[1] != 0.0);
+    sync();
+    return st;
   }
 
   __device__ void tally_reset() {

@@ -394,13 +394,13 @@ static __device__ int db_sqrt(Ops& ops, Slot& M, int n, int max_db, int* iters_o
     const bool taped = tape && it - 1 < tape->cap;
     double* Xi = taped ? tape->inv + (int64_t)(2 * (it - 1)) * tape->stride : M.W1;
     double* Yi = taped ? tape->inv + (int64_t)(2 * (it - 1) + 1) * tape->stride : M.W2;
-    if (ops.inverse(X, Xi, n, &ldx)) { status = 1; break; }
     if (it == 1) {
+      if (ops.inverse(X, Xi, n, &ldx)) { status = 1; break; }
       // Y_0 = I: its inverse is I and log|det Y_0| = 0 exactly.
       identity_matrix(ops, Yi, n);
       ldy = 0.0;
     } else {
-      if (ops.inverse(Y, Yi, n, &ldy)) { status = 1; break; }
+      if (ops.inverse_pair(X, Xi, Y, Yi, n, &ldx, &ldy)) { status = 1; break; }
     }
     const double mu = ops.bcast0(scale ? exp(-(ldx + ldy) / (2.0 * n)) : 1.0);
     const double imu = ops.bcast0(1.0 / mu);

@@ -49,26 +49,34 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+struct GroupLayout {
+  size_t cand_v, cand_i, panel, R, piv, perm, work;
+};
+
 struct LargeLayout {
-  size_t bar, partial, ipartial, cand_v, cand_i, vec, panel, R, piv, perm, misc, work, slot, total;
+  size_t bar, partial, ipartial, vec, misc, slot, total;
+  GroupLayout g[2];
 };
 
 LargeLayout large_layout(int n_max) {
   LargeLayout L{};
   size_t o = 0;
   const size_t nm = (size_t)n_max;
-  L.bar = o;      o = align256(o + 16);
+  L.bar = o;      o = align256(o + 64);  // main barrier, error word, two group barriers
   L.partial = o;  o = align256(o + sizeof(double) * 2 * kMaxGrid);
   L.ipartial = o; o = align256(o + sizeof(int) * 2 * kMaxGrid);
-  L.cand_v = o;   o = align256(o + sizeof(double) * 2 * kMaxGrid);
-  L.cand_i = o;   o = align256(o + sizeof(int) * 2 * kMaxGrid);
   L.vec = o;      o = align256(o + sizeof(double) * 4 * nm);
-  L.panel = o;    o = align256(o + sizeof(double) * 2 * kGridPanel * nm);
-  L.R = o;        o = align256(o + sizeof(double) * kGridPanel * nm);
-  L.piv = o;      o = align256(o + sizeof(int) * nm);
-  L.perm = o;     o = align256(o + sizeof(int) * nm);
-  L.misc = o;     o = align256(o + sizeof(double) * 8);
-  L.work = o;     o = align256(o + sizeof(double) * nm * nm);
+  L.misc = o;     o = align256(o + sizeof(double) * 16);
+  for (int t = 0; t < 2; ++t) {
+    GroupLayout& g = L.g[t];
+    g.cand_v = o; o = align256(o + sizeof(double) * 2 * kMaxGrid);
+    g.cand_i = o; o = align256(o + sizeof(int) * 2 * kMaxGrid);
+    g.panel = o;  o = align256(o + sizeof(double) * 2 * kGridPanel * nm);
+    g.R = o;      o = align256(o + sizeof(double) * kGridPanel * nm);
+    g.piv = o;    o = align256(o + sizeof(int) * nm);
+    g.perm = o;   o = align256(o + sizeof(int) * nm);
+    g.work = o;   o = align256(o + sizeof(double) * nm * nm);
+  }
   L.slot = o;     o = align256(o + sizeof(double) * kSlotMats * nm * nm);
   L.total = o;
   return L;
@@ -84,15 +92,21 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
   w.err = reinterpret_cast<int*>(ws + L.bar + 8);
   w.partial = reinterpret_cast<double*>(ws + L.partial);
   w.ipartial = reinterpret_cast<int*>(ws + L.ipartial);
-  w.cand_v = reinterpret_cast<double*>(ws + L.cand_v);
-  w.cand_i = reinterpret_cast<int*>(ws + L.cand_i);
   w.vec = reinterpret_cast<double*>(ws + L.vec);
-  w.panel = reinterpret_cast<double*>(ws + L.panel);
-  w.R = reinterpret_cast<double*>(ws + L.R);
-  w.piv = reinterpret_cast<int*>(ws + L.piv);
-  w.perm = reinterpret_cast<int*>(ws + L.perm);
   w.misc = reinterpret_cast<double*>(ws + L.misc);
-  w.work = reinterpret_cast<double*>(ws + L.work);
+  for (int t = 0; t < 2; ++t) {
+    GjGroup& g = w.gj[t];
+    const GroupLayout& gl = L.g[t];
+    g.bar = reinterpret_cast<unsigned*>(ws + L.bar + 16 + 8 * t);
+    g.cand_v = reinterpret_cast<double*>(ws + gl.cand_v);
+    g.cand_i = reinterpret_cast<int*>(ws + gl.cand_i);
+    g.panel = reinterpret_cast<double*>(ws + gl.panel);
+    g.R = reinterpret_cast<double*>(ws + gl.R);
+    g.piv = reinterpret_cast<int*>(ws + gl.piv);
+    g.perm = reinterpret_cast<int*>(ws + gl.perm);
+    g.work = reinterpret_cast<double*>(ws + gl.work);
+    g.result = w.misc + 8 + 2 * t;
+  }
   w.n_max = p.n_max;
   const int64_t nn = (int64_t)p.n_max * p.n_max;
   double* base = reinterpret_cast<double*>(ws + L.slot);
@@ -110,7 +124,7 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
   if (grid < 1) return cudaErrorLaunchOutOfResources;
   g_large_grid = grid;
 
-  e = cudaMemsetAsync(ws + L.bar, 0, 16, st);
+  e = cudaMemsetAsync(ws + L.bar, 0, 64, st);
   if (e != cudaSuccess) return e;
   SmallParams pp = p;
   void* args[] = {&pp, &w, &M};
