@@ -188,6 +188,26 @@ int logm_backward(const logm_batch* batch, const logm_options* opts, const void*
 int logm_execute_noalloc(const logm_batch* batch, const logm_options* opts, const void* A, void* L,
                          int32_t* s_dev, int32_t* k_dev, int32_t* info_dev, void* stream);
 
+/* Per-size-bucket choice of the one-block-per-matrix kernel configuration
+ * used by logm_execute (batching form). Buckets: n <= 8, 16, 32, 64, 128, 256.
+ * Variants: 0 = 256-thread blocks, 64 x 64 DMMA tiles, any n <= 256;
+ *           1 = 128-thread blocks, 32 x 32 tiles, n <= 64 (buckets 0-3);
+ *           2 = 64-thread blocks, 32 x 32 tiles, n <= 32 (buckets 0-2).
+ * Smaller configurations keep more small matrices in flight per SM. The
+ * project's autotuner (paper_2401_10089_gb300.autotune) times the candidates
+ * on a sample of each bucket and writes the table it picks to JSON. */
+typedef struct logm_tuning {
+  int32_t variant[6];
+} logm_tuning;
+
+/* Set the process-wide table (NULL restores all-0). Returns LOGM_SUCCESS, or
+ * LOGM_ERR_INVALID_ARG for a variant a bucket cannot use. Not thread-safe
+ * against concurrent logm_execute calls. */
+int logm_set_tuning(const logm_tuning* t);
+
+/* Copy the current table to *t. */
+int logm_get_tuning(logm_tuning* t);
+
 /* Library version (major * 10000 + minor * 100 + patch). */
 int logm_version(void);
 

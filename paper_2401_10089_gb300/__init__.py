@@ -5,8 +5,10 @@ with computation-graph polynomials (Jarlebring, Sastre, Ibanez, arXiv
 The compute path is the CUDA library built from ``csrc/`` (C ABI in
 ``include/logm.h``); this package is its thin Python binding.
 """
-from .api import (LogmFunction, Ragged, logm, logm_backward, logm_backward_workspace_size, logm_context_size,
-                  logm_execute, logm_graph_eval, logm_plan, logm_sqrt, logm_version, logm_workspace_size)
+from .api import (LogmFunction, Ragged, get_tuning, logm, logm_backward, logm_backward_workspace_size,
+                  logm_context_size, logm_execute, logm_graph_eval, logm_plan, logm_sqrt, logm_version,
+                  logm_workspace_size, set_tuning)
 
-__all__ = ["LogmFunction", "Ragged", "logm", "logm_backward", "logm_backward_workspace_size", "logm_context_size",
-           "logm_execute", "logm_graph_eval", "logm_plan", "logm_sqrt", "logm_version", "logm_workspace_size"]
+__all__ = ["LogmFunction", "Ragged", "get_tuning", "logm", "logm_backward", "logm_backward_workspace_size",
+           "logm_context_size", "logm_execute", "logm_graph_eval", "logm_plan", "logm_sqrt", "logm_version",
+           "logm_workspace_size", "set_tuning"]

@@ -21,7 +21,8 @@ _ERRORS = {ERR_INVALID_ARG: "invalid argument", ERR_UNSUPPORTED: "unsupported", 
 
 # Every symbol include/logm.h declares.
 EXPORTS = ("logm_workspace_size", "logm_context_size", "logm_backward_workspace_size", "logm_plan", "logm_sqrt",
-           "logm_graph_eval", "logm_execute", "logm_backward", "logm_execute_noalloc", "logm_version")
+           "logm_graph_eval", "logm_execute", "logm_backward", "logm_execute_noalloc", "logm_set_tuning",
+           "logm_get_tuning", "logm_version")
 
 
 class LogmBatch(ctypes.Structure):
@@ -32,6 +33,10 @@ class LogmBatch(ctypes.Structure):
 class LogmOptions(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_sqrt", ctypes.c_int32),
                 ("max_db_iter", ctypes.c_int32), ("theta", ctypes.c_double * 3)]
+
+
+class LogmTuning(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32 * 6)]
 
 
 class LogmError(RuntimeError):
@@ -72,6 +77,8 @@ def load(build_if_missing: bool = True):
         L.logm_execute.argtypes = [B, O, V, V, V, V, V, V, V, V, SZ, V]
         L.logm_backward.argtypes = [B, O, V, V, V, V, V, V, SZ, V]
         L.logm_execute_noalloc.argtypes = [B, O, V, V, V, V, V, V]
+        L.logm_set_tuning.argtypes = [P(LogmTuning)]
+        L.logm_get_tuning.argtypes = [P(LogmTuning)]
         L.logm_version.argtypes = []
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
@@ -79,9 +86,28 @@ def load(build_if_missing: bool = True):
         L.logm_context_size.restype = SZ
         L.logm_backward_workspace_size.restype = SZ
         _lib = L
+        _apply_shipped_tuning(L)
         return _lib
 
 
 def check(rc: int, what: str):
     if rc != SUCCESS:
         raise LogmError(f"{what} failed: {_ERRORS.get(rc, rc)}")
+
+
+# Tuning table the project's autotuner picked on GB300 (see autotune.py);
+# applied when the library is first loaded.
+TUNING_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
+
+
+def _apply_shipped_tuning(L):
+    import json
+    if not os.path.exists(TUNING_FILE):
+        return
+    with open(TUNING_FILE) as f:
+        table = json.load(f).get("variant")
+    if table and len(table) == 6:
+        t = LogmTuning()
+        for i, v in enumerate(table):
+            t.variant[i] = int(v)
+        L.logm_set_tuning(ctypes.byref(t))

@@ -265,3 +265,24 @@ def logm(A, k_max=5, max_sqrt=40, max_db_iter=50):
     """Differentiable matrix logarithm of a (count, n, n) or (n, n) CUDA tensor."""
     L, s, k, info = LogmFunction.apply(A, k_max, max_sqrt, max_db_iter)
     return L
+
+
+def set_tuning(variants):
+    """Per-size-bucket kernel configuration (buckets n <= 8, 16, 32, 64, 128, 256;
+    0: 256-thread blocks, 1: 128-thread blocks for n <= 64, 2: 64-thread blocks
+    for n <= 32). ``None`` restores all-0."""
+    L = _lib.load()
+    if variants is None:
+        _lib.check(L.logm_set_tuning(None), "logm_set_tuning")
+        return
+    t = _lib.LogmTuning()
+    for i, v in enumerate(variants):
+        t.variant[i] = int(v)
+    _lib.check(L.logm_set_tuning(ctypes.byref(t)), "logm_set_tuning")
+
+
+def get_tuning():
+    L = _lib.load()
+    t = _lib.LogmTuning()
+    _lib.check(L.logm_get_tuning(ctypes.byref(t)), "logm_get_tuning")
+    return [int(t.variant[i]) for i in range(6)]

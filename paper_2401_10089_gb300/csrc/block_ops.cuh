@@ -5,7 +5,7 @@
 
 #include "cta_linalg.cuh"
 
-namespace lg {
+namespace LG_NS {
 
 struct BlockOps {
   BlockSmem& S;
@@ -70,4 +70,4 @@ struct BlockOps {
   __device__ int tally_get(int i) const { return S.work[i]; }
 };
 
-}  // namespace lg
+}  // namespace LG_NS

@@ -15,15 +15,33 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-namespace lg {
+// One translation unit builds one block configuration: LG_NS names its
+// namespace, LG_THREADS the block size, LG_MAXN the largest n, LG_TILE the
+// DMMA output tile (64: 8 warps of 16 x 32; 32: warps of 16 x 16 or 16 x 32).
+#ifndef LG_NS
+#define LG_NS lg
+#define LG_THREADS 256
+#define LG_MAXN 256
+#define LG_TILE 64
+#define LG_MINBLOCKS 2
+#endif
 
-constexpr int kThreads = 256;
+namespace lg {}
+namespace LG_NS {
+using namespace ::lg;
+
+constexpr int kThreads = LG_THREADS;
 constexpr int kWarps = kThreads / 32;
-constexpr int kMaxN = 256;   // largest n of the one-block-per-matrix kernels (= kSmallMaxN)
-constexpr int kPanel = 16;   // Gauss-Jordan panel width
-constexpr int kTileM = 64, kTileN = 64, kTileK = 16;
+constexpr int kMaxN = LG_MAXN;  // largest n of this one-block-per-matrix configuration
+constexpr int kPanel = 16;      // Gauss-Jordan panel width
+constexpr int kTileM = LG_TILE, kTileN = LG_TILE, kTileK = 16;
+constexpr int kWarpsM = (LG_TILE == 64) ? 4 : 2;   // warps along the tile's rows
+constexpr int kWarpsN = kWarps / kWarpsM;          // warps along its columns
+constexpr int kMB = kTileM / kWarpsM / 8;          // 8-row DMMA blocks per warp
+constexpr int kNB = kTileN / kWarpsN / 8;          // 8-column DMMA blocks per warp
 constexpr int kAsStride = kTileK + 4;  // shared-memory row strides that keep
 constexpr int kBsStride = kTileN + 4;  // DMMA fragment loads conflict-free
+static_assert(kWarpsM * kWarpsN == kWarps && kMB >= 1 && kNB >= 1, "tile / warp layout");
 
 struct Reduce {
   double v[kWarps];
@@ -224,13 +242,14 @@ static __device__ void gemm_tile(int n, int r0, int c0, const double* __restrict
                           const double* __restrict__ B, double b_shift, double alpha,
                           const EpiTerms& epi, OutView out, GemmSmem& sm, bool ta = false, bool tb = false) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;
+  const int wm = warp / kWarpsN, wn = warp % kWarpsN;
   const int g = lane >> 2, q = lane & 3;
-  double acc[2][4][2];
+  constexpr int RW = kTileM / kWarpsM, CW = kTileN / kWarpsN;  // rows, columns of a warp's sub-tile
+  double acc[kMB][kNB][2];
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < kMB; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+    for (int b = 0; b < kNB; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
   for (int k0 = 0; k0 < n; k0 += kTileK) {
 #pragma unroll
     for (int e = tid; e < kTileM * kTileK; e += kThreads) {
@@ -257,26 +276,26 @@ static __device__ void gemm_tile(int n, int r0, int c0, const double* __restrict
     __syncthreads();
 #pragma unroll
     for (int ks = 0; ks < kTileK; ks += 4) {
-      double af[2], bf[4];
+      double af[kMB], bf[kNB];
 #pragma unroll
-      for (int mb = 0; mb < 2; ++mb) af[mb] = sm.As[(wm * 16 + mb * 8 + g) * kAsStride + ks + q];
+      for (int mb = 0; mb < kMB; ++mb) af[mb] = sm.As[(wm * RW + mb * 8 + g) * kAsStride + ks + q];
 #pragma unroll
-      for (int nb = 0; nb < 4; ++nb) bf[nb] = sm.Bs[(ks + q) * kBsStride + wn * 32 + nb * 8 + g];
+      for (int nb = 0; nb < kNB; ++nb) bf[nb] = sm.Bs[(ks + q) * kBsStride + wn * CW + nb * 8 + g];
 #pragma unroll
-      for (int mb = 0; mb < 2; ++mb)
+      for (int mb = 0; mb < kMB; ++mb)
 #pragma unroll
-        for (int nb = 0; nb < 4; ++nb) dmma_8x8x4(acc[mb][nb][0], acc[mb][nb][1], af[mb], bf[nb]);
+        for (int nb = 0; nb < kNB; ++nb) dmma_8x8x4(acc[mb][nb][0], acc[mb][nb][1], af[mb], bf[nb]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int mb = 0; mb < 2; ++mb)
+  for (int mb = 0; mb < kMB; ++mb)
 #pragma unroll
-    for (int nb = 0; nb < 4; ++nb)
+    for (int nb = 0; nb < kNB; ++nb)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int gr = r0 + wm * 16 + mb * 8 + g;
-        const int gc = c0 + wn * 32 + nb * 8 + 2 * q + h;
+        const int gr = r0 + wm * RW + mb * 8 + g;
+        const int gc = c0 + wn * CW + nb * 8 + 2 * q + h;
         if (gr < n && gc < n) {
           const size_t idx = (size_t)gr * n + gc;
           double v = alpha * acc[mb][nb][h];
@@ -459,4 +478,4 @@ static __device__ int gj_inverse_block(double* __restrict__ W, int n, double* lo
   return status;
 }
 
-}  // namespace lg
+}  // namespace LG_NS

@@ -19,7 +19,7 @@
 #include "cta_linalg.cuh"
 #include "logm_internal.h"
 
-namespace lg {
+namespace LG_NS {
 
 // Table table_simple_experiment (Sec. 3): the k = 5 scheme fitted to
 // -log(1 - x). h_{j,i}, g_{j,i} for j = 2..5, i = 2..j+1 in that order.
@@ -831,4 +831,4 @@ static __device__ void run_backward(Ops& ops, const SmallParams& p, int b, int n
   if (ops.leader()) p.info[b] = 0;
 }
 
-}  // namespace lg
+}  // namespace LG_NS

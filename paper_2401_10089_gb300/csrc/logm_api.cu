@@ -11,6 +11,19 @@ namespace {
 
 constexpr double kThetaPaper[3] = {1.83e-8, 1.53e-4, 2.46e-1};  // Table Table_theta, k = 1, 2, 5
 
+// Kernel configuration per size bucket (logm_set_tuning).
+int g_variant[lg::kBuckets] = {0, 0, 0, 0, 0, 0};
+constexpr int kVariantMaxBucket[3] = {5, 3, 2};  // largest bucket each configuration serves
+
+size_t small_slots_bytes_all_variants(int count, int small_nmax) {
+  size_t m = lg::small_workspace_bytes(count, small_nmax);
+  const size_t m1 = lg_v1::small_workspace_bytes(count, small_nmax < 64 ? small_nmax : 64);
+  const size_t m2 = lg_v2::small_workspace_bytes(count, small_nmax < 32 ? small_nmax : 32);
+  if (m1 > m) m = m1;
+  if (m2 > m) m = m2;
+  return m;
+}
+
 int batch_n_max(const logm_batch* b) {
   if (!b) return -1;
   if (b->count < 0) return -1;
@@ -60,7 +73,7 @@ WsLayout ws_layout(const logm_batch* b, int precision) {
     L.large_nmax = n_max;
     if (ragged) L.small_nmax = lg::kSmallMaxN;
   }
-  L.small_bytes = L.small_nmax ? lg::small_workspace_bytes(b->count, L.small_nmax) : 0;
+  L.small_bytes = L.small_nmax ? small_slots_bytes_all_variants(b->count, L.small_nmax) : 0;
   L.large_off = round256(L.small_bytes);
   L.graph_off = round256(L.large_off + (L.large_nmax ? lg::large_workspace_bytes(L.large_nmax) : 0));
   L.total = L.graph_off + (precision != LOGM_PREC_FP64 ? graph_region_bytes(b, n_max) : 0);
@@ -124,8 +137,32 @@ int run_passes(lg::Mode mode, lg::SmallParams& p, const logm_batch* b, void* ws,
     q.order = reinterpret_cast<int32_t*>(w + 256);
     q.order_aux = q.order + b->count;
     q.slots = reinterpret_cast<double*>(w + 256 + ob);
-    q.n_slots = lg::small_kernel_slots(b->count);
-    if (lg::launch_small(mode, q, st) != cudaSuccess) return LOGM_ERR_CUDA;
+    // execute: one launch per kernel configuration, each taking the size
+    // buckets the tuning table gives it; other entry points: configuration 0
+    int mask[3] = {0, 0, 0};
+    const int top = lg::size_bucket(L.small_nmax);
+    for (int bk = 0; bk <= top; ++bk) mask[mode == lg::kModeExecute ? g_variant[bk] : 0] |= 1 << bk;
+    if (mask[0] == (1 << (top + 1)) - 1) mask[0] = 0;  // configuration 0 takes everything: no filter
+    for (int v = 2; v >= 0; --v) {
+      if (v > 0 && !mask[v]) continue;
+      if (v == 0 && !mask[0] && (mask[1] || mask[2])) continue;
+      lg::SmallParams r = q;
+      r.bucket_mask = mask[v];
+      cudaError_t e;
+      if (v == 0) {
+        r.n_slots = lg::small_kernel_slots(b->count);
+        e = lg::launch_small(mode, r, st);
+      } else if (v == 1) {
+        r.n_max = q.n_max < 64 ? q.n_max : 64;
+        r.n_slots = lg_v1::small_kernel_slots(b->count);
+        e = lg_v1::launch_small(mode, r, st);
+      } else {
+        r.n_max = q.n_max < 32 ? q.n_max : 32;
+        r.n_slots = lg_v2::small_kernel_slots(b->count);
+        e = lg_v2::launch_small(mode, r, st);
+      }
+      if (e != cudaSuccess) return LOGM_ERR_CUDA;
+    }
   }
   if (L.large_nmax) {
     lg::SmallParams q = p;
@@ -148,6 +185,25 @@ int check_ws(const logm_batch* b, void* ws, size_t ws_bytes, int precision = LOG
 extern "C" {
 
 int logm_version(void) { return 100; }
+
+int logm_set_tuning(const logm_tuning* t) {
+  if (!t) {
+    for (int b = 0; b < lg::kBuckets; ++b) g_variant[b] = 0;
+    return LOGM_SUCCESS;
+  }
+  for (int b = 0; b < lg::kBuckets; ++b) {
+    const int v = t->variant[b];
+    if (v < 0 || v > 2 || b > kVariantMaxBucket[v]) return LOGM_ERR_INVALID_ARG;
+  }
+  for (int b = 0; b < lg::kBuckets; ++b) g_variant[b] = t->variant[b];
+  return LOGM_SUCCESS;
+}
+
+int logm_get_tuning(logm_tuning* t) {
+  if (!t) return LOGM_ERR_INVALID_ARG;
+  for (int b = 0; b < lg::kBuckets; ++b) t->variant[b] = g_variant[b];
+  return LOGM_SUCCESS;
+}
 
 size_t logm_workspace_size(const logm_batch* batch, const logm_options* opts) {
   if (batch_n_max(batch) <= 0) return 0;

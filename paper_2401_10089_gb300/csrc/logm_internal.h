@@ -52,6 +52,7 @@ struct SmallParams {
   int n_slots;
   int precision;       // graph products (FP64 in this kernel family)
   int large_pass;      // 1: matrices with n > kSmallMaxN are left to the whole-GPU kernel
+  int bucket_mask;     // nonzero: only matrices whose size bucket bit is set (see size_bucket)
   float* gbuf;         // precision form: hand P_2, P_3 over in FP32 here and stop before the graph
   int gbuf_nmax;       // n stride of gbuf
 };
@@ -86,6 +87,13 @@ constexpr int kCtxLevels = 12;
 constexpr int kSmallMaxN = 256;  // largest n of the one-block-per-matrix kernels
 
 int small_kernel_slots(int count);
+
+// Size buckets of the one-block-per-matrix kernels: n <= 8, 16, 32, 64, 128, 256.
+constexpr int kBuckets = 6;
+constexpr int kBucketMaxN[kBuckets] = {8, 16, 32, 64, 128, 256};
+__host__ __device__ inline int size_bucket(int n) {
+  return n <= 8 ? 0 : (n <= 16 ? 1 : (n <= 32 ? 2 : (n <= 64 ? 3 : (n <= 128 ? 4 : 5))));
+}
 size_t large_workspace_bytes(int n_max);
 int large_grid_size();
 cudaError_t launch_large(Mode mode, const SmallParams& p, void* ws, cudaStream_t stream);
@@ -94,3 +102,19 @@ size_t small_order_bytes(int count);
 cudaError_t launch_small(Mode mode, const SmallParams& p, cudaStream_t stream);
 
 }  // namespace lg
+
+// The other configurations of the one-block-per-matrix kernel (same sources,
+// built in their own translation units): lg_v1 = 128 threads, n <= 64,
+// 32 x 32 DMMA tiles; lg_v2 = 64 threads, n <= 32, 32 x 32 tiles.
+namespace lg_v1 {
+constexpr int kVariantMaxN = 64;
+int small_kernel_slots(int count);
+size_t small_workspace_bytes(int count, int n_max);
+cudaError_t launch_small(lg::Mode mode, const lg::SmallParams& p, cudaStream_t stream);
+}  // namespace lg_v1
+namespace lg_v2 {
+constexpr int kVariantMaxN = 32;
+int small_kernel_slots(int count);
+size_t small_workspace_bytes(int count, int n_max);
+cudaError_t launch_small(lg::Mode mode, const lg::SmallParams& p, cudaStream_t stream);
+}  // namespace lg_v2

@@ -14,11 +14,11 @@
 #include <cmath>
 #include <cstdio>
 
+#include "logm_internal.h"
 #include "block_ops.cuh"
 #include "logm_algo.cuh"
-#include "logm_internal.h"
 
-namespace lg {
+namespace LG_NS {
 
 // ---------------------------------------------------------------------------
 // Queue order for execute: longest work first. The cost of a matrix grows
@@ -85,7 +85,7 @@ __global__ void k_order_scatter(SmallParams p) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 2) k_logm_small(SmallParams p) {
+__global__ void __launch_bounds__(kThreads, LG_MINBLOCKS) k_logm_small(SmallParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockSmem& S = *reinterpret_cast<BlockSmem*>(smem_raw);
   BlockOps ops{S};
@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_logm_small(SmallParams p) {
     int n;
     int64_t off;
     matrix_geometry(p, b, &n, &off);
+    if (p.bucket_mask && !((p.bucket_mask >> size_bucket(n)) & 1)) continue;  // another configuration's
     if (n > kMaxN && p.large_pass) continue;  // handled by the whole-GPU kernel
     if (n < 1 || n > kMaxN || n > p.n_max) {
       if (threadIdx.x == 0) {
@@ -158,7 +159,7 @@ static int sm_count() {
 }
 
 int small_kernel_slots(int count) {
-  const int per_sm = 2;  // blocks resident per SM (shared memory and registers)
+  const int per_sm = LG_MINBLOCKS;  // blocks resident per SM (shared memory and registers)
   const int cap = sm_count() * per_sm;
   return count < cap ? (count > 0 ? count : 1) : cap;
 }
@@ -217,4 +218,4 @@ cudaError_t launch_small(Mode mode, const SmallParams& p, cudaStream_t st) {
   return cudaErrorInvalidValue;
 }
 
-}  // namespace lg
+}  // namespace LG_NS

@@ -62,3 +62,45 @@ def test_execute_captured_in_cuda_graph():
         torch.cuda.synchronize()
         assert torch.equal(L_g.values, L_eager.values)
         assert torch.equal(s_g, s_e) and torch.equal(k_g, k_e) and torch.equal(i_g, i_e)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_kernel_configurations_agree_with_oracle(variant):
+    """Every configuration of the one-block-per-matrix kernel, forced on the
+    buckets it can serve, matches the FP64 oracle (1e-12)."""
+    sizes = (4, 8, 16, 32, 64, 128, 256)
+    vals, ns, offs = workloads.ragged_spd(140, sizes, seed=43, lo=0.05, hi=20.0, dtype=np.float64)
+    R = lg().Ragged(torch.tensor(vals, device="cuda"), torch.tensor(ns, device="cuda"),
+                    torch.tensor(offs, device="cuda"), 256)
+    max_bucket = {0: 5, 1: 3, 2: 2}[variant]
+    table = [variant if b <= max_bucket else 0 for b in range(6)]
+    old = lg().get_tuning()
+    try:
+        lg().set_tuning(table)
+        L, s, k, info = lg().logm_execute(R)
+    finally:
+        lg().set_tuning(old)
+    out = L.values.cpu().numpy()
+    assert (info.cpu().numpy() == 0).all()
+    for b in range(len(ns)):
+        n = int(ns[b])
+        A = vals[offs[b]:offs[b] + n * n].reshape(n, n)
+        Lr, d = oracle.logm(A)
+        if (d["s"], d["k"]) == (int(s[b]), int(k[b])):
+            assert rel(out[offs[b]:offs[b] + n * n].reshape(n, n), Lr) <= 1e-12, (variant, n)
+
+
+def test_autotuner_picks_a_valid_table():
+    from paper_2401_10089_gb300 import autotune
+    vals, ns, offs, R = ragged(600, seed=44)
+    old = lg().get_tuning()
+    try:
+        table, times = autotune.autotune(R, precision="fp64", sample=512, reps=1)
+        assert len(table) == 6
+        for b, v in enumerate(table):
+            assert v in autotune.CANDIDATES[b]
+        assert lg().get_tuning() == table
+        L, s, k, info = lg().logm_execute(R, precision="tf32x3")
+        assert (info.cpu().numpy() == 0).all()
+    finally:
+        lg().set_tuning(old)
