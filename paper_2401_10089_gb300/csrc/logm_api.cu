@@ -124,6 +124,39 @@ void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o)
   p.ctx_nmax = p.n_max;
 }
 
+// One launch per block configuration, each taking the size buckets the
+// tuning table gives it (execute and backward; the other entry points use
+// configuration 0 for every bucket).
+cudaError_t launch_small_variants(lg::Mode mode, const lg::SmallParams& q, int small_nmax, int count,
+                                  cudaStream_t st) {
+  const bool tuned = mode == lg::kModeExecute || mode == lg::kModeBackward;
+  int mask[3] = {0, 0, 0};
+  const int top = lg::size_bucket(small_nmax);
+  for (int bk = 0; bk <= top; ++bk) mask[tuned ? g_variant[bk] : 0] |= 1 << bk;
+  if (mask[0] == (1 << (top + 1)) - 1) mask[0] = 0;  // configuration 0 takes everything: no filter
+  for (int v = 2; v >= 0; --v) {
+    if (v > 0 && !mask[v]) continue;
+    if (v == 0 && !mask[0] && (mask[1] || mask[2])) continue;
+    lg::SmallParams r = q;
+    r.bucket_mask = mask[v];
+    cudaError_t e;
+    if (v == 0) {
+      r.n_slots = lg::small_kernel_slots(count);
+      e = lg::launch_small(mode, r, st);
+    } else if (v == 1) {
+      r.n_max = q.n_max < 64 ? q.n_max : 64;
+      r.n_slots = lg_v1::small_kernel_slots(count);
+      e = lg_v1::launch_small(mode, r, st);
+    } else {
+      r.n_max = q.n_max < 32 ? q.n_max : 32;
+      r.n_slots = lg_v2::small_kernel_slots(count);
+      e = lg_v2::launch_small(mode, r, st);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Launch the small pass and/or the large pass for this batch.
 int run_passes(lg::Mode mode, lg::SmallParams& p, const logm_batch* b, void* ws, cudaStream_t st) {
   const WsLayout L = ws_layout(b, LOGM_PREC_FP64);
@@ -137,32 +170,7 @@ int run_passes(lg::Mode mode, lg::SmallParams& p, const logm_batch* b, void* ws,
     q.order = reinterpret_cast<int32_t*>(w + 256);
     q.order_aux = q.order + b->count;
     q.slots = reinterpret_cast<double*>(w + 256 + ob);
-    // execute: one launch per kernel configuration, each taking the size
-    // buckets the tuning table gives it; other entry points: configuration 0
-    int mask[3] = {0, 0, 0};
-    const int top = lg::size_bucket(L.small_nmax);
-    for (int bk = 0; bk <= top; ++bk) mask[mode == lg::kModeExecute ? g_variant[bk] : 0] |= 1 << bk;
-    if (mask[0] == (1 << (top + 1)) - 1) mask[0] = 0;  // configuration 0 takes everything: no filter
-    for (int v = 2; v >= 0; --v) {
-      if (v > 0 && !mask[v]) continue;
-      if (v == 0 && !mask[0] && (mask[1] || mask[2])) continue;
-      lg::SmallParams r = q;
-      r.bucket_mask = mask[v];
-      cudaError_t e;
-      if (v == 0) {
-        r.n_slots = lg::small_kernel_slots(b->count);
-        e = lg::launch_small(mode, r, st);
-      } else if (v == 1) {
-        r.n_max = q.n_max < 64 ? q.n_max : 64;
-        r.n_slots = lg_v1::small_kernel_slots(b->count);
-        e = lg_v1::launch_small(mode, r, st);
-      } else {
-        r.n_max = q.n_max < 32 ? q.n_max : 32;
-        r.n_slots = lg_v2::small_kernel_slots(b->count);
-        e = lg_v2::launch_small(mode, r, st);
-      }
-      if (e != cudaSuccess) return LOGM_ERR_CUDA;
-    }
+    if (launch_small_variants(mode, q, L.small_nmax, b->count, st) != cudaSuccess) return LOGM_ERR_CUDA;
   }
   if (L.large_nmax) {
     lg::SmallParams q = p;
@@ -224,7 +232,10 @@ size_t logm_backward_workspace_size(const logm_batch* batch, const logm_options*
   (void)opts;
   const int n_max = batch_n_max(batch);
   if (n_max <= 0 || n_max > lg::kSmallMaxN) return 0;
-  return lg::small_bwd_workspace_bytes(batch->count, n_max);
+  size_t m = lg::small_bwd_workspace_bytes(batch->count, n_max);
+  const size_t m1 = lg_v1::small_bwd_workspace_bytes(batch->count, n_max < 64 ? n_max : 64);
+  const size_t m2 = lg_v2::small_bwd_workspace_bytes(batch->count, n_max < 32 ? n_max : 32);
+  return m > m1 ? (m > m2 ? m : m2) : (m1 > m2 ? m1 : m2);
 }
 
 int logm_plan(const logm_batch* batch, const logm_options* opts, const void* A, const void* AI2,
@@ -378,8 +389,8 @@ int logm_backward(const logm_batch* batch, const logm_options* opts, const void*
   char* w = static_cast<char*>(ws);
   p.queue = reinterpret_cast<int32_t*>(w);
   p.slots = reinterpret_cast<double*>(w + 256 + lg::small_order_bytes(batch->count));
-  p.n_slots = lg::small_kernel_slots(batch->count);
-  const cudaError_t e = lg::launch_small(lg::kModeBackward, p, static_cast<cudaStream_t>(stream));
+  const cudaError_t e =
+      launch_small_variants(lg::kModeBackward, p, n_max, batch->count, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? LOGM_SUCCESS : LOGM_ERR_CUDA;
 }
 

@@ -109,12 +109,14 @@ cudaError_t launch_small(Mode mode, const SmallParams& p, cudaStream_t stream);
 namespace lg_v1 {
 constexpr int kVariantMaxN = 64;
 int small_kernel_slots(int count);
+size_t small_bwd_workspace_bytes(int count, int n_max);
 size_t small_workspace_bytes(int count, int n_max);
 cudaError_t launch_small(lg::Mode mode, const lg::SmallParams& p, cudaStream_t stream);
 }  // namespace lg_v1
 namespace lg_v2 {
 constexpr int kVariantMaxN = 32;
 int small_kernel_slots(int count);
+size_t small_bwd_workspace_bytes(int count, int n_max);
 size_t small_workspace_bytes(int count, int n_max);
 cudaError_t launch_small(lg::Mode mode, const lg::SmallParams& p, cudaStream_t stream);
 }  // namespace lg_v2
