@@ -204,7 +204,7 @@ def main():
     import torch.distributed as dist
 
     import paper_2401_10089_gb300 as lg
-    from paper_2401_10089_gb300 import workloads
+    from paper_2401_10089_gb300 import shard, workloads
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -257,10 +257,7 @@ def main():
     ms_a = sum(ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(args.steps)) / args.steps
     ms_b = sum(ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(args.steps)) / args.steps
     clocks = clk.summary()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = shard.max_over_ranks(ms, device=dev)  # the slowest rank's step
 
     flops_a = algorithmic_flops(stats.cpu().numpy(), N)
     flops_b = algorithmic_flops(stats_b.cpu().numpy(), args.big_n) if big else 0.0
@@ -284,10 +281,7 @@ def main():
             LB_host.copy_(Lbo, non_blocking=True)
         torch.cuda.synchronize(dev)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps if e2e_steps else float("nan")
-    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(e2e_t.item())
+    e2e_ms = shard.max_over_ranks(e2e_ms, device=dev)
     h2d = A_host.numel() * 8 + (B_host.numel() * 8 if big else 0)
 
     # precision forms: the same step with the graph products in split precision
