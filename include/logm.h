@@ -192,7 +192,8 @@ int logm_execute_noalloc(const logm_batch* batch, const logm_options* opts, cons
  * used by logm_execute (batching form). Buckets: n <= 8, 16, 32, 64, 128, 256.
  * Variants: 0 = 256-thread blocks, 64 x 64 DMMA tiles, any n <= 256;
  *           1 = 128-thread blocks, 32 x 32 tiles, n <= 64 (buckets 0-3);
- *           2 = 64-thread blocks, 32 x 32 tiles, n <= 32 (buckets 0-2).
+ *           2 = 64-thread blocks, 32 x 32 tiles, n <= 32 (buckets 0-2);
+ *           3 = 256-thread blocks as 0, three per SM (registers capped), any n <= 256.
  * Smaller configurations keep more small matrices in flight per SM. The
  * project's autotuner (paper_2401_10089_gb300.autotune) times the candidates
  * on a sample of each bucket and writes the table it picks to JSON. */

@@ -270,7 +270,7 @@ def logm(A, k_max=5, max_sqrt=40, max_db_iter=50):
 def set_tuning(variants):
     """Per-size-bucket kernel configuration (buckets n <= 8, 16, 32, 64, 128, 256;
     0: 256-thread blocks, 1: 128-thread blocks for n <= 64, 2: 64-thread blocks
-    for n <= 32). ``None`` restores all-0."""
+    for n <= 32, 3: 256-thread blocks three per SM). ``None`` restores all-0."""
     L = _lib.load()
     if variants is None:
         _lib.check(L.logm_set_tuning(None), "logm_set_tuning")

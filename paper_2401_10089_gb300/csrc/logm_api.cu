@@ -13,14 +13,17 @@ constexpr double kThetaPaper[3] = {1.83e-8, 1.53e-4, 2.46e-1};  // Table Table_t
 
 // Kernel configuration per size bucket (logm_set_tuning).
 int g_variant[lg::kBuckets] = {0, 0, 0, 0, 0, 0};
-constexpr int kVariantMaxBucket[3] = {5, 3, 2};  // largest bucket each configuration serves
+constexpr int kVariants = 4;
+constexpr int kVariantMaxBucket[kVariants] = {5, 3, 2, 5};  // largest bucket each configuration serves
 
 size_t small_slots_bytes_all_variants(int count, int small_nmax) {
   size_t m = lg::small_workspace_bytes(count, small_nmax);
   const size_t m1 = lg_v1::small_workspace_bytes(count, small_nmax < 64 ? small_nmax : 64);
   const size_t m2 = lg_v2::small_workspace_bytes(count, small_nmax < 32 ? small_nmax : 32);
+  const size_t m3 = lg_v3::small_workspace_bytes(count, small_nmax);
   if (m1 > m) m = m1;
   if (m2 > m) m = m2;
+  if (m3 > m) m = m3;
   return m;
 }
 
@@ -130,13 +133,13 @@ void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o)
 cudaError_t launch_small_variants(lg::Mode mode, const lg::SmallParams& q, int small_nmax, int count,
                                   cudaStream_t st) {
   const bool tuned = mode == lg::kModeExecute || mode == lg::kModeBackward;
-  int mask[3] = {0, 0, 0};
+  int mask[kVariants] = {0, 0, 0, 0};
   const int top = lg::size_bucket(small_nmax);
   for (int bk = 0; bk <= top; ++bk) mask[tuned ? g_variant[bk] : 0] |= 1 << bk;
   if (mask[0] == (1 << (top + 1)) - 1) mask[0] = 0;  // configuration 0 takes everything: no filter
-  for (int v = 2; v >= 0; --v) {
+  for (int v = kVariants - 1; v >= 0; --v) {
     if (v > 0 && !mask[v]) continue;
-    if (v == 0 && !mask[0] && (mask[1] || mask[2])) continue;
+    if (v == 0 && !mask[0] && (mask[1] || mask[2] || mask[3])) continue;
     lg::SmallParams r = q;
     r.bucket_mask = mask[v];
     cudaError_t e;
@@ -147,10 +150,13 @@ cudaError_t launch_small_variants(lg::Mode mode, const lg::SmallParams& q, int s
       r.n_max = q.n_max < 64 ? q.n_max : 64;
       r.n_slots = lg_v1::small_kernel_slots(count);
       e = lg_v1::launch_small(mode, r, st);
-    } else {
+    } else if (v == 2) {
       r.n_max = q.n_max < 32 ? q.n_max : 32;
       r.n_slots = lg_v2::small_kernel_slots(count);
       e = lg_v2::launch_small(mode, r, st);
+    } else {
+      r.n_slots = lg_v3::small_kernel_slots(count);
+      e = lg_v3::launch_small(mode, r, st);
     }
     if (e != cudaSuccess) return e;
   }
@@ -201,7 +207,7 @@ int logm_set_tuning(const logm_tuning* t) {
   }
   for (int b = 0; b < lg::kBuckets; ++b) {
     const int v = t->variant[b];
-    if (v < 0 || v > 2 || b > kVariantMaxBucket[v]) return LOGM_ERR_INVALID_ARG;
+    if (v < 0 || v >= kVariants || b > kVariantMaxBucket[v]) return LOGM_ERR_INVALID_ARG;
   }
   for (int b = 0; b < lg::kBuckets; ++b) g_variant[b] = t->variant[b];
   return LOGM_SUCCESS;
@@ -235,7 +241,10 @@ size_t logm_backward_workspace_size(const logm_batch* batch, const logm_options*
   size_t m = lg::small_bwd_workspace_bytes(batch->count, n_max);
   const size_t m1 = lg_v1::small_bwd_workspace_bytes(batch->count, n_max < 64 ? n_max : 64);
   const size_t m2 = lg_v2::small_bwd_workspace_bytes(batch->count, n_max < 32 ? n_max : 32);
-  return m > m1 ? (m > m2 ? m : m2) : (m1 > m2 ? m1 : m2);
+  const size_t m3 = lg_v3::small_bwd_workspace_bytes(batch->count, n_max);
+  size_t r = m > m1 ? m : m1;
+  r = r > m2 ? r : m2;
+  return r > m3 ? r : m3;
 }
 
 int logm_plan(const logm_batch* batch, const logm_options* opts, const void* A, const void* AI2,

@@ -120,3 +120,10 @@ size_t small_bwd_workspace_bytes(int count, int n_max);
 size_t small_workspace_bytes(int count, int n_max);
 cudaError_t launch_small(lg::Mode mode, const lg::SmallParams& p, cudaStream_t stream);
 }  // namespace lg_v2
+namespace lg_v3 {
+constexpr int kVariantMaxN = 256;
+int small_kernel_slots(int count);
+size_t small_bwd_workspace_bytes(int count, int n_max);
+size_t small_workspace_bytes(int count, int n_max);
+cudaError_t launch_small(lg::Mode mode, const lg::SmallParams& p, cudaStream_t stream);
+}  // namespace lg_v3
