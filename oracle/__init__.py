@@ -10,15 +10,18 @@ this module only marshals numpy arrays. Each function cites the part of the
 paper it follows:
 
 * ``graph_eval``   -- degree-optimal form, eq. (five_mult_degopt), Sec. 3, with
-                      Table table_simple_experiment for k = 5 and the exact
-                      Taylor polynomials of eq. (Taylor_log) for k = 1, 2.
-* ``sqrtm_db``     -- scaled Denman-Beavers iteration, eq. (ScalDB), Sec. 6.
+                      Table table_simple_experiment for k = 5, the exact
+                      Taylor polynomials of eq. (Taylor_log) for k = 1, 2 and
+                      T_8 by eq. (eqP8pol) for k = 3 (``coeffs_k3``).
+* ``sqrtm_db``     -- scaled Denman-Beavers iteration, eq. (ScalDB), Sec. 6, or
+                      its product form (``form=1``, the variant cited in Sec. 2).
+* ``balance``      -- the diagonal balancing T of Algorithm 1, Step 1.
 * ``normest_pow``  -- 1-norm power estimate (Higham 1988, cited in Sec. 6),
                       with A_I2 of eq. (AI2) for even powers.
 * ``plan``         -- one pass of Algorithm 1's loop test (eqs. alphaapprox,
                       normAm9, alpha2term1, normAm9plus1) and the order search
                       (eqs. min_in, min_inp, roughmax_even).
-* ``logm``         -- Algorithm 1 with T = I.
+* ``logm``         -- Algorithm 1 (T = I unless ``balance=1``).
 * ``expm_taylor``, ``frechet_adjoint``, ``horner`` -- independent checks.
 """
 from __future__ import annotations
@@ -38,8 +41,12 @@ _LIB_PATH = os.path.join(_BUILD, "liblogm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-# Theta_{m_k} of Table Table_theta (Sec. 5) for k = 1, 2, 5.
-THETA_TABLE = (1.83e-8, 1.53e-4, 2.46e-1)
+# Theta_{m_k} of Table Table_theta (Sec. 5) for k = 1..5.
+THETA_TABLE = (1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1)
+# Orders with coefficients: T_2, T_4 (eq. Taylor_log), T_8 (eq. eqP8pol) and
+# Table table_simple_experiment.
+AVAILABLE_K = (1, 2, 3, 5)
+M_OF_K = {1: 2, 2: 4, 3: 8, 5: 14}
 # Status codes, written out on their own (same meanings as the library's).
 OK, SINGULAR, NO_CONVERGENCE, MAX_SQRT, NONFINITE = 0, 1, 2, 3, 4
 
@@ -51,8 +58,10 @@ class Opts(ctypes.Structure):
         ("max_db_iter", ctypes.c_int32),
         ("force_s", ctypes.c_int32),
         ("force_k", ctypes.c_int32),
+        ("db_form", ctypes.c_int32),
+        ("balance", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
-        ("theta", ctypes.c_double * 3),
+        ("theta", ctypes.c_double * 5),
     ]
 
 
@@ -101,6 +110,9 @@ def lib():
             L.orc_lu.argtypes = [i, p, p]
             L.orc_inverse.argtypes = [i, p, p, p]
             L.orc_sqrtm_db.argtypes = [i, p, p, i, p]
+            L.orc_sqrtm_db_product.argtypes = [i, p, p, i, p]
+            L.orc_balance.argtypes = [i, p, p]
+            L.orc_coeffs_k3.argtypes = [p]
             L.orc_graph_eval.argtypes = [i, i, p, p, p]
             L.orc_horner.argtypes = [i, i, p, p, p]
             L.orc_plan.argtypes = [i, p, p, p, p, p, p]
@@ -121,14 +133,31 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-def make_opts(k_max=5, max_sqrt=40, max_db_iter=50, force_s=-1, force_k=0, theta=None) -> Opts:
+def make_opts(k_max=5, max_sqrt=40, max_db_iter=50, force_s=-1, force_k=0, theta=None,
+              db_form=0, balance=0) -> Opts:
     o = Opts()
     o.k_max, o.max_sqrt, o.max_db_iter = k_max, max_sqrt, max_db_iter
     o.force_s, o.force_k = force_s, force_k
+    o.db_form, o.balance = db_form, balance
     th = THETA_TABLE if theta is None else theta
-    for t in range(3):
+    for t in range(5):
         o.theta[t] = th[t]
     return o
+
+
+def coeffs_k3():
+    """c3, c4, d1, d2, e2, e0 of eq. (eqP8pol) for T_8 (closed form)."""
+    c = np.zeros(6)
+    lib().orc_coeffs_k3(_ptr(c))
+    return c
+
+
+def balance(A):
+    """(T^{-1} A T, diag(T)) by the radix-2 Parlett-Reinsch balancing."""
+    B = _c(A).copy()
+    d = np.empty(B.shape[0])
+    lib().orc_balance(B.shape[0], _ptr(B), _ptr(d))
+    return B, d
 
 
 def coeffs_k5():
@@ -160,12 +189,14 @@ def inverse(A):
     return Ai, ld.value, st
 
 
-def sqrtm_db(A, max_iter=50):
-    """(A^{1/2}, iterations, status) by eq. (ScalDB)."""
+def sqrtm_db(A, max_iter=50, form=0):
+    """(A^{1/2}, iterations, status) by eq. (ScalDB) (form 0) or its product
+    form (form 1)."""
     A = _c(A)
     X = np.empty_like(A)
     it = ctypes.c_int32()
-    st = lib().orc_sqrtm_db(A.shape[0], _ptr(A), _ptr(X), max_iter, ctypes.byref(it))
+    f = lib().orc_sqrtm_db_product if form == 1 else lib().orc_sqrtm_db
+    st = f(A.shape[0], _ptr(A), _ptr(X), max_iter, ctypes.byref(it))
     return X, it.value, st
 
 

@@ -27,8 +27,15 @@
  *    change of X in the 1-norm is <= 10 sqrt(n) u, or, once scaling is off
  *    and the change has reached 1e-7, when it no longer halves; scaling by
  *    mu is switched off once the change drops below 1e-2;
- *  - only k = 1, 2 (exact Taylor, eq. Taylor_log) and k = 5 (Table
- *    table_simple_experiment) have coefficients, so k_max <= 5.
+ *  - k = 1, 2 are the exact Taylor polynomials T_2, T_4 (eq. Taylor_log);
+ *    k = 3 is T_8 evaluated with three products by eq. (eqP8pol), its
+ *    coefficients solved here in closed form; k = 5 is Table
+ *    table_simple_experiment. k = 4 and k >= 6 have no coefficients in the
+ *    paper, so the available orders are k in {1, 2, 3, 5};
+ *  - the balancing T of Algorithm 1 (optional) is diagonal scaling by powers
+ *    of 2 (the Parlett-Reinsch iteration with 1-norms of the off-diagonal
+ *    parts of rows and columns, no permutations), so that T^{-1} A T and
+ *    T L T^{-1} are exact.
  */
 #include "logm_oracle.h"
 
@@ -42,7 +49,7 @@
 
 #define ORC_U 0x1p-53 /* unit roundoff of IEEE binary64 */
 
-int orc_version(void) { return 1; }
+int orc_version(void) { return 2; }
 
 /* ------------------------------------------------------------------------ */
 /* Coefficients of the degree-optimal form, eq. (five_mult_degopt).         */
@@ -77,6 +84,40 @@ void orc_coeffs_k5(double* h, double* g, double* y) {
   memcpy(y, K5_Y, sizeof(K5_Y));
 }
 
+/* k = 3: T_8 of eq. (Taylor_log) with three products, eq. (eqP8pol):
+ *   y02 = X^2 (c4 X^2 + c3 X),
+ *   z   = (y02 + d2 X^2 + d1 X)(y02 + e2 X^2) + e0 y02 + X^2/2 + X
+ * (f2 = 1, f1 = 1, f0 = 0 for -log(1 - x)). Matching x^8..x^3 of the
+ * expansion with 1/8..1/3 gives, top down,
+ *   c4^2 = 1/8, 2 c3 c4 = 1/7, c3^2 + c4 (d2 + e2) = 1/6,
+ *   c3 (d2 + e2) + c4 d1 = 1/5, d2 e2 + c3 d1 + c4 e0 = 1/4,
+ *   d1 e2 + c3 e0 = 1/3,
+ * so with S = d2 + e2 and e0 = (1/3 - d1 e2)/c3, e2 solves the quadratic
+ *   e2^2 - (S - c4 d1/c3) e2 - (c3 d1 + c4/(3 c3) - 1/4) = 0.
+ * Of its two roots (the other sign of c4 gives the same pair, negated) the
+ * one taken, e2 = (beta + sqrt(beta^2 + 4 gamma))/2, has the smaller
+ * coefficients and the smaller rounding indicator of eq. (stability_error):
+ * its monomials, expanded from the rounded coefficients, match 1/i within
+ * 1.3 u, the other root's within 2.7 u.
+ * c[0..5] = c3, c4, d1, d2, e2, e0. */
+void orc_coeffs_k3(double* c) {
+  const double c4 = 1.0 / sqrt(8.0);
+  const double c3 = 1.0 / (14.0 * c4);
+  const double S = (1.0 / 6.0 - c3 * c3) / c4;
+  const double d1 = (1.0 / 5.0 - c3 * S) / c4;
+  const double beta = S - c4 * d1 / c3;
+  const double gamma = c3 * d1 + c4 / (3.0 * c3) - 0.25;
+  const double e2 = 0.5 * (beta + sqrt(beta * beta + 4.0 * gamma));
+  const double d2 = S - e2;
+  const double e0 = (1.0 / 3.0 - d1 * e2) / c3;
+  c[0] = c3;
+  c[1] = c4;
+  c[2] = d1;
+  c[3] = d2;
+  c[4] = e2;
+  c[5] = e0;
+}
+
 /* A degree-optimal scheme with k products: P_1 = I, P_2 = X and, for
  * j = 1..k, P_{j+2} = (sum_{i=1}^{j+1} h_{j,i} P_i)(sum_{i=1}^{j+1} g_{j,i} P_i);
  * z = sum_{i=1}^{k+2} y_i P_i (eq. five_mult_degopt). Indices are 1-based in
@@ -106,6 +147,24 @@ static void scheme_for(int k, orc_scheme* S) {
     S->y[2] = 1.0;
     S->y[3] = 0.5;
     S->y[4] = 1.0;
+  } else if (k == 3) {
+    /* eq. (eqP8pol) in the degree-optimal form: P_4 = P_3 (c3 P_2 + c4 P_3),
+     * P_5 = (d1 P_2 + d2 P_3 + P_4)(e2 P_3 + P_4),
+     * z = P_2 + P_3/2 + e0 P_4 + P_5. */
+    double c[6];
+    orc_coeffs_k3(c);
+    S->h[2][3] = 1.0;
+    S->g[2][2] = c[0];
+    S->g[2][3] = c[1];
+    S->h[3][2] = c[2];
+    S->h[3][3] = c[3];
+    S->h[3][4] = 1.0;
+    S->g[3][3] = c[4];
+    S->g[3][4] = 1.0;
+    S->y[2] = 1.0;
+    S->y[3] = 0.5;
+    S->y[4] = c[5];
+    S->y[5] = 1.0;
   } else if (k == 5) {
     int t = 0;
     for (int j = 2; j <= 5; ++j)
@@ -118,9 +177,11 @@ static void scheme_for(int k, orc_scheme* S) {
 }
 
 /* m_k of Table Table_theta for the schemes that have coefficients. */
-static int m_of_k(int k) { return k == 1 ? 2 : (k == 2 ? 4 : 14); }
+static int m_of_k(int k) { return k == 1 ? 2 : (k == 2 ? 4 : (k == 3 ? 8 : 14)); }
 
-static int theta_index(int k) { return k == 1 ? 0 : (k == 2 ? 1 : 2); }
+static int theta_index(int k) { return k - 1; }
+
+static int k_available(int k) { return k == 1 || k == 2 || k == 3 || k == 5; }
 
 /* ------------------------------------------------------------------------ */
 /* Dense linear algebra, textbook forms.                                    */
@@ -295,6 +356,120 @@ int orc_sqrtm_db(int n, const double* A, double* Xout, int max_iter, int32_t* it
 }
 
 /* ------------------------------------------------------------------------ */
+/* Product form of the scaled Denman-Beavers iteration (the variant the     */
+/* paper cites in Sec. 2 for the square roots of the inverse scaling and    */
+/* squaring method). With M_k = X_k Y_k of eq. (ScalDB):                    */
+/*   M_{k+1} = I/2 + (mu_k^2 M_k + mu_k^{-2} M_k^{-1})/4,                   */
+/*   X_{k+1} = (mu_k X_k + mu_k^{-1} X_k M_k^{-1})/2,                       */
+/* M_0 = X_0 = A, mu_k = |det M_k|^{-1/(2n)} (= |det X_k det Y_k|^{-1/(2n)}). */
+/* The iterates X_k are those of eq. (ScalDB) in exact arithmetic; each     */
+/* step takes one inversion and one product instead of two inversions (the  */
+/* first takes no product: X_0 M_0^{-1} = I). Same stop rule.               */
+/* ------------------------------------------------------------------------ */
+int orc_sqrtm_db_product(int n, const double* A, double* Xout, int max_iter, int32_t* iters) {
+  double* X = alloc_mat(n);
+  double* M = alloc_mat(n);
+  double* Mi = alloc_mat(n);
+  double* XMi = alloc_mat(n);
+  double* Xn = alloc_mat(n);
+  double* D = alloc_mat(n);
+  const size_t nn = (size_t)n * n;
+  memcpy(X, A, sizeof(double) * nn);
+  memcpy(M, A, sizeof(double) * nn);
+  const double tol = 10.0 * sqrt((double)n) * ORC_U;
+  int scale = 1, status = ORC_NO_CONVERGENCE, it = 0;
+  double dprev = INFINITY;
+  for (it = 1; it <= max_iter; ++it) {
+    double ldm;
+    if (orc_inverse(n, M, Mi, &ldm) != ORC_OK) {
+      status = ORC_SINGULAR;
+      break;
+    }
+    double mu = scale ? exp(-ldm / (2.0 * n)) : 1.0;
+    if (it == 1)
+      set_identity(n, XMi);
+    else
+      orc_gemm(n, X, Mi, XMi);
+    for (size_t t = 0; t < nn; ++t) {
+      Xn[t] = 0.5 * (mu * X[t] + XMi[t] / mu);
+      M[t] = 0.25 * (mu * mu * M[t] + Mi[t] / (mu * mu));
+      D[t] = Xn[t] - X[t];
+    }
+    for (int i = 0; i < n; ++i) M[(size_t)i * n + i] += 0.5;
+    double delta = orc_norm1(n, D) / orc_norm1(n, Xn);
+    memcpy(X, Xn, sizeof(double) * nn);
+    if (!(delta == delta)) {
+      status = ORC_NO_CONVERGENCE;
+      break;
+    }
+    if (delta <= tol) {
+      status = ORC_OK;
+      break;
+    }
+    if (!scale && dprev <= 1e-7 && delta > 0.5 * dprev) {
+      status = ORC_OK;
+      break;
+    }
+    if (delta < 1e-2) scale = 0;
+    dprev = delta;
+  }
+  if (iters) *iters = it > max_iter ? max_iter : it;
+  memcpy(Xout, X, sizeof(double) * nn);
+  free(X);
+  free(M);
+  free(Mi);
+  free(XMi);
+  free(Xn);
+  free(D);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Balancing, the preprocessing step T^{-1} A T of Algorithm 1 (T diagonal).*/
+/* Parlett-Reinsch iteration, radix 2: for each i in turn, with c and r the */
+/* 1-norms of the off-diagonal parts of column i and row i, find the power  */
+/* of two f that brings c f and r / f closest to balance (c f^2 within a    */
+/* factor 4 of r) and apply it (column i times f, row i divided by f) when  */
+/* it cuts c + r by more than 5 %; sweep until a sweep applies nothing (at  */
+/* most 100 sweeps). Zero rows or columns are left alone. d gets T's        */
+/* diagonal; A is overwritten by T^{-1} A T. Every factor is a power of two,*/
+/* so the scaling and its undoing are exact.                                */
+/* ------------------------------------------------------------------------ */
+void orc_balance(int n, double* A, double* d) {
+  for (int i = 0; i < n; ++i) d[i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    int changed = 0;
+    for (int i = 0; i < n; ++i) {
+      double c = 0.0, r = 0.0;
+      for (int j = 0; j < n; ++j)
+        if (j != i) {
+          c += fabs(A[(size_t)j * n + i]);
+          r += fabs(A[(size_t)i * n + j]);
+        }
+      if (c == 0.0 || r == 0.0) continue;
+      const double s = c + r;
+      double f = 1.0, g = r / 2.0;
+      while (c < g) {
+        f *= 2.0;
+        c *= 4.0;
+      }
+      g = r * 2.0;
+      while (c >= g) {
+        f /= 2.0;
+        c /= 4.0;
+      }
+      if ((c + r) / f < 0.95 * s) {
+        changed = 1;
+        d[i] *= f;
+        for (int j = 0; j < n; ++j) A[(size_t)i * n + j] /= f;
+        for (int j = 0; j < n; ++j) A[(size_t)j * n + i] *= f;
+      }
+    }
+    if (!changed) break;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* 1-norm estimate of M = B^p (Higham 1988, cited in Sec. 6).               */
 /* With A_I2 = B^2 given (eq. AI2), M = B^{p mod 2} (A_I2)^{p div 2}, which */
 /* needs fewer matrix-vector products (Sec. 6, item 2).                     */
@@ -413,7 +588,7 @@ double orc_normest_pow(int n, const double* B, const double* AI2, int p) {
  * formed by one product) or the caller's X^2 (Algorithm 1 saves that
  * product with A_I2 when s >= 1). Returns 0, or -1 for an unsupported k. */
 int orc_graph_eval(int n, int k, const double* X, const double* P3, double* Z) {
-  if (k != 1 && k != 2 && k != 5) return -1;
+  if (!k_available(k)) return -1;
   orc_scheme S;
   scheme_for(k, &S);
   const size_t nn = (size_t)n * n;
@@ -531,9 +706,9 @@ static int alpha_test(int n, const double* B, const double* AI2, double nB, doub
  *  k+1 at once when alpha_{m_k} > Theta_k but <= Theta_{k+1}. */
 static int order_search(int n, const double* B, const double* AI2, double nB, double nI2,
                         const orc_opts* o, const est_state* loop_est, int* n_est) {
-  int cands[3], nc = 0;
-  const int all[3] = {1, 2, 5};
-  for (int t = 0; t < 3; ++t)
+  int cands[4], nc = 0;
+  const int all[4] = {1, 2, 3, 5};
+  for (int t = 0; t < 4; ++t)
     if (all[t] <= o->k_max) cands[nc++] = all[t];
   if (nc == 0) return o->k_max;
   /* min_im */
@@ -632,9 +807,30 @@ int orc_plan(int n, const double* A, const double* AI2in, const orc_opts* o, int
 }
 
 /* ------------------------------------------------------------------------ */
-/* Algorithm 1 with T = I (no balancing).                                   */
+/* Algorithm 1. With o->balance, the preprocessing A <- T^{-1} A T and the   */
+/* postprocessing L <- T L T^{-1} of Steps 1 and 'Step_Postproc' use the    */
+/* balancing above; otherwise T = I.                                        */
 /* ------------------------------------------------------------------------ */
+static int logm_core(int n, const double* A, double* L, const orc_opts* o, orc_diag* d);
+
 int orc_logm(int n, const double* A, double* L, const orc_opts* o, orc_diag* d) {
+  if (!o->balance) return logm_core(n, A, L, o, d);
+  const size_t nn = (size_t)n * n;
+  for (size_t t = 0; t < nn; ++t)
+    if (!isfinite(A[t])) return logm_core(n, A, L, o, d);
+  double* Ab = alloc_mat(n);
+  double* dg = (double*)malloc(sizeof(double) * (size_t)n);
+  memcpy(Ab, A, sizeof(double) * nn);
+  orc_balance(n, Ab, dg);
+  int r = logm_core(n, Ab, L, o, d);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) L[(size_t)i * n + j] = L[(size_t)i * n + j] * dg[i] / dg[j];
+  free(Ab);
+  free(dg);
+  return r;
+}
+
+static int logm_core(int n, const double* A, double* L, const orc_opts* o, orc_diag* d) {
   const size_t nn = (size_t)n * n;
   orc_diag dd;
   memset(&dd, 0, sizeof(dd));
@@ -676,7 +872,8 @@ int orc_logm(int n, const double* A, double* L, const orc_opts* o, orc_diag* d) 
     /* A_2 <- A; A <- A^{1/2} by eq. (ScalDB); A_I2 = A_2 - 2A + I (eq. AI2). */
     memcpy(A2, Acur, sizeof(double) * nn);
     int32_t it = 0;
-    int r = orc_sqrtm_db(n, A2, Acur, o->max_db_iter, &it);
+    int r = o->db_form == 1 ? orc_sqrtm_db_product(n, A2, Acur, o->max_db_iter, &it)
+                            : orc_sqrtm_db(n, A2, Acur, o->max_db_iter, &it);
     dd.db_iters += it;
     if (r == ORC_SINGULAR) {
       info = ORC_SINGULAR;

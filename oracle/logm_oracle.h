@@ -27,13 +27,15 @@ enum {
 };
 
 typedef struct {
-  int32_t k_max;       /* largest number of graph products: 1, 2 or 5 */
+  int32_t k_max;       /* largest number of graph products: 1, 2, 3 or 5 */
   int32_t max_sqrt;    /* maxiter of Algorithm 1 */
   int32_t max_db_iter; /* cap on Denman-Beavers iterations per square root */
   int32_t force_s;     /* < 0: choose s by the bound; >= 0: take exactly s roots */
   int32_t force_k;     /* <= 0: order search; else evaluate with this k */
+  int32_t db_form;     /* 0: eq. (ScalDB), two inversions; 1: product form */
+  int32_t balance;     /* 0: T = I; 1: diagonal balancing (Algorithm 1, Step 1) */
   int32_t reserved;
-  double theta[3];     /* Theta for k = 1, 2, 5 (Table Table_theta) */
+  double theta[5];     /* Theta_{m_k} for k = 1..5 (Table Table_theta); k = 4 unused */
 } orc_opts;
 
 typedef struct {
@@ -55,11 +57,17 @@ int orc_version(void);
  * y[7] = y_1..y_7. */
 void orc_coeffs_k5(double* h, double* g, double* y);
 
+/* k = 3 coefficients of eq. (eqP8pol), solved in closed form:
+ * c[6] = c3, c4, d1, d2, e2, e0. */
+void orc_coeffs_k3(double* c);
+
 void orc_gemm(int n, const double* A, const double* B, double* C);
 double orc_norm1(int n, const double* A);
 int orc_lu(int n, double* LU, int32_t* piv);
 int orc_inverse(int n, const double* A, double* Ainv, double* logabsdet);
 int orc_sqrtm_db(int n, const double* A, double* X, int max_iter, int32_t* iters);
+int orc_sqrtm_db_product(int n, const double* A, double* X, int max_iter, int32_t* iters);
+void orc_balance(int n, double* A, double* d);
 double orc_normest_pow(int n, const double* B, const double* AI2, int p);
 int orc_graph_eval(int n, int k, const double* X, const double* P3, double* Z);
 void orc_horner(int n, int deg, const double* b, const double* X, double* Z);

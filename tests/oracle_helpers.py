@@ -40,6 +40,23 @@ def k5_monomials(h, g, y):
     return z
 
 
+def k3_monomials(c):
+    """Monomials b_0..b_8 of eq. (eqP8pol) with c = (c3, c4, d1, d2, e2, e0)
+    given as doubles, in exact rational arithmetic:
+    y02 = x^2 (c4 x^2 + c3 x), z = (y02 + d2 x^2 + d1 x)(y02 + e2 x^2)
+    + e0 y02 + x^2/2 + x."""
+    c3, c4, d1, d2, e2, e0 = (Fraction(float(v)) for v in c)
+    x = [Fraction(0), Fraction(1)]
+    x2 = _mul(x, x)
+    y02 = _mul(x2, _add([c4 * t for t in x2], [c3 * t for t in x]))
+    left = _add(_add(y02, [d2 * t for t in x2]), [d1 * t for t in x])
+    right = _add(y02, [e2 * t for t in x2])
+    z = _mul(left, right)
+    z = _add(z, [e0 * t for t in y02])
+    z = _add(z, [Fraction(1, 2) * t for t in x2])
+    return _add(z, x)
+
+
 def read_golden_coeffs(path):
     vals = {}
     with open(path) as f:

@@ -14,7 +14,8 @@ import scipy.linalg as sla
 
 import oracle
 from paper_2401_10089_gb300 import workloads
-from tests.oracle_helpers import k5_monomials, read_golden_coeffs, theta_from_monomials
+from tests.oracle_helpers import (k3_monomials, k5_monomials, read_golden_coeffs,
+                                  theta_from_monomials)
 
 U = 2.0 ** -53
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -67,13 +68,31 @@ def test_theta_recomputed_from_backward_error():
     z = k5_monomials(*oracle.coeffs_k5())
     got = theta_from_monomials(z, 14)
     assert 0.2440 < got < 0.2455
+    # k = 3 from the oracle's rounded eq. (eqP8pol) coefficients: the table's value.
+    got = theta_from_monomials(k3_monomials(oracle.coeffs_k3()), 8)
+    assert float(f"{got:.2e}") == table[3][1]
+
+
+def test_k3_coefficients_give_taylor_t8():
+    # eq. (eqP8pol) with the closed-form coefficients, expanded exactly from
+    # their doubles, is T_8 of eq. (Taylor_log): b_0 = 0, b_i = 1/i within
+    # 2.5 u (the rounding of the coefficients; b_8 = c4^2), degree exactly 8.
+    from fractions import Fraction
+    z = k3_monomials(oracle.coeffs_k3())
+    assert len(z) == 9 and z[0] == 0
+    for i in range(1, 9):
+        assert abs(float(z[i] * i - 1)) <= 2.5 * U, (i, float(z[i] * i - 1) / U)
+    # the chosen root: the smaller coefficients (|e0| < 1) of the two
+    c = oracle.coeffs_k3()
+    assert c[1] == pytest.approx(1 / math.sqrt(8), rel=1e-15) and abs(c[5]) < 1
+    assert Fraction(float(c[1])) ** 2 == pytest.approx(Fraction(1, 8), rel=1e-15)
 
 
 # --------------------------------------------------------------------------
 # Graph evaluation, eq. (five_mult_degopt)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("k", [1, 2, 5])
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
 def test_graph_scalar_against_log(k):
     xs = np.linspace(-0.25, 0.25, 101)
     for x in xs:
@@ -82,6 +101,8 @@ def test_graph_scalar_against_log(k):
             ref = x + x * x / 2
         elif k == 2:
             ref = x + x * x / 2 + x ** 3 / 3 + x ** 4 / 4
+        elif k == 3:
+            ref = sum(x ** i / i for i in range(1, 9))
         else:
             ref = -math.log1p(-x)  # Fig. 1: error about u on the disk of radius ~0.25
         tol = 8 * U * max(abs(ref), 1e-300) if k == 5 else 4 * U * abs(ref) + 1e-300
@@ -99,16 +120,19 @@ def test_graph_k5_vs_horner():
     assert rel(G, H) < 1e-14
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3])
 def test_graph_taylor_matrix(k):
     rng = np.random.default_rng(11)
     X = rng.standard_normal((9, 9)) * 0.05
     X2 = X @ X
-    ref = X + X2 / 2 if k == 1 else X + X2 / 2 + X2 @ X / 3 + X2 @ X2 / 4
+    if k == 3:  # T_8 by Horner with b_i = 1/i
+        ref = oracle.horner(X, np.array([0.0] + [1.0 / i for i in range(1, 9)]))
+    else:
+        ref = X + X2 / 2 if k == 1 else X + X2 / 2 + X2 @ X / 3 + X2 @ X2 / 4
     assert rel(oracle.graph_eval(X, k), ref) < 1e-15
 
 
-@pytest.mark.parametrize("k", [1, 2, 5])
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
 def test_graph_p3_argument_and_diagonal(k):
     rng = np.random.default_rng(12)
     X = rng.standard_normal((7, 7)) * 0.03
@@ -163,6 +187,31 @@ def test_sqrt_dense():
     assert rel(X, sla.sqrtm(A).real) < 1e-13
 
 
+def test_sqrt_product_form_closed_forms():
+    lam = np.array([0.01, 0.5, 3.0, 100.0])
+    X, it, st = oracle.sqrtm_db(np.diag(lam), form=1)
+    assert st == oracle.OK and np.allclose(X, np.diag(np.sqrt(lam)), rtol=1e-14, atol=1e-16)
+    r, th = 2.5, 2.0
+    R = r * np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    X, it, st = oracle.sqrtm_db(R, form=1)
+    ref = math.sqrt(r) * np.array([[math.cos(th / 2), -math.sin(th / 2)], [math.sin(th / 2), math.cos(th / 2)]])
+    assert st == oracle.OK and rel(X, ref) < 1e-14
+
+
+def test_sqrt_product_form_matches_two_inverse_form():
+    # M_k = X_k Y_k turns eq. (ScalDB) into the product form: same iterates,
+    # same mu_k, so the same number of steps and the same root to rounding.
+    mats = [workloads.dense_32(), workloads.triangular_similar(40, seed=21)]
+    mats += list(workloads.identity_plus(3, 20, seed=22))
+    mats += list(workloads.spd(2, 24, seed=23, lo=1e-3, hi=1e3))
+    for A in mats:
+        X0, it0, st0 = oracle.sqrtm_db(A)
+        X1, it1, st1 = oracle.sqrtm_db(A, form=1)
+        assert st0 == st1 == oracle.OK and abs(it0 - it1) <= 1
+        assert rel(X1 @ X1, A) < 1e-13
+        assert rel(X1, X0) < 1e-12
+
+
 # --------------------------------------------------------------------------
 # 1-norm power estimator (Higham 1988)
 # --------------------------------------------------------------------------
@@ -207,17 +256,18 @@ def test_normest_lower_bound_and_quality():
 def _expected_plan_diagonal(lam, theta=oracle.THETA_TABLE):
     s = 0
     mu = np.array(lam, dtype=float)
-    while np.max(np.abs(mu - 1)) > theta[2]:
+    while np.max(np.abs(mu - 1)) > theta[4]:
         mu = np.sqrt(mu)
         s += 1
     a = np.max(np.abs(mu - 1))
-    k = 1 if a <= theta[0] else (2 if a <= theta[1] else 5)
+    k = next(k for k in oracle.AVAILABLE_K if a <= theta[k - 1])
     return s, k
 
 
 @pytest.mark.parametrize("lam", [
     [1.0 + 1e-9, 1.0 - 5e-9],
     [1.0 + 1e-5, 0.99999],
+    [1.004, 0.993, 1.0],
     [1.1, 0.95, 1.2],
     [3.0, 0.2, 1.0],
     [100.0, 0.01],
@@ -294,6 +344,89 @@ def test_logm_forced_plan_reproduces():
     # one root more or one less still gives log A to high accuracy
     Lp, _ = oracle.logm(A, force_s=d["s"] + 1, force_k=5)
     assert rel(Lp, L) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# Balancing, Algorithm 1 Steps 1 and 'Step_Postproc' (T diagonal, powers of 2)
+# --------------------------------------------------------------------------
+
+def test_balance_hand_example():
+    # [[1, 1e4], [1e-4, 1]]: i = 0 has c = 1e-4, r = 1e4; the power of two with
+    # c f^2 in [r/4, r) is f = 2^13 = 8192; then i = 1 (c = 1e4/8192, r =
+    # 8192e-4) and a second sweep change nothing.
+    A = np.array([[1.0, 1e4], [1e-4, 1.0]])
+    B, d = oracle.balance(A)
+    assert np.array_equal(d, [8192.0, 1.0])
+    assert np.array_equal(B, [[1.0, 1e4 / 8192], [1e-4 * 8192, 1.0]])
+
+
+def test_balance_exact_similarity_and_idempotent():
+    rng = np.random.default_rng(50)
+    for n in (3, 10, 31):
+        A0 = rng.standard_normal((n, n))
+        D = 2.0 ** rng.integers(-20, 21, n)
+        A = (A0 * D[:, None]) / D[None, :]
+        B, d = oracle.balance(A)
+        assert np.all(np.log2(d) == np.round(np.log2(d)))  # powers of two
+        assert np.array_equal(B, (A / d[:, None]) * d[None, :])  # T^{-1} A T, exactly
+        B2, d2 = oracle.balance(B)  # a balanced matrix is left alone
+        assert np.array_equal(B2, B) and np.all(d2 == 1.0)
+        # the scaling spread shrinks (the balanced matrix is within a few
+        # powers of two of the unscaled A0)
+        assert np.abs(B).max() <= 64 * np.abs(A0).max()
+
+
+def test_logm_balanced_closed_form():
+    # log(D A0 D^{-1}) = D log(A0) D^{-1}; A0 = V diag(lam) V^{-1} with known log.
+    rng = np.random.default_rng(51)
+    for n in (4, 12):
+        lam = np.exp(rng.uniform(-2, 2, n))
+        A0, V = workloads.diag_from_eigs(lam, seed=int(rng.integers(1000)))
+        L0 = V @ np.diag(np.log(lam)) @ np.linalg.inv(V)
+        D = 2.0 ** rng.integers(-15, 16, n)
+        A = (A0 * D[:, None]) / D[None, :]
+        L, dd = oracle.logm(A, balance=1)
+        assert dd["info"] == oracle.OK
+        Lu = (L / D[:, None]) * D[None, :]  # D^{-1} L D, exact
+        assert rel(Lu, L0) < 1e-13
+        Ln, _ = oracle.logm(A0)
+        assert rel(oracle.logm(A0, balance=1)[0], Ln) < 1e-13
+
+
+def test_logm_product_form_and_k3():
+    # Algorithm 1 with the product-form square root, and with k_max = 3, on the
+    # closed-form cases: diagonal, rotation, brute force on V diag V^{-1}.
+    # (k_max = 3 needs s = 9 roots here, and the rounding of the last root is
+    # scaled by 2^s: the bound is 2^s * 32 u * max |log lambda|.)
+    lam = np.array([0.03, 0.7, 2.0, 40.0])
+    for kw in ({"db_form": 1}, {"k_max": 3}, {"k_max": 3, "db_form": 1}):
+        L, d = oracle.logm(np.diag(lam), **kw)
+        bound = 2.0 ** d["s"] * 32 * U * np.abs(np.log(lam)).max()
+        assert d["info"] == oracle.OK and np.abs(np.diag(L) - np.log(lam)).max() <= bound
+        assert np.count_nonzero(L - np.diag(np.diag(L))) == 0
+        r, th = 2.0, 1.5
+        A = r * np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+        L, d = oracle.logm(A, **kw)
+        err = np.abs(L - np.array([[math.log(r), -th], [th, math.log(r)]])).max()
+        assert err <= 2.0 ** d["s"] * 32 * U * th
+        rng = np.random.default_rng(52)
+        lam2 = np.exp(rng.uniform(-2, 2, 6))
+        A, V = workloads.diag_from_eigs(lam2, seed=53)
+        L, d = oracle.logm(A, **kw)
+        assert rel(L, V @ np.diag(np.log(lam2)) @ np.linalg.inv(V)) < 1e-12
+    # near the identity the order search takes k = 3 (Theta_2 < alpha <= Theta_3)
+    rng = np.random.default_rng(54)
+    B = rng.standard_normal((20, 20))
+    A = np.eye(20) + 0.006 * B / np.abs(B).sum(axis=0).max()
+    L, d = oracle.logm(A)
+    assert (d["s"], d["k"]) == (0, 3)
+    # reference: the series log(I + E) = sum (-1)^{i+1} E^i / i, summed until
+    # the terms are below u (||E|| = 0.006: 9 terms)
+    E, S, P = A - np.eye(20), np.zeros((20, 20)), np.eye(20)
+    for i in range(1, 12):
+        P = P @ E
+        S += (-1) ** (i + 1) * P / i
+    assert rel(L, S) < 1e-13
 
 
 def test_logm_status_codes():
