@@ -286,37 +286,51 @@ def main():
 
     # precision forms: the same step with the graph products in split precision
     # on the tensor cores (square roots and plan stay FP64); error vs the FP64 result
+    # The same step with one option changed: the graph products in split
+    # precision on the tensor cores (square roots and plan stay FP64), the
+    # product form of the Denman-Beavers iteration, and diagonal balancing;
+    # each timed on the same inputs, error against the FP64 result.
     forms = {}
-    for prec in ([] if args.no_forms else ["tf32x3", "bf16x3"]):
-        lg.logm_execute(A_dev, precision=prec)
+    variants = [] if args.no_forms else [("tf32x3", {"precision": "tf32x3"}, 2), ("bf16x3", {"precision": "bf16x3"}, 2),
+                                         ("db_product", {"db_form": "product"}, 1), ("balanced", {"balance": True}, 1)]
+    st_fa = torch.zeros(4 * count, dtype=torch.int32, device=dev)
+    st_fb = torch.zeros(4, dtype=torch.int32, device=dev)
+    for name, vopts, vreps in variants:
+        lg.logm_execute(A_dev, **vopts)
         if big:
-            lg.logm_execute(B_dev, precision=prec)
+            lg.logm_execute(B_dev, **vopts)
         barrier()
         fa0, fa1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         fb1 = torch.cuda.Event(enable_timing=True)
-        reps = max(1, min(args.steps, 2))
+        reps = max(1, min(args.steps, vreps))
         fa0.record(stream)
         for _ in range(reps):
-            Lp, sp, kp, ip = lg.logm_execute(A_dev, precision=prec)
+            Lp, sp, kp, ip = lg.logm_execute(A_dev, stats=st_fa, **vopts)
         fa1.record(stream)
         if big:
             for _ in range(reps):
-                Lpb, _, _, _ = lg.logm_execute(B_dev, precision=prec)
+                Lpb, _, _, _ = lg.logm_execute(B_dev, stats=st_fb, **vopts)
         fb1.record(stream)
         barrier()
         ms_fa = fa0.elapsed_time(fa1) / reps
         ms_fb = fa1.elapsed_time(fb1) / reps if big else 0.0
+        fl_a = algorithmic_flops(st_fa.cpu().numpy(), N)
         errs_a = ((Lp - L).flatten(1).norm(dim=1) / L.flatten(1).norm(dim=1)).cpu().numpy()
-        ent = {"batch256": {"ms": ms_fa, "matrices_per_s": count / (ms_fa * 1e-3),
-                            "tflops": flops_a / (ms_fa * 1e-3) / 1e12, "speedup_vs_fp64": ms_a / ms_fa,
+        ent = {"options": vopts,
+               "batch256": {"ms": ms_fa, "matrices_per_s": count / (ms_fa * 1e-3),
+                            "tflops": fl_a / (ms_fa * 1e-3) / 1e12, "speedup_vs_fp64": ms_a / ms_fa,
                             "rel_err_vs_fp64": {"max": float(errs_a.max()), "median": float(np.median(errs_a))}}}
+        if name in ("db_product",):
+            sa = st_fa.cpu().numpy().reshape(-1, 4).sum(axis=0)
+            ent["batch256"]["work"] = {"db_iterations": int(sa[0]), "inverses": int(sa[1]), "products": int(sa[2])}
         if big:
+            fl_b = algorithmic_flops(st_fb.cpu().numpy(), args.big_n)
             eb = float(((Lpb - Lb).norm() / Lb.norm()).item())
-            ent["n4096"] = {"ms": ms_fb, "tflops": flops_b / (ms_fb * 1e-3) / 1e12, "speedup_vs_fp64": ms_b / ms_fb,
+            ent["n4096"] = {"ms": ms_fb, "tflops": fl_b / (ms_fb * 1e-3) / 1e12, "speedup_vs_fp64": ms_b / ms_fb,
                             "rel_err_vs_fp64": eb}
-            ent["step"] = {"ms": ms_fa + ms_fb, "tflops": (flops_a + flops_b) / ((ms_fa + ms_fb) * 1e-3) / 1e12,
+            ent["step"] = {"ms": ms_fa + ms_fb, "tflops": (fl_a + fl_b) / ((ms_fa + ms_fb) * 1e-3) / 1e12,
                            "speedup_vs_fp64": ms / (ms_fa + ms_fb)}
-        forms[prec] = ent
+        forms[name] = ent
 
     # differentiation form: 1024 SPD 64 x 64 (lambda log-uniform in [1e-2, 1e2]),
     # loss = sum(W o log A): forward with checkpoints, then the hand-written adjoint
@@ -390,7 +404,9 @@ def main():
                               "tflops": flops_a / (ms_a * 1e-3) / 1e12,
                               "frac": flops_a / (ms_a * 1e-3) / 1e12 / pk_a, "peak_note": "FP64 " + note_a,
                               "s_hist": np.bincount(s_np).tolist(), "k_hist": np.bincount(k_np, minlength=6).tolist(),
-                              "info_nonzero": int((info_np != 0).sum())}}
+                              "info_nonzero": int((info_np != 0).sum()),
+                              "work": dict(zip(("db_iterations", "inverses", "products"),
+                                               stats.cpu().numpy().reshape(-1, 4).sum(axis=0)[:3].tolist()))}}
         if big:
             parts["n4096"] = {"ms": ms_b, "tflops": ach, "frac": ach / peak, "s": int(sb[0]), "k": int(kb[0]),
                               "info": int(infob[0]), "work": stats_b.cpu().numpy().tolist()}

@@ -11,6 +11,7 @@
  *   s and the number of products k chosen by the backward-error bound
  *   alpha_m <= Theta_m                        (Sec. 5 Table Table_theta; Sec. 6
  *                                               eqs. alphaapprox, AI2, normAm9)
+ *   optional balancing T^{-1} A T / T L T^{-1}   (Algorithm 1, Steps 1 and 'Step_Postproc')
  *
  * Conventions shared by every call:
  *  - Matrices are dense, square, row-major. A batch holds `count` matrices.
@@ -74,13 +75,30 @@ typedef struct logm_batch {
   const int64_t* offset;  /* ragged: device int64[count] element offset of each matrix */
 } logm_batch;
 
+/* Form of the Denman-Beavers square root (logm_options.db_form). */
+#define LOGM_DB_TWO_INVERSE 0 /* eq. (ScalDB): X_k^{-1} and Y_k^{-1} each step */
+#define LOGM_DB_PRODUCT 1     /* product form (the variant cited in Sec. 2): M_k = X_k Y_k,
+                                 one inversion M_k^{-1} and one product X_k M_k^{-1} per step,
+                                 mu_k = |det M_k|^{-1/(2n)}; the same iterates X_k in exact
+                                 arithmetic, none of the first step's product */
+
+/* Preprocessing of Algorithm 1, Step 1 (logm_options.balance). */
+#define LOGM_BALANCE_NONE 0   /* T = I */
+#define LOGM_BALANCE_SCALE 1  /* T diagonal, powers of two (radix-2 Parlett-Reinsch on the
+                                 1-norms of the off-diagonal parts of rows and columns);
+                                 A <- T^{-1} A T before, L <- T L T^{-1} after, both exact */
+
 typedef struct logm_options {
-  int32_t k_max;          /* largest number of graph products: 1, 2 or 5 (Table Table_theta) */
+  int32_t k_max;          /* largest number of graph products: 1, 2, 3 or 5 (Table Table_theta;
+                             k = 3 is T_8 by eq. eqP8pol, k = 4 has no scheme) */
   int32_t precision;      /* LOGM_PREC_* of the graph products */
   int32_t max_sqrt;       /* maxiter of Algorithm 1 (default 40) */
   int32_t max_db_iter;    /* cap on Denman-Beavers iterations per root (default 50) */
-  double theta[3];        /* Theta_{m_k} for k = 1, 2, 5; 0 selects the paper's
-                             1.83e-8, 1.53e-4, 2.46e-1 (Table Table_theta) */
+  int32_t db_form;        /* LOGM_DB_* (default LOGM_DB_TWO_INVERSE) */
+  int32_t balance;        /* LOGM_BALANCE_*, logm_execute / logm_backward only (default NONE) */
+  double theta[5];        /* Theta_{m_k} for k = 1..5 (theta[3], k = 4, is unused); 0 selects
+                             the paper's 1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1
+                             (Table Table_theta) */
 } logm_options;
 
 /* Bytes of device workspace the calls below need for this batch and options
@@ -108,7 +126,8 @@ int logm_plan(const logm_batch* batch, const logm_options* opts, const void* A,
 
 /* logm_sqrt -- one square root A <- A^{1/2} by the scaled Denman-Beavers
  * iteration (Sec. 6, eq. ScalDB; two LU-type left divisions per iteration,
- * mu_k from their determinants), plus A_I2 = A_2 - 2A + I (eq. AI2).
+ * mu_k from their determinants; or its product form, opts->db_form), plus
+ * A_I2 = A_2 - 2A + I (eq. AI2).
  *   A         : device in/out (dtype per batch). Replaced by its square root.
  *   A2_out    : device or NULL; receives the input A (the A_2 of Algorithm 1).
  *   AI2_out   : device or NULL; receives (A^{1/2} - I)^2 = A_2 - 2 A^{1/2} + I.
@@ -122,18 +141,20 @@ int logm_sqrt(const logm_batch* batch, const logm_options* opts, void* A, void* 
 /* logm_graph_eval -- Z = z(X) with the degree-optimal graph of k products
  * (Sec. 3, eq. five_mult_degopt): P_1 = I, P_2 = X, P_3 = X^2 and
  * P_{j+2} = (sum_i h_{j,i} P_i)(sum_i g_{j,i} P_i), z = sum_i y_i P_i, with
- * Table table_simple_experiment for k = 5 and exact Taylor T_2, T_4 (eq.
- * Taylor_log) for k = 1, 2.
+ * Table table_simple_experiment for k = 5, exact Taylor T_2, T_4 (eq.
+ * Taylor_log) for k = 1, 2 and T_8 with three products (eq. eqP8pol, its
+ * coefficients solved in closed form) for k = 3.
  *   X    : device (dtype per batch).
  *   P3   : device or NULL; X^2 if the caller has it (saves one product, as
  *          Algorithm 1 does with A_I2 when s >= 1).
- *   k_dev: device int32[count], each 1, 2 or 5.
+ *   k_dev: device int32[count], each 1, 2, 3 or 5.
  *   Z    : device output (dtype per batch).
  *   precision: LOGM_PREC_* for the products. */
 int logm_graph_eval(const logm_batch* batch, int32_t precision, const void* X, const void* P3,
                     const int32_t* k_dev, void* Z, void* ws, size_t ws_bytes, void* stream);
 
-/* logm_execute -- L = log(A) by Algorithm 1 (T = I: no balancing).
+/* logm_execute -- L = log(A) by Algorithm 1 (balancing T per opts->balance;
+ * diag(T) goes to ctx when given, else to the workspace).
  *   A      : device input, untouched.   L : device output (dtype per batch).
  *   s_dev, k_dev : device int32[count] or NULL; square roots and products used.
  *   info_dev     : device int32[count].
@@ -159,7 +180,11 @@ size_t logm_backward_workspace_size(const logm_batch* batch, const logm_options*
  * iterations (eq. ScalDB) of every level are reversed; the iterates of a level
  * are recomputed from the level's input, which logm_execute checkpointed in
  * ctx. The plan (s, k) and the scalings mu_k are held fixed (they do not
- * change the converged root).
+ * change the converged root). With balancing, the adjoint of L = T z T^{-1},
+ * B = T^{-1} A T is applied with the forward's T (saved in ctx); opts must be
+ * the forward's. The levels are always recomputed with eq. (ScalDB): after a
+ * forward in the product form the recomputed roots equal the forward's to
+ * rounding.
  *   A   : the forward's input.  ctx: the forward's context (logm_context_size
  *         bytes, filled by logm_execute).  dL, dA: device, dtype per batch.
  *   ws  : logm_backward_workspace_size bytes.  n_max <= 256.
@@ -176,8 +201,8 @@ int logm_backward(const logm_batch* batch, const logm_options* opts, const void*
  * A, L and the per-matrix outputs; the scratch space lives in a file-scope
  * device array of 32 MiB that every GPU loading the library keeps until the
  * process exits. The call runs as many matrices at a time as that array
- * holds (7 n_max^2 doubles each), FP64 precision only, n_max <= 256;
- * larger n_max returns LOGM_ERR_UNSUPPORTED and another precision
+ * holds (7 n_max^2 doubles each), FP64 precision only, n_max <= 256, no
+ * balancing; larger n_max, another precision or balancing return
  * LOGM_ERR_UNSUPPORTED. It calls no cudaMalloc, cudaFree or other allocating
  * routine. The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress), so make that first call before any stream capture.

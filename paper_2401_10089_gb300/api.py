@@ -77,12 +77,21 @@ def _values(A):
     return A.values if isinstance(A, Ragged) else A
 
 
-def _options(k_max=5, precision="fp64", max_sqrt=40, max_db_iter=50, theta=None) -> _lib.LogmOptions:
+_DB_FORM = {"two_inverse": 0, "product": 1}
+
+
+def _options(k_max=5, precision="fp64", max_sqrt=40, max_db_iter=50, theta=None, db_form="two_inverse",
+             balance=False) -> _lib.LogmOptions:
+    """k_max in (1, 2, 3, 5); db_form "two_inverse" (eq. ScalDB) or "product";
+    balance: diagonal balancing of Algorithm 1, Step 1; theta: Theta_{m_k} for
+    k = 1..5 (0 = the paper's Table Table_theta)."""
     o = _lib.LogmOptions()
     o.k_max, o.max_sqrt, o.max_db_iter = k_max, max_sqrt, max_db_iter
     o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
-    th = (0.0, 0.0, 0.0) if theta is None else theta
-    for t in range(3):
+    o.db_form = _DB_FORM[db_form] if isinstance(db_form, str) else int(db_form)
+    o.balance = 1 if balance else 0
+    th = (0.0,) * 5 if theta is None else theta
+    for t in range(5):
         o.theta[t] = th[t]
     return o
 
@@ -245,8 +254,8 @@ class LogmFunction(torch.autograd.Function):
     """L = log(A) with the hand-written adjoint (logm_backward) as its backward."""
 
     @staticmethod
-    def forward(ctx, A, k_max=5, max_sqrt=40, max_db_iter=50):
-        opts = dict(k_max=k_max, max_sqrt=max_sqrt, max_db_iter=max_db_iter)
+    def forward(ctx, A, k_max=5, max_sqrt=40, max_db_iter=50, db_form="two_inverse", balance=False):
+        opts = dict(k_max=k_max, max_sqrt=max_sqrt, max_db_iter=max_db_iter, db_form=db_form, balance=balance)
         Ac = A.contiguous()
         L, s, k, info, cbuf = logm_execute(Ac, with_ctx=True, **opts)
         ctx.save_for_backward(Ac, cbuf)
@@ -258,12 +267,12 @@ class LogmFunction(torch.autograd.Function):
     def backward(ctx, dL, ds, dk, dinfo):
         A, cbuf = ctx.saved_tensors
         dA, info = logm_backward(A, cbuf, dL.contiguous(), **ctx.opts)
-        return dA, None, None, None
+        return dA, None, None, None, None, None
 
 
-def logm(A, k_max=5, max_sqrt=40, max_db_iter=50):
+def logm(A, k_max=5, max_sqrt=40, max_db_iter=50, db_form="two_inverse", balance=False):
     """Differentiable matrix logarithm of a (count, n, n) or (n, n) CUDA tensor."""
-    L, s, k, info = LogmFunction.apply(A, k_max, max_sqrt, max_db_iter)
+    L, s, k, info = LogmFunction.apply(A, k_max, max_sqrt, max_db_iter, db_form, balance)
     return L
 
 

@@ -38,7 +38,8 @@ constexpr long long kTcWaitLimit = 1ll << 20;
 
 // Scheme tables (Sec. 3): index j = product number (1: P_3 = X X, 2..5), terms
 // i = 2..j+1 of the factors, y_i of the output. Table table_simple_experiment
-// for k = 5; exact Taylor T_4 (eq. Taylor_log) for k = 2.
+// for k = 5; exact Taylor T_4 (eq. Taylor_log) for k = 2; T_8 by eq.
+// (eqP8pol) for k = 3, its coefficients solved in closed form below.
 static __constant__ float c_tc_h5[14] = {
     7.363757032799957e-02f, -1.050281301619960e+00f, 8.897468955192446e-02f,
     -1.599651928992725e-01f, 9.577281350989334e-01f, 5.394999133948797e-01f,
@@ -60,6 +61,27 @@ struct Coeffs {
   int terms;         // j (number of P_i in each factor)
 };
 
+// k = 3, eq. (eqP8pol): y02 = X^2 (c4 X^2 + c3 X), z = (y02 + d2 X^2 + d1 X)
+// (y02 + e2 X^2) + e0 y02 + X^2/2 + X. Matching x^8 .. x^3 with 1/8 .. 1/3
+// gives c4 = 1/sqrt(8), c3 = 1/(14 c4), d2 + e2 = S, d1, and a quadratic in
+// e2 whose root with the smaller coefficients is taken. Solved in FP64, used
+// in FP32. c = c3, c4, d1, d2, e2, e0.
+static __device__ void tc_k3_coeffs(float* c) {
+  const double c4 = 1.0 / sqrt(8.0);
+  const double c3 = 1.0 / (14.0 * c4);
+  const double sum = (1.0 / 6.0 - c3 * c3) / c4;
+  const double d1 = (1.0 / 5.0 - c3 * sum) / c4;
+  const double beta = sum - c4 * d1 / c3;
+  const double gamma = c3 * d1 + c4 / (3.0 * c3) - 0.25;
+  const double e2 = 0.5 * (beta + sqrt(beta * beta + 4.0 * gamma));
+  c[0] = (float)c3;
+  c[1] = (float)c4;
+  c[2] = (float)d1;
+  c[3] = (float)(sum - e2);
+  c[4] = (float)e2;
+  c[5] = (float)((1.0 / 3.0 - d1 * e2) / c3);
+}
+
 // Factor coefficients of product j for a matrix evaluated with k products.
 static __device__ void scheme_coeffs(int k, int j, Coeffs& c) {
   for (int t = 0; t < 6; ++t) c.h[t] = c.g[t] = 0.0f;
@@ -75,6 +97,22 @@ static __device__ void scheme_coeffs(int k, int j, Coeffs& c) {
     c.g[1] = 0.25f;
     return;
   }
+  if (k == 3) {
+    float q[6];
+    tc_k3_coeffs(q);
+    if (j == 2) {  // P_4 = P_3 (c3 X + c4 P_3)
+      c.h[1] = 1.0f;
+      c.g[0] = q[0];
+      c.g[1] = q[1];
+    } else {  // P_5 = (d1 X + d2 P_3 + P_4)(e2 P_3 + P_4)
+      c.h[0] = q[2];
+      c.h[1] = q[3];
+      c.h[2] = 1.0f;
+      c.g[1] = q[4];
+      c.g[2] = 1.0f;
+    }
+    return;
+  }
   int t = 0;
   for (int jj = 2; jj < j; ++jj) t += jj;
   for (int i = 0; i < j; ++i) {
@@ -87,18 +125,27 @@ static __device__ void scheme_coeffs(int k, int j, Coeffs& c) {
 static __device__ float scheme_y(int k, int i2) {
   if (k == 1) return i2 == 0 ? 1.0f : (i2 == 1 ? 0.5f : 0.0f);
   if (k == 2) return i2 == 0 ? 1.0f : (i2 == 1 ? 0.5f : (i2 == 2 ? 1.0f : 0.0f));
+  if (k == 3) {
+    if (i2 == 2) {
+      float q[6];
+      tc_k3_coeffs(q);
+      return q[5];  // e0
+    }
+    return i2 == 0 ? 1.0f : (i2 == 1 ? 0.5f : (i2 == 3 ? 1.0f : 0.0f));
+  }
   return c_tc_y5[i2 + 1];
 }
 
 static __device__ __forceinline__ int needs_product(int k, int p3_given, int j) {
   if (j == 1) return !p3_given;    // P_3 = X X only when the caller did not supply it
   if (k == 2) return j == 2;
+  if (k == 3) return j <= 3;
   if (k == 5) return j <= 5;
   return 0;
 }
 
 static __device__ __forceinline__ int is_last_product(int k, int j) {
-  return (k == 2 && j == 2) || (k == 5 && j == 5);
+  return (k == 2 || k == 3 || k == 5) && j == k;
 }
 
 // ---------------------------------------------------------------------------
@@ -378,6 +425,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_graph_tc(GraphParams p) {
             float v = ylast * acc;
             for (int i = 0; i < p.j && i < 5; ++i) v = fmaf(yv[i], P[i][idx], v);
             v *= scale;
+            if (p.bal) v *= (float)(p.bal[(int64_t)b * p.n_max + row] / p.bal[(int64_t)b * p.n_max + gc]);
             if (p.out_dtype == 0)
               static_cast<double*>(p.L)[off + idx] = static_cast<double>(v);
             else
@@ -417,7 +465,8 @@ __global__ void k_graph_k1(GraphParams p) {
   const float scale = p.s_dev ? -ldexpf(1.0f, p.s_dev[b]) : 1.0f;
   const int64_t nn = (int64_t)n * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
-    const float v = scale * fmaf(0.5f, P3[t], P2[t]);
+    float v = scale * fmaf(0.5f, P3[t], P2[t]);
+    if (p.bal) v *= (float)(p.bal[(int64_t)b * p.n_max + t / n] / p.bal[(int64_t)b * p.n_max + t % n]);
     if (p.out_dtype == 0)
       static_cast<double*>(p.L)[off + t] = static_cast<double>(v);
     else
@@ -458,6 +507,14 @@ cudaError_t launch_graph_prep(const GraphParams& p, const void* X, const void* P
 }
 
 size_t graph_tc_smem_bytes() { return sizeof(TcSmem); }
+
+cudaError_t launch_graph_k1(const GraphParams& p, cudaStream_t st) {
+  if (p.count <= 0) return cudaSuccess;
+  GraphParams q = p;
+  q.j = 1;
+  k_graph_k1<<<dim3(64, p.count), 256, 0, st>>>(q);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_graph_tc(const GraphParams& p, cudaStream_t st) {
   if (p.count <= 0) return cudaSuccess;

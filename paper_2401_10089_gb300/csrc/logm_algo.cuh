@@ -46,8 +46,31 @@ struct Slot {
   double *Acur, *A2, *Y, *W1, *W2, *T1, *T2;
 };
 
-static __device__ __forceinline__ int m_of_k(int k) { return k == 1 ? 2 : (k == 2 ? 4 : 14); }
-static __device__ __forceinline__ int theta_slot(int k) { return k == 1 ? 0 : (k == 2 ? 1 : 2); }
+static __device__ __forceinline__ int m_of_k(int k) { return k == 1 ? 2 : (k == 2 ? 4 : (k == 3 ? 8 : 14)); }
+static __device__ __forceinline__ int theta_slot(int k) { return k - 1; }
+
+// k = 3 (Sec. 2, eq. eqP8pol): T_8 of eq. (Taylor_log) with three products,
+//   y02 = X^2 (c4 X^2 + c3 X),
+//   z   = (y02 + d2 X^2 + d1 X)(y02 + e2 X^2) + e0 y02 + X^2/2 + X.
+// Equating the coefficients of x^8 .. x^3 with 1/8 .. 1/3 fixes, in turn,
+// c4 = 1/sqrt(8), c3 = 1/(14 c4), d2 + e2 = S, d1, and leaves a quadratic in
+// e2; the root with the smaller coefficients is taken (it also rounds better:
+// its monomials match 1/i within about 1.3 u). c = c3, c4, d1, d2, e2, e0.
+static __device__ void k3_coeffs(double* c) {
+  const double c4 = 1.0 / sqrt(8.0);
+  const double c3 = 1.0 / (14.0 * c4);
+  const double sum = (1.0 / 6.0 - c3 * c3) / c4;  // d2 + e2
+  const double d1 = (1.0 / 5.0 - c3 * sum) / c4;
+  const double beta = sum - c4 * d1 / c3;
+  const double gamma = c3 * d1 + c4 / (3.0 * c3) - 0.25;
+  const double e2 = 0.5 * (beta + sqrt(beta * beta + 4.0 * gamma));
+  c[0] = c3;
+  c[1] = c4;
+  c[2] = d1;
+  c[3] = sum - e2;
+  c[4] = e2;
+  c[5] = (1.0 / 3.0 - d1 * e2) / c3;
+}
 
 // x^m by repeated multiplication, so that "x^{1/m} <= Theta" is decided as
 // "x <= Theta^m" exactly the same way in every implementation.
@@ -314,9 +337,9 @@ static __device__ int alpha_test(Ops& ops, const double* Acur, const double* AI2
 template <class Ops>
 static __device__ int order_search(Ops& ops, const double* Acur, const double* AI2, int n, double nB, double nI2,
                             int k_max, const double* theta, const EstState* loop_est) {
-  int cands[3], nc = 0;
-  const int all[3] = {1, 2, 5};
-  for (int t = 0; t < 3; ++t)
+  int cands[4], nc = 0;
+  const int all[4] = {1, 2, 3, 5};
+  for (int t = 0; t < 4; ++t)
     if (all[t] <= k_max) cands[nc++] = all[t];
   if (nc == 0) return k_max;
   int lo = 0;
@@ -434,6 +457,69 @@ static __device__ int db_sqrt(Ops& ops, Slot& M, int n, int max_db, int* iters_o
 }
 
 // ---------------------------------------------------------------------------
+// Product form of the scaled Denman-Beavers iteration (the variant cited in
+// Sec. 2): with M_k = X_k Y_k the two inversions of eq. (ScalDB) become one,
+//   M_{k+1} = I/2 + (mu_k^2 M_k + mu_k^{-2} M_k^{-1}) / 4,
+//   X_{k+1} = (mu_k X_k + mu_k^{-1} X_k M_k^{-1}) / 2,
+// M_0 = X_0 = A, mu_k = |det M_k|^{-1/(2n)}: one inversion and one product
+// per step (none in the first: X_0 M_0^{-1} = I). Same stop rule. X lives in
+// Acur, M in Y, M^{-1} in W1, X M^{-1} in W2 (A2 is left alone).
+// ---------------------------------------------------------------------------
+template <class Ops>
+static __device__ int db_sqrt_product(Ops& ops, Slot& M, int n, int max_db, int* iters_out) {
+  double* X = M.Acur;
+  double* Mk = M.Y;
+  double* Mi = M.W1;
+  double* XMi = M.W2;
+  copy_matrix(ops, Mk, X, n);
+  const double tol = 10.0 * sqrt((double)n) * kUnitRoundoff;
+  int scale = 1, status = 2, it;
+  double dprev = INFINITY;
+  for (it = 1; it <= max_db; ++it) {
+    double ldm;
+    ops.tally(0, 1);
+    ops.tally(1, 1);
+    if (ops.inverse(Mk, Mi, n, &ldm)) { status = 1; break; }
+    const double mu = ops.bcast0(scale ? exp(-ldm / (2.0 * n)) : 1.0);
+    const double imu = ops.bcast0(1.0 / mu);
+    const double mu2 = ops.bcast0(mu * mu);
+    const double imu2 = ops.bcast0(imu * imu);
+    if (it > 1) {
+      EpiTerms none;
+      none.count = 0;
+      ops.tally(2, 1);
+      ops.gemm(n, X, 0.0, Mi, 0.0, 1.0, none, OutView{XMi, 0});
+    }
+    double sd = 0.0, sx = 0.0;
+    for (int j = ops.tid(); j < n; j += ops.nthreads()) {
+      double cd = 0.0, cx = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const int64_t t = (int64_t)i * n + j;
+        const double xo = X[t];
+        const double xmi = (it > 1) ? XMi[t] : (i == j ? 1.0 : 0.0);
+        const double xn = 0.5 * fma(mu, xo, xmi * imu);
+        Mk[t] = fma(0.25, fma(mu2, Mk[t], Mi[t] * imu2), i == j ? 0.5 : 0.0);
+        X[t] = xn;
+        cd += fabs(xn - xo);
+        cx += fabs(xn);
+      }
+      sd = nanmax(sd, cd);
+      sx = nanmax(sx, cx);
+    }
+    const double nd = ops.max(sd);
+    const double nx = ops.max(sx);
+    const double delta = nd / nx;
+    if (!(delta == delta)) { status = 2; break; }
+    if (delta <= tol) { status = 0; break; }
+    if (!scale && dprev <= 1e-7 && delta > 0.5 * dprev) { status = 0; break; }
+    if (delta < 1e-2) scale = 0;
+    dprev = delta;
+  }
+  *iters_out = it > max_db ? max_db : it;
+  return status;
+}
+
+// ---------------------------------------------------------------------------
 // Graph evaluation, eq. (five_mult_degopt): out = scale * z(X) with P_2 = X
 // (Acur), P_3 = X^2 (A2) given. For Algorithm 1, scale = -2^s (eq. logipASTM
 // and the final squaring step): a power of two, so it changes no rounding.
@@ -454,6 +540,24 @@ static __device__ void graph_eval(Ops& ops, int k, int n, Slot& M, double scale,
     EpiTerms e{{P2, P3}, {scale, 0.5 * scale}, 2};
     ops.tally(2, 1);
     ops.gemm(n, P3, 0.0, M.T2, 0.0, scale, e, out);
+    return;
+  }
+  if (k == 3) {  // eq. (eqP8pol): P_4 = P_3 (c3 X + c4 P_3), z = (P_4 + d2 P_3 + d1 X)(P_4 + e2 P_3) + ...
+    double c[6];
+    k3_coeffs(c);
+    EpiTerms r{{P2, P3}, {c[0], c[1]}, 2};
+    ops.lincomb(n, r, M.T2);
+    EpiTerms none;
+    none.count = 0;
+    ops.tally(2, 1);
+    ops.gemm(n, P3, 0.0, M.T2, 0.0, 1.0, none, OutView{M.Y, 0});  // P_4 = y02
+    EpiTerms hl{{M.Y, P3, P2}, {1.0, c[3], c[2]}, 3};
+    EpiTerms gl{{M.Y, P3}, {1.0, c[4]}, 2};
+    ops.lincomb(n, hl, M.T1);
+    ops.lincomb(n, gl, M.T2);
+    EpiTerms e{{M.Y, P3, P2}, {scale * c[5], 0.5 * scale, scale}, 3};
+    ops.tally(2, 1);
+    ops.gemm(n, M.T1, 0.0, M.T2, 0.0, scale, e, out);
     return;
   }
   // k = 5: P_4 .. P_7 from Table table_simple_experiment
@@ -488,6 +592,88 @@ static __device__ void graph_eval(Ops& ops, int k, int n, Slot& M, double scale,
 }
 
 // ---------------------------------------------------------------------------
+// Balancing, the optional preprocessing A <- T^{-1} A T of Algorithm 1 (Step
+// 1) and the postprocessing L <- T L T^{-1}: T diagonal with powers of two
+// (radix-2 Parlett-Reinsch). For each i in turn, c and r are the 1-norms of
+// the off-diagonal parts of column i and row i; the power of two f that
+// brings c f and r / f within a factor 2 of each other is applied (column i
+// times f, row i divided by f) when it cuts c + r by more than 5 %. Sweeps
+// repeat until one applies nothing (at most 100). Zero rows or columns are
+// left alone. Every factor is a power of two, so both similarities are exact.
+// d (global, n doubles) gets diag(T).
+// ---------------------------------------------------------------------------
+template <class Ops>
+static __device__ void balance_matrix(Ops& ops, double* A, int n, double* d) {
+  for (int i = ops.tid(); i < n; i += ops.nthreads()) d[i] = 1.0;
+  ops.sync();
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    int changed = 0;
+    for (int i = 0; i < n; ++i) {
+      double c = 0.0, r = 0.0;
+      for (int j = ops.tid(); j < n; j += ops.nthreads())
+        if (j != i) {
+          c += fabs(A[(int64_t)j * n + i]);
+          r += fabs(A[(int64_t)i * n + j]);
+        }
+      c = ops.sum(c);
+      r = ops.sum(r);
+      if (c == 0.0 || r == 0.0) continue;
+      const double s = c + r;
+      double f = 1.0, g = r * 0.5;
+      while (c < g) {
+        f *= 2.0;
+        c *= 4.0;
+      }
+      g = r * 2.0;
+      while (c >= g) {
+        f *= 0.5;
+        c *= 0.25;
+      }
+      if ((c + r) / f < 0.95 * s) {
+        changed = 1;
+        const double fi = 1.0 / f;  // a power of two: exact
+        for (int j = ops.tid(); j < n; j += ops.nthreads()) {
+          A[(int64_t)i * n + j] *= fi;
+          A[(int64_t)j * n + i] *= f;
+        }
+        if (ops.leader()) d[i] *= f;
+        ops.sync();
+      }
+    }
+    if (!changed) break;
+  }
+}
+
+// M_ij <- M_ij d_i / d_j (T M T^{-1}) or, with inverse, M_ij d_j / d_i
+// (T^{-1} M T), for an FP64 work matrix.
+template <class Ops>
+static __device__ void similarity_diag(Ops& ops, double* Mx, int n, const double* d, bool inverse) {
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = ops.tid(); t < nn; t += ops.nthreads()) {
+    const int i = (int)(t / n), j = (int)(t % n);
+    Mx[t] *= inverse ? d[j] / d[i] : d[i] / d[j];
+  }
+  ops.sync();
+}
+
+// The output L <- T L T^{-1} in place, in the caller's dtype.
+template <class Ops>
+static __device__ void unbalance_output(Ops& ops, void* L, int dtype, int64_t off, int n, const double* d) {
+  ops.sync();
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t t = ops.tid(); t < nn; t += ops.nthreads()) {
+    const double f = d[t / n] / d[t % n];
+    if (dtype == 0) {
+      static_cast<double*>(L)[off + t] *= f;
+    } else {
+      float* q = static_cast<float*>(L) + off + t;
+      *q = (float)((double)*q * f);
+    }
+  }
+  ops.sync();
+}
+
+// ---------------------------------------------------------------------------
 // One matrix, per entry point.
 // ---------------------------------------------------------------------------
 template <class Ops>
@@ -506,6 +692,8 @@ static __device__ void run_execute(Ops& ops, const SmallParams& p, int b, int n,
     }
     return;
   }
+  double* dvec = p.balance ? p.bal + (int64_t)b * p.bal_stride : nullptr;
+  if (dvec) balance_matrix(ops, M.Acur, n, dvec);
   const int m = m_of_k(km);
   const double th = p.theta[theta_slot(km)];
   double nB = ops.norm1(M.Acur, n, 1.0), nI2 = 0.0;
@@ -523,7 +711,7 @@ static __device__ void run_execute(Ops& ops, const SmallParams& p, int b, int n,
     }
     copy_matrix(ops, M.A2, M.Acur, n);
     int it;
-    const int r = db_sqrt(ops, M, n, p.max_db, &it);
+    const int r = p.db_form == 1 ? db_sqrt_product(ops, M, n, p.max_db, &it) : db_sqrt(ops, M, n, p.max_db, &it);
     if (r == 1) { info = 1; break; }
     if (r == 2 && info == 0) info = 2;
     ai2_from(ops, M, n);
@@ -558,6 +746,7 @@ static __device__ void run_execute(Ops& ops, const SmallParams& p, int b, int n,
       ops.sync();
     } else {
       graph_eval(ops, k, n, M, -ldexp(1.0, s), out_view(p.L, p.dtype, off));
+      if (dvec) unbalance_output(ops, p.L, p.dtype, off, n, dvec);
     }
   }
   if (ops.leader()) {
@@ -630,7 +819,7 @@ static __device__ void run_sqrt(Ops& ops, const SmallParams& p, int b, int n, in
   copy_matrix(ops, M.A2, M.Acur, n);
   if (p.A2_out) store_matrix(ops, p.A2_out, p.dtype, off, n, M.A2);
   int it;
-  const int r = db_sqrt(ops, M, n, p.max_db, &it);
+  const int r = p.db_form == 1 ? db_sqrt_product(ops, M, n, p.max_db, &it) : db_sqrt(ops, M, n, p.max_db, &it);
   store_matrix(ops, p.A_inout, p.dtype, off, n, M.Acur);
   if (p.AI2_out) {
     ai2_from(ops, M, n);
@@ -645,7 +834,7 @@ static __device__ void run_sqrt(Ops& ops, const SmallParams& p, int b, int n, in
 template <class Ops>
 static __device__ void run_graph(Ops& ops, const SmallParams& p, int b, int n, int64_t off, Slot& M) {
   const int k = p.k_in[b];
-  if (!(k == 1 || k == 2 || k == 5)) {
+  if (!(k == 1 || k == 2 || k == 3 || k == 5)) {
     if (ops.leader() && p.info) p.info[b] = -1;
     return;
   }
@@ -690,6 +879,18 @@ static __device__ __forceinline__ void scheme64(int k, int j, int i, double* h, 
     }
     return;
   }
+  if (k == 3) {  // eq. (eqP8pol) in the degree-optimal form
+    double c[6];
+    k3_coeffs(c);
+    if (j == 2) {  // P_4 = P_3 (c3 P_2 + c4 P_3)
+      *h = (i == 3) ? 1.0 : 0.0;
+      *g = (i == 2) ? c[0] : (i == 3 ? c[1] : 0.0);
+    } else if (j == 3) {  // P_5 = (d1 P_2 + d2 P_3 + P_4)(e2 P_3 + P_4)
+      *h = (i == 2) ? c[2] : (i == 3 ? c[3] : 1.0);
+      *g = (i == 2) ? 0.0 : (i == 3 ? c[4] : 1.0);
+    }
+    return;
+  }
   int t = 0;
   for (int jj = 2; jj < j; ++jj) t += jj;
   *h = c_h5[t + i - 2];
@@ -699,6 +900,14 @@ static __device__ __forceinline__ void scheme64(int k, int j, int i, double* h, 
 static __device__ __forceinline__ double y64(int k, int i) {  // y_i, i = 2..k+2
   if (k == 1) return i == 2 ? 1.0 : 0.5;
   if (k == 2) return i == 2 ? 1.0 : (i == 3 ? 0.5 : 1.0);
+  if (k == 3) {
+    if (i == 4) {
+      double c[6];
+      k3_coeffs(c);
+      return c[5];
+    }
+    return i == 2 ? 1.0 : (i == 3 ? 0.5 : 1.0);
+  }
   return c_y5[i - 1];
 }
 
@@ -718,7 +927,7 @@ template <class Ops>
 static __device__ void run_backward(Ops& ops, const SmallParams& p, int b, int n, int64_t off, BwdSlot& W) {
   const int s = p.ctx_hdr[2 * b], k = p.ctx_hdr[2 * b + 1];
   const int64_t nn = (int64_t)n * n;
-  if (k != 1 && k != 2 && k != 5) {  // the forward produced no result
+  if (k != 1 && k != 2 && k != 3 && k != 5) {  // the forward produced no result
     fill_nan(ops, p.dA, p.dtype, off, n);
     if (ops.leader()) p.info[b] = 1;
     return;
@@ -729,6 +938,7 @@ static __device__ void run_backward(Ops& ops, const SmallParams& p, int b, int n
     return;
   }
   const int64_t lstride = (int64_t)p.ctx_nmax * p.ctx_nmax;
+  const double* dvec = p.balance ? p.bal + (int64_t)b * p.bal_stride : nullptr;
   Slot& F = W.F;
   int it = 0, status = 0;
   // 1. recompute the last level (its tape serves the first reversal) and P_3
@@ -739,6 +949,7 @@ static __device__ void run_backward(Ops& ops, const SmallParams& p, int b, int n
     ai2_from(ops, F, n);
   } else {
     load_matrix(ops, p.A, p.dtype, off, n, F.Acur);
+    if (dvec) similarity_diag(ops, F.Acur, n, dvec, true);  // T^{-1} A T
     EpiTerms none;
     none.count = 0;
     ops.gemm(n, F.Acur, 1.0, F.Acur, 1.0, 1.0, none, OutView{F.A2, 0});
@@ -746,7 +957,7 @@ static __device__ void run_backward(Ops& ops, const SmallParams& p, int b, int n
   to_x(ops, F.Acur, n);
   double* P[7] = {nullptr, nullptr, F.Acur, F.A2, F.Y, F.W1, F.W2};
   // 2. recompute the products that later products use as factors
-  const int last_j = (k == 5) ? 5 : (k == 2 ? 2 : 1);
+  const int last_j = k;  // P_{k+2} is the last product
   for (int j = 2; j < last_j; ++j) {
     EpiTerms hl, gl;
     factor_terms<Ops>(k, j, P, hl, gl);
@@ -758,6 +969,7 @@ static __device__ void run_backward(Ops& ops, const SmallParams& p, int b, int n
   }
   // 3. zbar = -2^s dL; Pbar_i = y_i zbar
   load_matrix(ops, p.dL, p.dtype, off, n, W.Lb);
+  if (dvec) similarity_diag(ops, W.Lb, n, dvec, false);  // the adjoint of L = T z T^{-1}: T Lbar T^{-1}
   const double sc = -ldexp(1.0, s);
   for (int i = 2; i <= k + 2; ++i) {
     EpiTerms e{{W.Lb}, {sc * y64(k, i)}, 1};
@@ -827,6 +1039,7 @@ static __device__ void run_backward(Ops& ops, const SmallParams& p, int b, int n
     if (ops.leader()) p.info[b] = status == 1 ? 1 : 6;
     return;
   }
+  if (dvec) similarity_diag(ops, W.Ab, n, dvec, true);  // the adjoint of T^{-1} A T: T^{-1} Abar T
   store_matrix(ops, p.dA, p.dtype, off, n, W.Ab);
   if (ops.leader()) p.info[b] = 0;
 }

@@ -9,7 +9,8 @@
 
 namespace {
 
-constexpr double kThetaPaper[3] = {1.83e-8, 1.53e-4, 2.46e-1};  // Table Table_theta, k = 1, 2, 5
+// Table Table_theta, k = 1..5 (k = 4 has no scheme here)
+constexpr double kThetaPaper[5] = {1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1};
 
 // Kernel configuration per size bucket (logm_set_tuning).
 int g_variant[lg::kBuckets] = {0, 0, 0, 0, 0, 0};
@@ -38,11 +39,13 @@ int batch_n_max(const logm_batch* b) {
 
 int opts_ok(const logm_options* o) {
   if (!o) return 0;
-  if (o->k_max != 1 && o->k_max != 2 && o->k_max != 5) return 0;
+  if (o->k_max != 1 && o->k_max != 2 && o->k_max != 3 && o->k_max != 5) return 0;
   if (o->precision < LOGM_PREC_FP64 || o->precision > LOGM_PREC_BF16X3) return 0;
   if (o->max_sqrt < 0 || o->max_sqrt > 1000) return 0;
   if (o->max_db_iter < 1 || o->max_db_iter > 1000) return 0;
-  for (int t = 0; t < 3; ++t)
+  if (o->db_form != LOGM_DB_TWO_INVERSE && o->db_form != LOGM_DB_PRODUCT) return 0;
+  if (o->balance != LOGM_BALANCE_NONE && o->balance != LOGM_BALANCE_SCALE) return 0;
+  for (int t = 0; t < 5; ++t)
     if (!(o->theta[t] >= 0.0) || !(o->theta[t] < 1.0)) return 0;
   return 1;
 }
@@ -53,16 +56,18 @@ int opts_ok(const logm_options* o) {
 struct WsLayout {
   int small_nmax;   // 0: no small pass
   int large_nmax;   // 0: no large pass
-  size_t small_bytes, large_off, graph_off, total;
+  size_t small_bytes, large_off, bal_off, graph_off, total;
 };
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Tensor-core graph stage region: FP32 slots P_2 .. P_6 per matrix, then k, s
-// (when the caller passes none) and an error word.
+// (when the caller passes none), an error word and, for uniform batches, the
+// packed operand slices of the TMA-fed product kernel.
 size_t graph_region_bytes(const logm_batch* b, int n_max) {
   return round256(sizeof(float) * 5 * (size_t)b->count * n_max * n_max) +
-         2 * round256(sizeof(int32_t) * (size_t)b->count) + 256;
+         2 * round256(sizeof(int32_t) * (size_t)b->count) + 256 +
+         (b->n_uniform > 0 ? round256(lg::graph_pack_bytes(b->count, n_max)) : 0);
 }
 
 WsLayout ws_layout(const logm_batch* b, int precision) {
@@ -78,7 +83,9 @@ WsLayout ws_layout(const logm_batch* b, int precision) {
   }
   L.small_bytes = L.small_nmax ? small_slots_bytes_all_variants(b->count, L.small_nmax) : 0;
   L.large_off = round256(L.small_bytes);
-  L.graph_off = round256(L.large_off + (L.large_nmax ? lg::large_workspace_bytes(L.large_nmax) : 0));
+  // diag(T) of the balancing, per matrix (used when no context is given)
+  L.bal_off = round256(L.large_off + (L.large_nmax ? lg::large_workspace_bytes(L.large_nmax) : 0));
+  L.graph_off = round256(L.bal_off + sizeof(double) * (size_t)b->count * n_max);
   L.total = L.graph_off + (precision != LOGM_PREC_FP64 ? graph_region_bytes(b, n_max) : 0);
   return L;
 }
@@ -88,6 +95,7 @@ struct GraphRegion {
   int32_t* k;
   int32_t* s;
   int32_t* err;
+  void* pack;  // uniform batches only
 };
 
 GraphRegion graph_region(const logm_batch* b, const WsLayout& L, void* ws) {
@@ -101,6 +109,8 @@ GraphRegion graph_region(const logm_batch* b, const WsLayout& L, void* ws) {
   g.s = reinterpret_cast<int32_t*>(w);
   w += round256(sizeof(int32_t) * (size_t)b->count);
   g.err = reinterpret_cast<int32_t*>(w);
+  w += 256;
+  g.pack = b->n_uniform > 0 ? static_cast<void*>(w) : nullptr;
   return g;
 }
 
@@ -116,15 +126,18 @@ void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o)
     p.k_max = o->k_max;
     p.max_sqrt = o->max_sqrt;
     p.max_db = o->max_db_iter;
-    for (int t = 0; t < 3; ++t) p.theta[t] = o->theta[t] > 0.0 ? o->theta[t] : kThetaPaper[t];
+    for (int t = 0; t < 5; ++t) p.theta[t] = o->theta[t] > 0.0 ? o->theta[t] : kThetaPaper[t];
     p.precision = o->precision;
+    p.db_form = o->db_form;
+    p.balance = o->balance;
   } else {
     p.k_max = 5;
     p.max_sqrt = 40;
     p.max_db = 50;
-    for (int t = 0; t < 3; ++t) p.theta[t] = kThetaPaper[t];
+    for (int t = 0; t < 5; ++t) p.theta[t] = kThetaPaper[t];
   }
   p.ctx_nmax = p.n_max;
+  p.bal_stride = p.n_max;
 }
 
 // One launch per block configuration, each taking the size buckets the
@@ -187,6 +200,18 @@ int run_passes(lg::Mode mode, lg::SmallParams& p, const logm_batch* b, void* ws,
   return LOGM_SUCCESS;
 }
 
+// Split-precision graph products: uniform batches take the packed TMA-fed
+// kernels (graph_tma.cu), ragged ones the kernel that forms its operand
+// tiles in shared memory (graph_tc.cu); k = 1 matrices need no product.
+cudaError_t launch_graph_products(const lg::GraphParams& gp, cudaStream_t st) {
+  if (gp.pack) {
+    cudaError_t e = lg::launch_graph_tma(gp, st);
+    if (e != cudaSuccess) return e;
+    return lg::launch_graph_k1(gp, st);
+  }
+  return lg::launch_graph_tc(gp, st);
+}
+
 int check_ws(const logm_batch* b, void* ws, size_t ws_bytes, int precision = LOGM_PREC_FP64) {
   if (!ws) return LOGM_ERR_WORKSPACE;
   if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return LOGM_ERR_WORKSPACE;
@@ -198,7 +223,7 @@ int check_ws(const logm_batch* b, void* ws, size_t ws_bytes, int precision = LOG
 
 extern "C" {
 
-int logm_version(void) { return 100; }
+int logm_version(void) { return 200; }
 
 int logm_set_tuning(const logm_tuning* t) {
   if (!t) {
@@ -224,14 +249,19 @@ size_t logm_workspace_size(const logm_batch* batch, const logm_options* opts) {
   return ws_layout(batch, opts ? opts->precision : LOGM_PREC_TF32X3).total;
 }
 
-// Context: (s, k) per matrix, then the input of every square-root level.
+// Context: (s, k) per matrix, diag(T) of the balancing per matrix, then the
+// input of every square-root level.
 size_t ctx_header_bytes(const logm_batch* b) { return round256(sizeof(int32_t) * 2 * (size_t)b->count); }
+size_t ctx_bal_bytes(const logm_batch* b) {
+  return round256(sizeof(double) * (size_t)b->count * (size_t)batch_n_max(b));
+}
 
 size_t logm_context_size(const logm_batch* batch, const logm_options* opts) {
   (void)opts;
   const int n_max = batch_n_max(batch);
   if (n_max <= 0) return 0;
-  return ctx_header_bytes(batch) + (size_t)batch->count * lg::kCtxLevels * (size_t)n_max * n_max * sizeof(double);
+  return ctx_header_bytes(batch) + ctx_bal_bytes(batch) +
+         (size_t)batch->count * lg::kCtxLevels * (size_t)n_max * n_max * sizeof(double);
 }
 
 size_t logm_backward_workspace_size(const logm_batch* batch, const logm_options* opts) {
@@ -311,10 +341,11 @@ int logm_graph_eval(const logm_batch* batch, int32_t precision, const void* X, c
     gp.precision = precision;
     gp.p3_given = P3 ? 1 : 0;
     gp.err = g.err;
+    gp.pack = g.pack;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(g.err, 0, sizeof(int32_t), st) != cudaSuccess) return LOGM_ERR_CUDA;
     if (lg::launch_graph_prep(gp, X, P3, batch->dtype, st) != cudaSuccess) return LOGM_ERR_CUDA;
-    return lg::launch_graph_tc(gp, st) == cudaSuccess ? LOGM_SUCCESS : LOGM_ERR_CUDA;
+    return launch_graph_products(gp, st) == cudaSuccess ? LOGM_SUCCESS : LOGM_ERR_CUDA;
   }
   lg::SmallParams p;
   fill_common(p, batch, nullptr);
@@ -344,7 +375,10 @@ int logm_execute(const logm_batch* batch, const logm_options* opts, const void* 
   p.stats = stats_dev;
   if (ctx) {
     p.ctx_hdr = static_cast<int32_t*>(ctx);
-    p.ctx = reinterpret_cast<double*>(static_cast<char*>(ctx) + ctx_header_bytes(batch));
+    p.bal = reinterpret_cast<double*>(static_cast<char*>(ctx) + ctx_header_bytes(batch));
+    p.ctx = reinterpret_cast<double*>(static_cast<char*>(ctx) + ctx_header_bytes(batch) + ctx_bal_bytes(batch));
+  } else {
+    p.bal = reinterpret_cast<double*>(static_cast<char*>(ws) + ws_layout(batch, opts->precision).bal_off);
   }
   p.ctx_levels = lg::kCtxLevels;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -372,8 +406,10 @@ int logm_execute(const logm_batch* batch, const logm_options* opts, const void* 
   gp.precision = opts->precision;
   gp.p3_given = 1;
   gp.err = g.err;
+  gp.bal = p.balance ? p.bal : nullptr;
+  gp.pack = g.pack;
   if (cudaMemsetAsync(g.err, 0, sizeof(int32_t), st) != cudaSuccess) return LOGM_ERR_CUDA;
-  return lg::launch_graph_tc(gp, st) == cudaSuccess ? LOGM_SUCCESS : LOGM_ERR_CUDA;
+  return launch_graph_products(gp, st) == cudaSuccess ? LOGM_SUCCESS : LOGM_ERR_CUDA;
 }
 
 int logm_backward(const logm_batch* batch, const logm_options* opts, const void* A, const void* ctx,
@@ -393,7 +429,9 @@ int logm_backward(const logm_batch* batch, const logm_options* opts, const void*
   p.dA = dA;
   p.info = info_dev;
   p.ctx_hdr = const_cast<int32_t*>(static_cast<const int32_t*>(ctx));
-  p.ctx = reinterpret_cast<double*>(const_cast<char*>(static_cast<const char*>(ctx)) + ctx_header_bytes(batch));
+  char* cb = const_cast<char*>(static_cast<const char*>(ctx));
+  p.bal = reinterpret_cast<double*>(cb + ctx_header_bytes(batch));
+  p.ctx = reinterpret_cast<double*>(cb + ctx_header_bytes(batch) + ctx_bal_bytes(batch));
   p.ctx_levels = lg::kCtxLevels;
   char* w = static_cast<char*>(ws);
   p.queue = reinterpret_cast<int32_t*>(w);

@@ -19,7 +19,11 @@ struct SmallParams {
   const int64_t* off_dev;
   // options
   int k_max, max_sqrt, max_db;
-  double theta[3];
+  int db_form;         // 0: eq. (ScalDB), two inversions per step; 1: product form
+  int balance;         // 1: T^{-1} A T before and T L T^{-1} after (execute; backward reverses it)
+  double* bal;         // balance: diag(T) per matrix, stride bal_stride (execute writes, backward reads)
+  int bal_stride;      // the batch's n_max
+  double theta[5];     // Theta_{m_k}, k = 1..5 (k = 4 unused)
   // inputs / outputs (NULL when unused by the mode)
   const void* A;       // execute, plan, sqrt (sqrt: in/out)
   void* A_inout;       // sqrt
@@ -62,7 +66,7 @@ struct GraphParams {
   int count, n_uniform, n_max;
   const int32_t* n_dev;
   const int64_t* off_dev;
-  const int32_t* k_dev;     // products per matrix (1, 2, 5)
+  const int32_t* k_dev;     // products per matrix (1, 2, 3, 5)
   const int32_t* s_dev;     // square roots per matrix (scale -2^s), NULL: scale 1
   const int32_t* info_dev;  // matrices with info 1 or 4 are skipped; may be NULL
   float* gbuf;              // per matrix 5 slots of n_max^2 floats: P_2 .. P_6
@@ -72,10 +76,16 @@ struct GraphParams {
   int j;                    // product of this launch (1: P_3 = X X, 2..5)
   int p3_given;             // 1: slot 1 already holds P_3
   int32_t* err;             // set when a tensor-core wait timed out
+  const double* bal;        // NULL, or diag(T) of the balancing per matrix (stride n_max): L <- T L T^{-1}
+  void* pack;               // uniform batches: packed operand slices (graph_pack_bytes), else NULL
 };
 
 size_t graph_tc_smem_bytes();
 cudaError_t launch_graph_tc(const GraphParams& p, cudaStream_t st);
+cudaError_t launch_graph_k1(const GraphParams& p, cudaStream_t st);
+// Uniform batches: pack + TMA-fed tcgen05 products (graph_tma.cu).
+size_t graph_pack_bytes(int count, int n);
+cudaError_t launch_graph_tma(const GraphParams& p, cudaStream_t st);
 cudaError_t launch_graph_prep(const GraphParams& p, const void* X, const void* P3, int in_dtype, cudaStream_t st);
 
 constexpr int kSlotMats = 7;

@@ -22,7 +22,8 @@ namespace {
 
 constexpr size_t kNoallocScratchBytes = size_t(32) << 20;
 constexpr int kMaxDevices = 64;
-constexpr double kThetaPaperNoalloc[3] = {1.83e-8, 1.53e-4, 2.46e-1};  // Table Table_theta
+// Table Table_theta, k = 1..5 (k = 4 has no scheme here)
+constexpr double kThetaPaperNoalloc[5] = {1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1};
 
 // The scratch array. Host code must not pass `g_noalloc_scratch` itself to a
 // kernel: on the host that name is a stand-in, not a device address. The
@@ -63,12 +64,17 @@ extern "C" int logm_execute_noalloc(const logm_batch* batch, const logm_options*
       return LOGM_ERR_INVALID_ARG;
     n_max = batch->n_max;
   }
-  if (opts->k_max != 1 && opts->k_max != 2 && opts->k_max != 5) return LOGM_ERR_INVALID_ARG;
+  if (opts->k_max != 1 && opts->k_max != 2 && opts->k_max != 3 && opts->k_max != 5) return LOGM_ERR_INVALID_ARG;
   if (opts->max_sqrt < 0 || opts->max_sqrt > 1000) return LOGM_ERR_INVALID_ARG;
   if (opts->max_db_iter < 1 || opts->max_db_iter > 1000) return LOGM_ERR_INVALID_ARG;
-  for (int t = 0; t < 3; ++t)
+  if (opts->db_form != LOGM_DB_TWO_INVERSE && opts->db_form != LOGM_DB_PRODUCT) return LOGM_ERR_INVALID_ARG;
+  if (opts->balance != LOGM_BALANCE_NONE && opts->balance != LOGM_BALANCE_SCALE) return LOGM_ERR_INVALID_ARG;
+  for (int t = 0; t < 5; ++t)
     if (!(opts->theta[t] >= 0.0) || !(opts->theta[t] < 1.0)) return LOGM_ERR_INVALID_ARG;
   if (opts->precision != LOGM_PREC_FP64) return LOGM_ERR_UNSUPPORTED;
+  // Balancing keeps diag(T) per matrix (count * n_max doubles), which has no
+  // fixed bound: not offered here.
+  if (opts->balance != LOGM_BALANCE_NONE) return LOGM_ERR_UNSUPPORTED;
   if (batch->count == 0) return LOGM_SUCCESS;
   if (!A || !L || !info_dev) return LOGM_ERR_INVALID_ARG;
   // Sizes beyond what this entry point can hold are rejected here.
@@ -90,8 +96,9 @@ extern "C" int logm_execute_noalloc(const logm_batch* batch, const logm_options*
   p.k_max = opts->k_max;
   p.max_sqrt = opts->max_sqrt;
   p.max_db = opts->max_db_iter;
-  for (int t = 0; t < 3; ++t) p.theta[t] = opts->theta[t] > 0.0 ? opts->theta[t] : kThetaPaperNoalloc[t];
+  for (int t = 0; t < 5; ++t) p.theta[t] = opts->theta[t] > 0.0 ? opts->theta[t] : kThetaPaperNoalloc[t];
   p.precision = opts->precision;
+  p.db_form = opts->db_form;
   p.A = A;
   p.L = L;
   p.s_out = s_dev;

@@ -3,10 +3,13 @@ products and the Denman-Beavers iterations) against central finite
 differences of the GPU forward (h = 1e-6, FP64) and against the oracle's
 Frechet adjoint L(A^T, W), read off the block-triangular logarithm.
 
-Tolerances: central differences carry h^2 |f'''| + u |f| / h ~ 1e-10
-relative, so 1e-6 is loose enough for plan-stable inputs (the plan (s, k) is
-piecewise constant; inputs are chosen away from its thresholds and the test
-checks that both perturbed points keep the plan). Against the exact Frechet
+Tolerances: a central difference D(h) carries h^2 |f'''| / 6 of truncation
+plus kappa u |f| / h of rounding noise of the forward map. For SPD inputs
+with eigenvalues down to 1e-2 (kappa ~ 1e4) the noise alone reaches ~1e-6
+relative at h = 1e-6, so each comparison allows 1e-6 relative plus twice
+|D(h) - D(2h)|, a measured bound on both terms (the plan (s, k) is piecewise
+constant; inputs are chosen away from its thresholds and the test checks that
+every perturbed point keeps the plan). Against the exact Frechet
 adjoint the adjoint of the computed map differs by the derivative of the
 approximation error, bounded by the same backward-error analysis (u-level
 relative) times the conditioning: 1e-11 relative here (measured on GB300:
@@ -38,9 +41,18 @@ def fd_dir(A, W, E, h=1e-6, **kw):
     return (fp - fm) / (2 * h), (sp.cpu().numpy(), kp.cpu().numpy(), sm.cpu().numpy(), km.cpu().numpy())
 
 
+def fd_with_error(A, W, E, h=1e-6, **kw):
+    """(D(h), |D(h) - D(2h)|, plans at +-h, whether the +-2h points kept
+    the same plan) from central differences at h and 2h."""
+    d1, p1 = fd_dir(A, W, E, h, **kw)
+    d2, p2 = fd_dir(A, W, E, 2 * h, **kw)
+    same = ((p1[0] == p2[0]) & (p1[1] == p2[1]) & (p1[2] == p2[2]) & (p1[3] == p2[3]))
+    return d1, np.abs(d1 - d2), p1, same
+
+
 @pytest.mark.parametrize("case", ["spd64", "dense48", "near_identity", "kmax2", "kmax1"])
 def test_backward_vs_central_differences(case):
-    rng = np.random.default_rng(hash(case) % 1000)
+    rng = np.random.default_rng(["spd64", "dense48", "near_identity", "kmax2", "kmax1"].index(case) + 90)
     kw = {}
     if case == "spd64":
         A = workloads.spd(3, 64, seed=80, lo=1e-2, hi=1e2)
@@ -60,13 +72,14 @@ def test_backward_vs_central_differences(case):
         assert (s == 0).all()
     for t in range(3):
         E = rng.standard_normal(A.shape)
-        fd, plans = fd_dir(A, W, E, **kw)
-        same = (plans[0] == s) & (plans[1] == k) & (plans[2] == s) & (plans[3] == k)
+        fd, fd_err, plans, same2 = fd_with_error(A, W, E, **kw)
+        same = same2 & (plans[0] == s) & (plans[1] == k) & (plans[2] == s) & (plans[3] == k)
         an = (dA * E).sum(axis=(-2, -1))
         for b in range(A.shape[0]):
             if same[b]:
                 tol = 1e-5 if kw.get("k_max") == 1 else 1e-6  # k_max = 1: s ~ 28, cancellation ~u/Theta_1
-                assert abs(an[b] - fd[b]) <= tol * max(1.0, abs(fd[b])), (case, b, an[b], fd[b])
+                bound = tol * max(1.0, abs(fd[b])) + 2 * fd_err[b]
+                assert abs(an[b] - fd[b]) <= bound, (case, b, an[b], fd[b], fd_err[b])
 
 
 def test_backward_level_limit_status():

@@ -29,7 +29,7 @@ def _call_noalloc(lib, A):
     b.count, b.dtype, b.n_uniform, b.n_max, b.n, b.offset = count, _lib.DTYPE_F64, n, n, None, None
     o = _lib.LogmOptions()
     o.k_max, o.precision, o.max_sqrt, o.max_db_iter = 5, _lib.PREC_FP64, 40, 50
-    for t in range(3):
+    for t in range(5):
         o.theta[t] = 0.0
     L = torch.empty_like(A)
     s = torch.empty(count, dtype=torch.int32, device=A.device)
