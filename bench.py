@@ -314,7 +314,10 @@ def main():
         barrier()
         ms_fa = fa0.elapsed_time(fa1) / reps
         ms_fb = fa1.elapsed_time(fb1) / reps if big else 0.0
-        fl_a = algorithmic_flops(st_fa.cpu().numpy(), N)
+        # the split-precision forms run the same plan as the FP64 path (same s, k),
+        # but their products are not in the FP64 kernel's tally: count the FP64 run's
+        split = "precision" in vopts
+        fl_a = flops_a if split else algorithmic_flops(st_fa.cpu().numpy(), N)
         errs_a = ((Lp - L).flatten(1).norm(dim=1) / L.flatten(1).norm(dim=1)).cpu().numpy()
         ent = {"options": vopts,
                "batch256": {"ms": ms_fa, "matrices_per_s": count / (ms_fa * 1e-3),
@@ -324,7 +327,7 @@ def main():
             sa = st_fa.cpu().numpy().reshape(-1, 4).sum(axis=0)
             ent["batch256"]["work"] = {"db_iterations": int(sa[0]), "inverses": int(sa[1]), "products": int(sa[2])}
         if big:
-            fl_b = algorithmic_flops(st_fb.cpu().numpy(), args.big_n)
+            fl_b = flops_b if split else algorithmic_flops(st_fb.cpu().numpy(), args.big_n)
             eb = float(((Lpb - Lb).norm() / Lb.norm()).item())
             ent["n4096"] = {"ms": ms_fb, "tflops": fl_b / (ms_fb * 1e-3) / 1e12, "speedup_vs_fp64": ms_b / ms_fb,
                             "rel_err_vs_fp64": eb}
