@@ -23,10 +23,15 @@
  *  - with s = 0 there is no A_I2 yet, so the powers are applied with A - I;
  *  - comparisons "x^{1/m} <= Theta" are made as "x <= Theta^m", both sides
  *    formed by repeated multiplication, so that the decision is exact;
- *  - the Denman-Beavers stop rule is not given: stop when the relative
- *    change of X in the 1-norm is <= 10 sqrt(n) u, or, once scaling is off
- *    and the change has reached 1e-7, when it no longer halves; scaling by
- *    mu is switched off once the change drops below 1e-2;
+ *  - the Denman-Beavers stop rule is not given: with delta the relative
+ *    change of X in the 1-norm and tol = 10 sqrt(n) u, stop when delta <=
+ *    tol; or, once scaling is off, when delta^2 ||X_k^{-1}|| ||X_{k+1}|| <=
+ *    tol (the error left after a step of a quadratically convergent
+ *    iteration, so the step that would only confirm convergence is not
+ *    taken; the product form bounds that error by the distance of M_k from
+ *    I instead, see orc_sqrtm_db_product);
+ *    or, once scaling is off and delta has reached 1e-7, when it no longer
+ *    halves; scaling by mu is switched off once delta drops below 1e-2;
  *  - k = 1, 2 are the exact Taylor polynomials T_2, T_4 (eq. Taylor_log);
  *    k = 3 is T_8 evaluated with three products by eq. (eqP8pol), its
  *    coefficients solved here in closed form; k = 5 is Table
@@ -337,6 +342,13 @@ int orc_sqrtm_db(int n, const double* A, double* Xout, int max_iter, int32_t* it
       status = ORC_OK;
       break;
     }
+    /* With mu = 1 the step is Newton's: X_{k+1} - X_* ~ (X_k - X_*) X_k^{-1}
+     * (X_k - X_*) / 2, so ||X_{k+1} - X_*|| / ||X_{k+1}|| is below
+     * delta^2 ||X_k^{-1}|| ||X_{k+1}||: stop once that is below tol. */
+    if (!scale && delta * delta * orc_norm1(n, Xi) * orc_norm1(n, X) <= tol) {
+      status = ORC_OK;
+      break;
+    }
     if (!scale && dprev <= 1e-7 && delta > 0.5 * dprev) {
       status = ORC_OK; /* converged to rounding level */
       break;
@@ -364,8 +376,20 @@ int orc_sqrtm_db(int n, const double* A, double* Xout, int max_iter, int32_t* it
 /* M_0 = X_0 = A, mu_k = |det M_k|^{-1/(2n)} (= |det X_k det Y_k|^{-1/(2n)}). */
 /* The iterates X_k are those of eq. (ScalDB) in exact arithmetic; each     */
 /* step takes one inversion and one product instead of two inversions (the  */
-/* first takes no product: X_0 M_0^{-1} = I). Same stop rule.               */
+/* first takes no product: X_0 M_0^{-1} = I). Same stop rule, the error a  */
+/* step leaves bounded through M_k (below) instead of X_k^{-1}.             */
 /* ------------------------------------------------------------------------ */
+/* ||A - s I||_1 */
+static double norm1_shift(int n, const double* A, double s) {
+  double best = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double c = 0.0;
+    for (int i = 0; i < n; ++i) c += fabs(A[(size_t)i * n + j] - (i == j ? s : 0.0));
+    if (c > best || isnan(c)) best = c;
+  }
+  return best;
+}
+
 int orc_sqrtm_db_product(int n, const double* A, double* Xout, int max_iter, int32_t* iters) {
   double* X = alloc_mat(n);
   double* M = alloc_mat(n);
@@ -386,6 +410,15 @@ int orc_sqrtm_db_product(int n, const double* A, double* Xout, int max_iter, int
       break;
     }
     double mu = scale ? exp(-ldm / (2.0 * n)) : 1.0;
+    /* With mu = 1, M_{k+1} - I = M_k^{-1} (M_k - I)^2 / 4 and X_{k+1} = X_*
+     * M_{k+1}^{1/2} (commuting case), so X_{k+1} is left with a relative
+     * error of about ||M_{k+1} - I|| / 2 <= ||M_k^{-1}|| ||M_k||^2
+     * ||I - M_k^{-1}||^2 / 8: stop after this step once that is <= tol. */
+    double pred = INFINITY;
+    if (!scale) {
+      const double nm = orc_norm1(n, M), nmi = orc_norm1(n, Mi), d = norm1_shift(n, Mi, 1.0);
+      pred = 0.125 * nmi * nm * nm * d * d;
+    }
     if (it == 1)
       set_identity(n, XMi);
     else
@@ -402,7 +435,7 @@ int orc_sqrtm_db_product(int n, const double* A, double* Xout, int max_iter, int
       status = ORC_NO_CONVERGENCE;
       break;
     }
-    if (delta <= tol) {
+    if (delta <= tol || pred <= tol) {
       status = ORC_OK;
       break;
     }

@@ -388,9 +388,12 @@ static __device__ int order_search(Ops& ops, const double* Acur, const double* A
 // ---------------------------------------------------------------------------
 // Scaled Denman-Beavers square root, eq. (ScalDB): X_0 = A (in Acur, in
 // place), Y_0 = I, mu_k = |det X_k det Y_k|^{-1/(2n)} from the pivots of the
-// two inverses. Stop when the relative 1-norm change of X is <= 10 sqrt(n) u,
-// or, once scaling is off and the change has reached 1e-7, when it no longer
-// halves; scaling is switched off below 1e-2.
+// two inverses. With delta the relative 1-norm change of X and tol =
+// 10 sqrt(n) u: stop when delta <= tol; or, once scaling is off (mu = 1, a
+// Newton step, quadratically convergent), when delta^2 ||X_k^{-1}|| ||X_{k+1}||
+// <= tol, the relative error that step leaves, so that no step is spent only
+// confirming convergence; or, once scaling is off and delta has reached
+// 1e-7, when it no longer halves. Scaling is switched off below 1e-2.
 // Returns 0 (converged), 1 (singular) or 2 (no convergence).
 // ---------------------------------------------------------------------------
 // Optional record of one square root for the adjoint: X_i^{-1}, Y_i^{-1} and
@@ -448,6 +451,7 @@ static __device__ int db_sqrt(Ops& ops, Slot& M, int n, int max_db, int* iters_o
     const double delta = nd / nx;
     if (!(delta == delta)) { status = 2; break; }
     if (delta <= tol) { status = 0; break; }
+    if (!scale && delta * delta * ops.norm1(Xi, n, 0.0) * nx <= tol) { status = 0; break; }
     if (!scale && dprev <= 1e-7 && delta > 0.5 * dprev) { status = 0; break; }
     if (delta < 1e-2) scale = 0;
     dprev = delta;
@@ -462,7 +466,8 @@ static __device__ int db_sqrt(Ops& ops, Slot& M, int n, int max_db, int* iters_o
 //   M_{k+1} = I/2 + (mu_k^2 M_k + mu_k^{-2} M_k^{-1}) / 4,
 //   X_{k+1} = (mu_k X_k + mu_k^{-1} X_k M_k^{-1}) / 2,
 // M_0 = X_0 = A, mu_k = |det M_k|^{-1/(2n)}: one inversion and one product
-// per step (none in the first: X_0 M_0^{-1} = I). Same stop rule. X lives in
+// per step (none in the first: X_0 M_0^{-1} = I). Same stop rule, with the
+// error left by a step bounded through M_k instead of X_k^{-1}. X lives in
 // Acur, M in Y, M^{-1} in W1, X M^{-1} in W2 (A2 is left alone).
 // ---------------------------------------------------------------------------
 template <class Ops>
@@ -484,6 +489,13 @@ static __device__ int db_sqrt_product(Ops& ops, Slot& M, int n, int max_db, int*
     const double imu = ops.bcast0(1.0 / mu);
     const double mu2 = ops.bcast0(mu * mu);
     const double imu2 = ops.bcast0(imu * imu);
+    // With mu = 1, M_{k+1} - I = M_k^{-1} (M_k - I)^2 / 4 and X_{k+1} ~ X_* M_{k+1}^{1/2}:
+    // the step leaves a relative error <= ||M_k^{-1}|| ||M_k||^2 ||I - M_k^{-1}||^2 / 8.
+    double pred = INFINITY;
+    if (!scale) {
+      const double nm = ops.norm1(Mk, n, 0.0), nmi = ops.norm1(Mi, n, 0.0), d = ops.norm1(Mi, n, 1.0);
+      pred = 0.125 * nmi * nm * nm * d * d;
+    }
     if (it > 1) {
       EpiTerms none;
       none.count = 0;
@@ -510,7 +522,7 @@ static __device__ int db_sqrt_product(Ops& ops, Slot& M, int n, int max_db, int*
     const double nx = ops.max(sx);
     const double delta = nd / nx;
     if (!(delta == delta)) { status = 2; break; }
-    if (delta <= tol) { status = 0; break; }
+    if (delta <= tol || pred <= tol) { status = 0; break; }
     if (!scale && dprev <= 1e-7 && delta > 0.5 * dprev) { status = 0; break; }
     if (delta < 1e-2) scale = 0;
     dprev = delta;

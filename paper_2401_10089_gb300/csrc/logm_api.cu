@@ -148,8 +148,11 @@ cudaError_t launch_small_variants(lg::Mode mode, const lg::SmallParams& q, int s
   const bool tuned = mode == lg::kModeExecute || mode == lg::kModeBackward;
   int mask[kVariants] = {0, 0, 0, 0};
   const int top = lg::size_bucket(small_nmax);
-  for (int bk = 0; bk <= top; ++bk) mask[tuned ? g_variant[bk] : 0] |= 1 << bk;
-  if (mask[0] == (1 << (top + 1)) - 1) mask[0] = 0;  // configuration 0 takes everything: no filter
+  // a uniform batch fills one bucket: only its configuration is launched
+  const int lo = q.n_uniform > 0 ? top : 0;
+  for (int bk = lo; bk <= top; ++bk) mask[tuned ? g_variant[bk] : 0] |= 1 << bk;
+  if (lo == 0 && mask[0] == (1 << (top + 1)) - 1) mask[0] = 0;  // configuration 0 takes everything: no filter
+  if (lo > 0 && mask[0]) mask[0] = 0;  // configuration 0 holds the only bucket: no filter
   for (int v = kVariants - 1; v >= 0; --v) {
     if (v > 0 && !mask[v]) continue;
     if (v == 0 && !mask[0] && (mask[1] || mask[2] || mask[3])) continue;

@@ -38,7 +38,10 @@ __global__ void __launch_bounds__(kThreads) k_order_keys(SmallParams p) {
     int64_t off;
     matrix_geometry(p, b, &n, &off);
     double best = 0.0;
-    if (n >= 1 && n <= p.n_max) {
+    // matrices another configuration (or the whole-GPU kernel) takes are not
+    // read: they go to the cheapest bucket, at the end of this queue
+    const bool mine = !(p.bucket_mask && !((p.bucket_mask >> size_bucket(n)) & 1)) && !(n > kMaxN && p.large_pass);
+    if (mine && n >= 1 && n <= p.n_max) {
       for (int j = threadIdx.x; j < n; j += kThreads) {
         double sum = 0.0;
         for (int i = 0; i < n; ++i) {
@@ -51,7 +54,7 @@ __global__ void __launch_bounds__(kThreads) k_order_keys(SmallParams p) {
     }
     const double nu = block_max(best, red);
     if (threadIdx.x == 0) {
-      const double n3 = (n >= 1 ? (double)n * n * n : 1.0);
+      const double n3 = (mine && n >= 1 ? (double)n * n * n : 0.0);
       double key = n3 * (1.0 + log2(1.0 + (nu == nu ? nu : 1e30) / th));
       int bk = (int)(4.0 * log2(key + 1.0));
       bk = bk < 0 ? 0 : (bk >= kOrderBuckets ? kOrderBuckets - 1 : bk);
