@@ -113,6 +113,52 @@ static __device__ double block_max(double v, Reduce& r) {
   return s;
 }
 
+// |v| as an integer whose order is that of |v| (IEEE binary64 magnitudes order
+// like their bit patterns); NaN maps to the key of +Inf, so a NaN pivot is
+// taken like an infinite one and then rejected. Integer work only: on this
+// GPU every FP64 instruction on the pivot search's critical path is costly.
+static __device__ __forceinline__ unsigned long long abs_key(double v) {
+  unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7FFFFFFFFFFFFFFFull;
+  return b > 0x7FF0000000000000ull ? 0x7FF0000000000000ull : b;
+}
+static __device__ __forceinline__ bool key_better(unsigned long long a, int ia, unsigned long long b, int ib) {
+  return a > b || (a == b && ia < ib);
+}
+
+// Block argmax over (key, index): largest key, smallest index on ties; the
+// result in every thread. Ends with a block barrier.
+static __device__ void block_argmax_key(unsigned long long key, int idx, Reduce& r, unsigned long long* ok,
+                                        int* oi) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (key_better(k2, i2, key, idx)) {
+      key = k2;
+      idx = i2;
+    }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    r.v[w] = __longlong_as_double(static_cast<long long>(key));
+    r.i[w] = idx;
+  }
+  __syncthreads();
+  unsigned long long bk = static_cast<unsigned long long>(__double_as_longlong(r.v[0]));
+  int bi = r.i[0];
+#pragma unroll
+  for (int t = 1; t < kWarps; ++t) {
+    const unsigned long long kt = static_cast<unsigned long long>(__double_as_longlong(r.v[t]));
+    if (key_better(kt, r.i[t], bk, bi)) {
+      bk = kt;
+      bi = r.i[t];
+    }
+  }
+  __syncthreads();
+  *ok = bk;
+  *oi = bi;
+}
+
 // max of v with the smallest index among ties; v < 0 marks "not a candidate".
 static __device__ void block_argmax(double v, int idx, Reduce& r, double* out_v, int* out_i) {
 #pragma unroll
@@ -343,7 +389,10 @@ static __device__ int gj_inverse_block(double* __restrict__ W, int n, double* lo
   double* P = S.u.gj.P;
   double* R = S.u.gj.R;
   int* piv = S.piv;
-  double ld = 0.0;  // meaningful in thread 0
+  // |det| as dm * 2^dex (thread 0): one multiply per step instead of a log,
+  // dm kept in [1, 2) by moving its exponent into dex (exact)
+  double dm = 1.0, ld_slow = 0.0;
+  long long dex = 0;
   int status = 0;
   for (int kb = 0; kb < n && !status; kb += kPanel) {
     const int jb = min(kPanel, n - kb);
@@ -355,22 +404,21 @@ static __device__ int gj_inverse_block(double* __restrict__ W, int n, double* lo
     __syncthreads();
     for (int c = 0; c < jb; ++c) {
       const int k = kb + c;
-      double cand = -1.0;
+      unsigned long long cand = 0;
       int cidx = n;
       for (int i = tid; i < n; i += kThreads) {
         if (i >= k) {
-          double v = fabs(P[c * kMaxN + i]);
-          if (v != v) v = INFINITY;  // NaN pivots are taken (and rejected below)
-          if (v > cand || (v == cand && i < cidx)) {
+          const unsigned long long v = abs_key(P[c * kMaxN + i]);  // NaN pivots are taken (and rejected below)
+          if (key_better(v, i, cand, cidx)) {
             cand = v;
             cidx = i;
           }
         }
       }
-      double pv;
+      unsigned long long pv;
       int p;
-      block_argmax(cand, cidx, S.red, &pv, &p);
-      if (!(pv > 0.0) || !(pv < INFINITY)) {
+      block_argmax_key(cand, cidx, S.red, &pv, &p);
+      if (pv == 0 || pv >= 0x7FF0000000000000ull) {  // zero, Inf or NaN
         status = 1;
         break;
       }
@@ -383,8 +431,16 @@ static __device__ int gj_inverse_block(double* __restrict__ W, int n, double* lo
       __syncthreads();
       if (tid == 0) {
         const double d = P[c * kMaxN + k];
-        ld += log(fabs(d));
         S.bc[0] = 1.0 / d;
+        const unsigned long long bits =
+            static_cast<unsigned long long>(__double_as_longlong(dm * d)) & 0x7FFFFFFFFFFFFFFFull;
+        const int ef = (int)(bits >> 52);
+        if (ef == 0 || ef == 0x7FF) {  // subnormal or overflow: fall back to a log
+          ld_slow += log(fabs(d));
+        } else {
+          dex += ef - 1023;
+          dm = __longlong_as_double(static_cast<long long>((bits & 0x000FFFFFFFFFFFFFull) | (1023ull << 52)));
+        }
       }
       __syncthreads();
       const double inv = S.bc[0];
@@ -471,7 +527,7 @@ static __device__ int gj_inverse_block(double* __restrict__ W, int n, double* lo
         }
       }
   }
-  if (tid == 0) S.bc[1] = ld;
+  if (tid == 0) S.bc[1] = log(dm) + (double)dex * 0.69314718055994530942 + ld_slow;
   __syncthreads();
   *logabsdet = S.bc[1];
   __syncthreads();

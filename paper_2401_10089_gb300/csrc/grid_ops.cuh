@@ -2,9 +2,12 @@
 //
 // One cooperative launch (every block resident) runs Algorithm 1 with all
 // blocks working on the same matrix; phases are separated by a grid barrier.
-// The barrier is bounded: a block that waits longer than kBarrierTimeoutNs
-// sets an error flag, and from then on every barrier returns at once, so the
-// kernel always finishes (with LOGM_INFO error status) instead of hanging.
+// The barrier is a monotonic 64-bit arrival counter (no reset: episode e of a
+// barrier completes when its counter reaches (e + 1) * nblocks; each block
+// counts its episodes in shared memory), one release add and acquire polls.
+// It is bounded: a block that waits longer than kBarrierTimeoutNs sets an
+// error flag, and from then on every barrier returns at once, so the kernel
+// always finishes (with LOGM_INFO error status) instead of hanging.
 //
 // Reductions are deterministic and identical in every block: each block
 // writes its partial result, and after the barrier every block reduces the
@@ -24,10 +27,14 @@ constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  //
 
 // Buffers of one Gauss-Jordan inversion running on a group of blocks.
 struct GjGroup {
-  unsigned* bar;     // [2] arrivals, generation of the group's own barrier
-  double* cand_v;    // [2][kMaxGrid] pivot candidates (value)
+  unsigned long long* bar;  // arrival counter of the group's own barrier
+  unsigned long long* cand_v;  // [2][kMaxGrid] pivot candidates: |value| as an ordered integer key
   int* cand_i;       // [2][kMaxGrid] pivot candidates (row)
-  double* panel;     // [2][kGridPanel][n_max] panel, column-major, double-buffered
+  double* pivval;    // [n_max] pivot of every Gauss-Jordan step (log|det| is summed after the loop)
+  double* ldpart;    // [kMaxGrid] per-block partial sums of log|pivot|
+  double* cand_row;  // [2][kMaxGrid][kGridPanel] each block's candidate row of the panel
+  double* row_k;     // [2][kGridPanel] the panel row of the next pivot position
+  double* panel;     // [kGridPanel][n_max] the finished panel, column-major
   double* R;         // [kGridPanel][n_max] pivot rows of the panel
   int* piv;          // [n_max] pivot rows of the Gauss-Jordan steps
   int* perm;         // [n_max] composite column permutation
@@ -36,7 +43,7 @@ struct GjGroup {
 };
 
 struct GridWs {
-  unsigned* bar;     // [0] arrivals, [1] generation (zeroed before the launch)
+  unsigned long long* bar;  // arrival counter of the whole-grid barrier (zeroed before the launch)
   int* err;          // set when a barrier wait timed out (zeroed before the launch)
   double* partial;   // [2][kMaxGrid] partial results of sum / max
   int* ipartial;     // [2][kMaxGrid] partial results of all / argmax indices
@@ -51,9 +58,16 @@ struct GridSmem {
   Reduce red;
   double rowk[kGridPanel];
   double rowp[kGridPanel];
+  double prow[kGridPanel];
   double bc[4];
   int work[4];
+  unsigned long long ep[3];  // barrier episodes seen: whole grid, group 0, group 1
+  int winner;                // block holding the pivot candidate of the current column
 };
+
+// Dynamic shared memory of the whole-GPU kernel: this block's rows of the
+// current Gauss-Jordan panel, row-major, two buffers of rows_cap x kGridPanel.
+extern __shared__ double grid_panel_smem[];
 
 static __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -61,28 +75,34 @@ static __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Barrier over `nblocks` blocks sharing the counter pair bar[0..1].
-static __device__ void bounded_barrier(unsigned* bar, unsigned nblocks, int* err) {
+static __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+static __device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Barrier over `nblocks` blocks sharing the arrival counter *bar; *ep is this
+// block's episode count for that counter (shared memory, thread 0 only).
+static __device__ void bounded_barrier(unsigned long long* bar, unsigned nblocks, int* err,
+                                       unsigned long long* ep) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
     volatile int* verr = err;
+    const unsigned long long target = (*ep + 1) * nblocks;
+    *ep += 1;
     if (*verr == 0) {
-      const unsigned g = *vgen;
-      __threadfence();
-      const unsigned arrived = atomicAdd(bar, 1u);
-      if (arrived == nblocks - 1) {
-        atomicExch(bar, 0u);
-        __threadfence();
-        atomicAdd(bar + 1, 1u);
-      } else {
-        const unsigned long long t0 = global_ns();
-        while (*vgen == g && *verr == 0) {
-          __nanosleep(64);
-          if (global_ns() - t0 > kBarrierTimeoutNs) {
-            atomicExch(err, 1);
-            break;
-          }
+      red_release_add(bar, 1ull);  // publishes this block's writes (release, gpu scope)
+      const unsigned long long t0 = global_ns();
+      int polls = 0;
+      while (ld_acquire(bar) < target) {
+        if (*verr) break;
+        if ((++polls & 63) == 0 && global_ns() - t0 > kBarrierTimeoutNs) {
+          atomicExch(err, 1);
+          break;
         }
       }
     }
@@ -91,8 +111,6 @@ static __device__ void bounded_barrier(unsigned* bar, unsigned nblocks, int* err
   __syncthreads();
 }
 
-static __device__ __forceinline__ void grid_barrier(GridWs& w) { bounded_barrier(w.bar, gridDim.x, w.err); }
-
 struct GridOps {
   GridWs& w;
   GridSmem& S;
@@ -100,7 +118,7 @@ struct GridOps {
 
   __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
   __device__ int nthreads() const { return gridDim.x * blockDim.x; }
-  __device__ void sync() { grid_barrier(w); }
+  __device__ void sync() { bounded_barrier(w.bar, gridDim.x, w.err, &S.ep[0]); }
   __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
 
   __device__ double sum(double v) {
@@ -282,12 +300,18 @@ struct GridOps {
 
   // dst <- src^{-1} by Gauss-Jordan with partial pivoting (same steps as
   // gj_inverse_block), panels of kGridPanel columns, on the gn blocks
-  // starting at g0 with the group's buffers and barrier `bar`. The panel is
-  // spread over the group's blocks by rows; each column step is one group
-  // barrier: the owners of every row apply the step and publish the next
-  // column's pivot candidates. Writes log|det| and the status (0, or 1 for a
-  // zero / non-finite pivot) to g.result.
-  __device__ void inverse_group(GjGroup& g, int g0, int gn, unsigned* bar, const double* src, double* dst, int n) {
+  // starting at g0 with the group's buffers, barrier counter `bar` and
+  // episode count `ep`. The panel is spread over the group's blocks by rows
+  // and each block keeps its rows in shared memory (grid_panel_smem, at most
+  // rows_cap rows). Each column step is one group barrier: every block then
+  // reads all blocks' pivot candidates and the row of the pivot position (one
+  // round of loads), picks the pivot, reads the winning block's candidate row
+  // (one more), applies the step to its own rows and publishes its candidate
+  // for the next column together with that candidate's panel row. Writes
+  // log|det| and the status (0, or 1 for a zero / non-finite pivot) to
+  // g.result.
+  __device__ void inverse_group(GjGroup& g, int g0, int gn, unsigned long long* bar, unsigned long long* ep,
+                                const double* src, double* dst, int n, int first_jb = kGridPanel) {
     const int lb = blockIdx.x - g0;
     const int gt = lb * kThreads + threadIdx.x, gnt = gn * kThreads;
     const bool glead = lb == 0 && threadIdx.x == 0;
@@ -299,100 +323,119 @@ struct GridOps {
     const int r_lo = lb * rows_per;
     const int r_hi = min(n, r_lo + rows_per);
     const int my_rows = r_hi > r_lo ? r_hi - r_lo : 0;
-    double* P0 = g.panel;
-    double* P1 = g.panel + (int64_t)kGridPanel * w.n_max;
+    double* Sp0 = grid_panel_smem;                             // [rows_per][kGridPanel]
+    double* Sp1 = grid_panel_smem + rows_per * kGridPanel;
+    double* Pf = g.panel;                                      // finished panel, column-major
     double ld = 0.0;  // group leader
     int status = 0;
-    bounded_barrier(bar, gn, w.err);
-    for (int kb = 0; kb < n && !status; kb += kGridPanel) {
-      const int jb = min(kGridPanel, n - kb);
-      // own rows of W[:, J] -> P0, and the candidates of column kb
+    bounded_barrier(bar, gn, w.err, ep);
+    for (int kb = 0, jw = first_jb; kb < n && !status; kb += jw, jw = kGridPanel) {
+      const int jb = min(jw, n - kb);
+      // own rows of W[:, J] -> shared memory; candidates of column kb; the
+      // candidate's row and the row of pivot position kb are published
       {
-        double cv = -1.0;
+        unsigned long long cv = 0;
         int ci = 0x7fffffff;
         for (int e = threadIdx.x; e < my_rows * jb; e += kThreads) {
-          const int r = r_lo + e / jb, c = e % jb;
+          const int rr = e / jb, c = e % jb;
+          const int r = r_lo + rr;
           const double v = W[(int64_t)r * n + kb + c];
-          P0[(int64_t)c * n + r] = v;
+          Sp0[rr * kGridPanel + c] = v;
           if (c == 0 && r >= kb) {
-            double a = fabs(v);
-            if (a != a) a = INFINITY;
-            if (a > cv || (a == cv && r < ci)) { cv = a; ci = r; }
+            const unsigned long long a = abs_key(v);
+            if (key_better(a, r, cv, ci)) { cv = a; ci = r; }
           }
         }
-        double bv;
+        unsigned long long bv;
         int bi;
-        block_argmax(cv, ci, S.red, &bv, &bi);
+        block_argmax_key(cv, ci, S.red, &bv, &bi);  // ends with a block barrier: Sp0 is complete
         if (threadIdx.x == 0) {
           g.cand_v[lb] = bv;
           g.cand_i[lb] = bi;
         }
+        if (bi >= r_lo && bi < r_hi && threadIdx.x < jb)
+          g.cand_row[(int64_t)lb * kGridPanel + threadIdx.x] = Sp0[(bi - r_lo) * kGridPanel + threadIdx.x];
+        if (kb >= r_lo && kb < r_hi && threadIdx.x < jb) g.row_k[threadIdx.x] = Sp0[(kb - r_lo) * kGridPanel + threadIdx.x];
       }
-      bounded_barrier(bar, gn, w.err);
+      bounded_barrier(bar, gn, w.err, ep);
       for (int c = 0; c < jb; ++c) {
         const int k = kb + c;
-        const double* Pin = (c & 1) ? P1 : P0;
-        double* Pout = (c & 1) ? P0 : P1;
-        const double* cvv = g.cand_v + (c & 1) * kMaxGrid;
-        const int* cii = g.cand_i + (c & 1) * kMaxGrid;
-        double pv;
+        const int buf = c & 1;
+        const double* Sin = buf ? Sp1 : Sp0;
+        double* Sout = buf ? Sp0 : Sp1;
+        const unsigned long long* cvv = g.cand_v + buf * kMaxGrid;
+        const int* cii = g.cand_i + buf * kMaxGrid;
+        // pivot: the largest candidate (smallest row on ties), and the row of position k
+        unsigned long long pv;
         int p;
         {
-          double cv = -1.0;
+          unsigned long long cv = 0;
           int ci = 0x7fffffff;
           for (int q = threadIdx.x; q < G; q += kThreads)
-            if (cvv[q] > cv || (cvv[q] == cv && cii[q] < ci)) { cv = cvv[q]; ci = cii[q]; }
-          block_argmax(cv, ci, S.red, &pv, &p);
+            if (key_better(cvv[q], cii[q], cv, ci)) { cv = cvv[q]; ci = cii[q]; }
+          if (threadIdx.x < jb) S.rowk[threadIdx.x] = g.row_k[buf * kGridPanel + threadIdx.x];
+          block_argmax_key(cv, ci, S.red, &pv, &p);
         }
-        if (!(pv > 0.0) || !(pv < INFINITY) || p < k || p >= n) { status = 1; break; }
-        if (threadIdx.x < jb) {
-          S.rowk[threadIdx.x] = Pin[(int64_t)threadIdx.x * n + k];
-          S.rowp[threadIdx.x] = Pin[(int64_t)threadIdx.x * n + p];
-        }
+        if (pv == 0 || pv >= 0x7FF0000000000000ull || p < k || p >= n) { status = 1; break; }  // zero, Inf or NaN
+        if (threadIdx.x < jb)
+          S.rowp[threadIdx.x] = g.cand_row[((int64_t)buf * kMaxGrid + p / rows_per) * kGridPanel + threadIdx.x];
         __syncthreads();
-        const double d = S.rowp[c];
-        const double inv = bcast0(1.0 / d);
+        // one division per step (thread 0), then the scaled pivot row (one warp)
+        if (threadIdx.x == 0) S.bc[0] = 1.0 / S.rowp[c];
+        __syncthreads();
+        const double inv = S.bc[0];
+        if (threadIdx.x < jb) S.prow[threadIdx.x] = (threadIdx.x == c) ? inv : S.rowp[threadIdx.x] * inv;
         if (glead) {
-          ld += log(fabs(d));
+          g.pivval[k] = S.rowp[c];
           g.piv[k] = p;
         }
-        double cv = -1.0;
+        __syncthreads();
+        unsigned long long cv = 0;
         int ci = 0x7fffffff;
         for (int e = threadIdx.x; e < my_rows * jb; e += kThreads) {
-          const int r = r_lo + e / jb, cc = e % jb;
-          const double prow = (cc == c) ? inv : S.rowp[cc] * inv;
+          const int rr = e / jb, cc = e % jb;
+          const int r = r_lo + rr;
           double val;
           if (r == k) {
-            val = prow;
+            val = S.prow[cc];
           } else {
-            const double srcv = (r == p) ? S.rowk[cc] : Pin[(int64_t)cc * n + r];
-            const double f = (r == p) ? S.rowk[c] : Pin[(int64_t)c * n + r];
-            val = (cc == c) ? -f * inv : fma(-f, prow, srcv);
+            const double srcv = (r == p) ? S.rowk[cc] : Sin[rr * kGridPanel + cc];
+            const double f = (r == p) ? S.rowk[c] : Sin[rr * kGridPanel + c];
+            val = (cc == c) ? -f * inv : fma(-f, S.prow[cc], srcv);
           }
-          Pout[(int64_t)cc * n + r] = val;
+          Sout[rr * kGridPanel + cc] = val;
           if (cc == c + 1 && r > k) {
-            double a = fabs(val);
-            if (a != a) a = INFINITY;
-            if (a > cv || (a == cv && r < ci)) { cv = a; ci = r; }
+            const unsigned long long a = abs_key(val);
+            if (key_better(a, r, cv, ci)) { cv = a; ci = r; }
           }
         }
         if (c + 1 < jb) {
-          double bv;
+          unsigned long long bv;
           int bi;
-          block_argmax(cv, ci, S.red, &bv, &bi);
+          block_argmax_key(cv, ci, S.red, &bv, &bi);  // ends with a block barrier: Sout is complete
+          const int nb = (c + 1) & 1;
           if (threadIdx.x == 0) {
-            g.cand_v[((c + 1) & 1) * kMaxGrid + lb] = bv;
-            g.cand_i[((c + 1) & 1) * kMaxGrid + lb] = bi;
+            g.cand_v[nb * kMaxGrid + lb] = bv;
+            g.cand_i[nb * kMaxGrid + lb] = bi;
           }
+          if (bi >= r_lo && bi < r_hi && threadIdx.x < jb)
+            g.cand_row[((int64_t)nb * kMaxGrid + lb) * kGridPanel + threadIdx.x] =
+                Sout[(bi - r_lo) * kGridPanel + threadIdx.x];
+          if (k + 1 >= r_lo && k + 1 < r_hi && threadIdx.x < jb)
+            g.row_k[nb * kGridPanel + threadIdx.x] = Sout[(k + 1 - r_lo) * kGridPanel + threadIdx.x];
         }
-        bounded_barrier(bar, gn, w.err);
+        bounded_barrier(bar, gn, w.err, ep);
       }
       if (status) break;
-      const double* Pf = (jb & 1) ? P1 : P0;
-      // panel -> W, the panel's row swaps on the other columns, pivot rows -> R
+      const double* Sf = (jb & 1) ? Sp1 : Sp0;
+      // panel -> W and the column-major copy Pf, the panel's row swaps on the
+      // other columns, pivot rows -> R
       for (int e = threadIdx.x; e < my_rows * jb; e += kThreads) {
-        const int r = r_lo + e / jb, c = e % jb;
-        W[(int64_t)r * n + kb + c] = Pf[(int64_t)c * n + r];
+        const int rr = e / jb, c = e % jb;
+        const int r = r_lo + rr;
+        const double v = Sf[rr * kGridPanel + c];
+        W[(int64_t)r * n + kb + c] = v;
+        Pf[(int64_t)c * n + r] = v;
       }
       for (int j = gt; j < n; j += gnt) {
         if (j >= kb && j < kb + jb) continue;
@@ -406,13 +449,18 @@ struct GridOps {
         }
         for (int c = 0; c < jb; ++c) g.R[(int64_t)c * n + j] = W[(int64_t)(kb + c) * n + j];
       }
-      bounded_barrier(bar, gn, w.err);
+      bounded_barrier(bar, gn, w.err, ep);
       const int tiles = (n + kTileM - 1) / kTileM;
       for (int t = lb; t < tiles * tiles; t += G)
         rank_update_tile(W, n, kb, jb, Pf, g.R, (t / tiles) * kTileM, (t % tiles) * kTileN);
-      bounded_barrier(bar, gn, w.err);
+      bounded_barrier(bar, gn, w.err, ep);
     }
     if (!status) {
+      // log|det| = sum of log|pivot|, one log per thread, per-block partial sums
+      double lsum = 0.0;
+      for (int k = gt; k < n; k += gnt) lsum += log(fabs(g.pivval[k]));
+      lsum = block_sum(lsum, S.red);
+      if (threadIdx.x == 0) g.ldpart[lb] = lsum;
       if (glead) {
         for (int j = 0; j < n; ++j) g.perm[j] = j;
         for (int k = n - 1; k >= 0; --k) {
@@ -422,7 +470,9 @@ struct GridOps {
           g.perm[p] = t0;
         }
       }
-      bounded_barrier(bar, gn, w.err);
+      bounded_barrier(bar, gn, w.err, ep);
+      if (glead)
+        for (int q = 0; q < G; ++q) ld += g.ldpart[q];
       for (int64_t t = gt; t < nn; t += gnt) {
         const int64_t i = t / n, j = t % n;
         dst[t] = W[i * n + g.perm[j]];
@@ -436,7 +486,7 @@ struct GridOps {
 
   // dst <- src^{-1} on the whole grid; returns 0, or 1 for a zero / non-finite pivot.
   __device__ int inverse(const double* src, double* dst, int n, double* logabsdet) {
-    inverse_group(w.gj[0], 0, gridDim.x, w.bar, src, dst, n);
+    inverse_group(w.gj[0], 0, gridDim.x, w.bar, &S.ep[0], src, dst, n);
     sync();
     *logabsdet = w.gj[0].result[0];
     const int st = w.gj[0].result[1] != 0.0;
@@ -456,9 +506,9 @@ struct GridOps {
       return a | b;
     }
     if ((int)blockIdx.x < half)
-      inverse_group(w.gj[0], 0, half, w.gj[0].bar, X, Xi, n);
+      inverse_group(w.gj[0], 0, half, w.gj[0].bar, &S.ep[1], X, Xi, n);
     else
-      inverse_group(w.gj[1], half, gridDim.x - half, w.gj[1].bar, Y, Yi, n);
+      inverse_group(w.gj[1], half, gridDim.x - half, w.gj[1].bar, &S.ep[2], Y, Yi, n);
     sync();
     *ldx = w.gj[0].result[0];
     *ldy = w.gj[1].result[0];

@@ -15,6 +15,8 @@ namespace lg {
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2) k_logm_large(SmallParams p, GridWs w, Slot M) {
   __shared__ GridSmem S;
+  if (threadIdx.x == 0) S.ep[0] = S.ep[1] = S.ep[2] = 0;
+  __syncthreads();
   GridOps ops{w, S, 0};
   for (int b = 0; b < p.count; ++b) {
     int n;
@@ -50,7 +52,7 @@ namespace {
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct GroupLayout {
-  size_t cand_v, cand_i, panel, R, piv, perm, work;
+  size_t cand_v, cand_i, cand_row, row_k, pivval, ldpart, panel, R, piv, perm, work;
 };
 
 struct LargeLayout {
@@ -62,16 +64,20 @@ LargeLayout large_layout(int n_max) {
   LargeLayout L{};
   size_t o = 0;
   const size_t nm = (size_t)n_max;
-  L.bar = o;      o = align256(o + 64);  // main barrier, error word, two group barriers
+  L.bar = o;      o = align256(o + 64);  // main barrier counter, error word, two group barrier counters
   L.partial = o;  o = align256(o + sizeof(double) * 2 * kMaxGrid);
   L.ipartial = o; o = align256(o + sizeof(int) * 2 * kMaxGrid);
   L.vec = o;      o = align256(o + sizeof(double) * 4 * nm);
   L.misc = o;     o = align256(o + sizeof(double) * 16);
   for (int t = 0; t < 2; ++t) {
     GroupLayout& g = L.g[t];
-    g.cand_v = o; o = align256(o + sizeof(double) * 2 * kMaxGrid);
+    g.cand_v = o; o = align256(o + sizeof(unsigned long long) * 2 * kMaxGrid);
     g.cand_i = o; o = align256(o + sizeof(int) * 2 * kMaxGrid);
-    g.panel = o;  o = align256(o + sizeof(double) * 2 * kGridPanel * nm);
+    g.cand_row = o; o = align256(o + sizeof(double) * 2 * kMaxGrid * kGridPanel);
+    g.row_k = o;  o = align256(o + sizeof(double) * 2 * kGridPanel);
+    g.pivval = o; o = align256(o + sizeof(double) * nm);
+    g.ldpart = o; o = align256(o + sizeof(double) * kMaxGrid);
+    g.panel = o;  o = align256(o + sizeof(double) * kGridPanel * nm);
     g.R = o;      o = align256(o + sizeof(double) * kGridPanel * nm);
     g.piv = o;    o = align256(o + sizeof(int) * nm);
     g.perm = o;   o = align256(o + sizeof(int) * nm);
@@ -88,7 +94,7 @@ template <int MODE>
 cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
   const LargeLayout L = large_layout(p.n_max);
   GridWs w{};
-  w.bar = reinterpret_cast<unsigned*>(ws + L.bar);
+  w.bar = reinterpret_cast<unsigned long long*>(ws + L.bar);
   w.err = reinterpret_cast<int*>(ws + L.bar + 8);
   w.partial = reinterpret_cast<double*>(ws + L.partial);
   w.ipartial = reinterpret_cast<int*>(ws + L.ipartial);
@@ -97,9 +103,13 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
   for (int t = 0; t < 2; ++t) {
     GjGroup& g = w.gj[t];
     const GroupLayout& gl = L.g[t];
-    g.bar = reinterpret_cast<unsigned*>(ws + L.bar + 16 + 8 * t);
-    g.cand_v = reinterpret_cast<double*>(ws + gl.cand_v);
+    g.bar = reinterpret_cast<unsigned long long*>(ws + L.bar + 16 + 8 * t);
+    g.cand_v = reinterpret_cast<unsigned long long*>(ws + gl.cand_v);
+    g.pivval = reinterpret_cast<double*>(ws + gl.pivval);
+    g.ldpart = reinterpret_cast<double*>(ws + gl.ldpart);
     g.cand_i = reinterpret_cast<int*>(ws + gl.cand_i);
+    g.cand_row = reinterpret_cast<double*>(ws + gl.cand_row);
+    g.row_k = reinterpret_cast<double*>(ws + gl.row_k);
     g.panel = reinterpret_cast<double*>(ws + gl.panel);
     g.R = reinterpret_cast<double*>(ws + gl.R);
     g.piv = reinterpret_cast<int*>(ws + gl.piv);
@@ -117,10 +127,24 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_logm_large<MODE>, kThreads, 0);
-  if (e != cudaSuccess) return e;
-  int grid = sms * (per_sm < 2 ? per_sm : 2);
-  if (grid > kMaxGrid) grid = kMaxGrid;
+  // Dynamic shared memory: two buffers of a block's panel rows, sized for the
+  // smallest group (half the grid). Two blocks per SM if they fit, else one.
+  int grid = 0;
+  size_t dyn = 0;
+  for (int want = 2; want >= 1 && grid == 0; --want) {
+    int gsz = sms * want;
+    if (gsz > kMaxGrid) gsz = kMaxGrid;
+    const int min_group = gsz / 2 >= 8 ? gsz / 2 : gsz;
+    const size_t d = 2 * (size_t)((p.n_max + min_group - 1) / min_group) * kGridPanel * sizeof(double);
+    e = cudaFuncSetAttribute(k_logm_large<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d);
+    if (e != cudaSuccess) continue;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_logm_large<MODE>, kThreads, d);
+    if (e != cudaSuccess) return e;
+    if (per_sm >= want) {
+      grid = gsz;
+      dyn = d;
+    }
+  }
   if (grid < 1) return cudaErrorLaunchOutOfResources;
   g_large_grid = grid;
 
@@ -128,7 +152,7 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   SmallParams pp = p;
   void* args[] = {&pp, &w, &M};
-  return cudaLaunchCooperativeKernel((const void*)k_logm_large<MODE>, dim3(grid), dim3(kThreads), args, 0, st);
+  return cudaLaunchCooperativeKernel((const void*)k_logm_large<MODE>, dim3(grid), dim3(kThreads), args, dyn, st);
 }
 
 }  // namespace
