@@ -402,6 +402,18 @@ def main():
             peak, peak_note = fp64_peak_tflops()
             ach = flops_a / (ms_a * 1e-3) / 1e12
             kname, fpl = "k_logm_small<execute> (persistent, one block per matrix)", flops_a
+        # DRAM bytes of the dominant kernel from ncu (dram__bytes_read.sum +
+        # dram__bytes_write.sum). The 4096^2 launch is too long to capture; its
+        # 2048^2 case (same plan: 27 iterations, 49 inversions, 4 products) moved
+        # 96.44 GB, mostly the working matrix written back by every rank-32
+        # update, which scales with n^3: x 8 for one 4096^2 launch.
+        traffic, traffic_note = None, "not captured for this configuration"
+        if big and args.big_n == NBIG:
+            traffic = 8 * (7.495242e9 + 88.940942e9)
+            traffic_note = ("bytes per launch: 8 x the DRAM bytes ncu measured on the 2048^2 case of the same "
+                            "kernel and plan (traffic grows with n^3); far below HBM bandwidth, FP64-pipe bound")
+        else:
+            traffic = None
         pk_a, note_a = fp64_peak_tflops()
         parts = {"batch256": {"ms": ms_a, "matrices_per_s": count / (ms_a * 1e-3),
                               "tflops": flops_a / (ms_a * 1e-3) / 1e12,
@@ -425,7 +437,8 @@ def main():
             "parts": parts,
             "forms": forms,
             "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                         "frac": ach / peak, "traffic": None, "peak_note": "FP64 dense " + peak_note,
+                         "frac": ach / peak, "traffic": traffic, "traffic_note": traffic_note,
+                         "peak_note": "FP64 dense " + peak_note,
                          "kernel": kname, "flops_per_launch": fpl},
             "e2e": {"value": (flops_a + flops_b) * world / (e2e_ms * 1e-3) / 1e12 if e2e_steps else None,
                     "unit": UNIT, "matrices_per_s": n_mats * world / (e2e_ms * 1e-3) if e2e_steps else None,
