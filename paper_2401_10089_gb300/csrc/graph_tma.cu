@@ -28,6 +28,7 @@
 
 #include "../../include/logm.h"
 #include "logm_internal.h"
+#include "scheme_f32.cuh"
 
 namespace lg {
 
@@ -64,106 +65,6 @@ constexpr int kTmStages = 2;
 // swizzle repeats every 8 rows = 1024 bytes). 96 KB per stage in both cases.
 constexpr int kTmStageBytes = 96 * 1024;
 constexpr size_t kTmSmemBytes = kTmStages * kTmStageBytes + 1024 /* barriers */ + 1024 /* alignment slack */;
-
-// ---------------------------------------------------------------------------
-// Scheme coefficients (the same tables as graph_tc.cu, written for this file)
-// ---------------------------------------------------------------------------
-static __constant__ float c_tm_h5[14] = {
-    7.363757032799957e-02f, -1.050281301619960e+00f, 8.897468955192446e-02f,
-    -1.599651928992725e-01f, 9.577281350989334e-01f, 5.394999133948797e-01f,
-    6.700731102561937e-02f, -5.158769100223212e-02f, 1.094308587350110e+00f,
-    1.027072285939197e-01f, -8.964023050065877e-03f, -2.100705663612491e-01f,
-    1.949655359168707e-01f, 1.117368056772713e+00f};
-static __constant__ float c_tm_g5[14] = {
-    -9.666134174379001e-01f, -4.395519034717933e-01f, 1.048664069004776e-01f,
-    1.585606124033259e-01f, 1.668066506920988e-01f, -8.025600931705978e-02f,
-    -1.159854366397558e-01f, 1.066554944706011e-01f, 1.127094008297975e+00f,
-    2.702180425508705e-01f, 4.137541209720699e-02f, 4.857347452405025e-01f,
-    -6.000256005636980e-01f, 1.063393233943084e+00f};
-static __constant__ float c_tm_y5[7] = {0.0f, 1.0f, 5.065546620208965e-01f, 3.832512052972577e-01f,
-                                        1.088307723749078e+00f, 2.787461897212877e-01f,
-                                        8.157421998489228e-01f};
-
-// k = 3, eq. (eqP8pol), solved in closed form (see logm_algo.cuh): c3, c4, d1, d2, e2, e0.
-static __device__ void tm_k3(float* c) {
-  const double c4 = 1.0 / sqrt(8.0);
-  const double c3 = 1.0 / (14.0 * c4);
-  const double sum = (1.0 / 6.0 - c3 * c3) / c4;
-  const double d1 = (1.0 / 5.0 - c3 * sum) / c4;
-  const double beta = sum - c4 * d1 / c3;
-  const double gamma = c3 * d1 + c4 / (3.0 * c3) - 0.25;
-  const double e2 = 0.5 * (beta + sqrt(beta * beta + 4.0 * gamma));
-  c[0] = (float)c3;
-  c[1] = (float)c4;
-  c[2] = (float)d1;
-  c[3] = (float)(sum - e2);
-  c[4] = (float)e2;
-  c[5] = (float)((1.0 / 3.0 - d1 * e2) / c3);
-}
-
-// Factor coefficients h, g of product j (index 0 = P_2) for a matrix with k products.
-static __device__ void tm_factors(int k, int j, float* h, float* g, int* terms) {
-  for (int t = 0; t < 6; ++t) h[t] = g[t] = 0.0f;
-  if (j == 1) {  // P_3 = X X
-    *terms = 1;
-    h[0] = g[0] = 1.0f;
-    return;
-  }
-  *terms = j;
-  if (k == 2) {  // P_4 = P_3 (X/3 + P_3/4)
-    h[1] = 1.0f;
-    g[0] = 1.0f / 3.0f;
-    g[1] = 0.25f;
-    return;
-  }
-  if (k == 3) {
-    float q[6];
-    tm_k3(q);
-    if (j == 2) {
-      h[1] = 1.0f;
-      g[0] = q[0];
-      g[1] = q[1];
-    } else {
-      h[0] = q[2];
-      h[1] = q[3];
-      h[2] = 1.0f;
-      g[1] = q[4];
-      g[2] = 1.0f;
-    }
-    return;
-  }
-  int t = 0;
-  for (int jj = 2; jj < j; ++jj) t += jj;
-  for (int i = 0; i < j; ++i) {
-    h[i] = c_tm_h5[t + i];
-    g[i] = c_tm_g5[t + i];
-  }
-}
-
-// y_2 .. y_{k+2} (index 0 = y_2).
-static __device__ float tm_y(int k, int i2) {
-  if (k == 1) return i2 == 0 ? 1.0f : (i2 == 1 ? 0.5f : 0.0f);
-  if (k == 2) return i2 == 0 ? 1.0f : (i2 == 1 ? 0.5f : (i2 == 2 ? 1.0f : 0.0f));
-  if (k == 3) {
-    if (i2 == 2) {
-      float q[6];
-      tm_k3(q);
-      return q[5];
-    }
-    return i2 == 0 ? 1.0f : (i2 == 1 ? 0.5f : (i2 == 3 ? 1.0f : 0.0f));
-  }
-  return c_tm_y5[i2 + 1];
-}
-
-static __device__ __forceinline__ int tm_needs(int k, int p3_given, int j) {
-  if (j == 1) return !p3_given;
-  if (k == 2) return j == 2;
-  if (k == 3) return j <= 3;
-  if (k == 5) return j <= 5;
-  return 0;
-}
-
-static __device__ __forceinline__ int tm_last(int k, int j) { return (k == 2 || k == 3 || k == 5) && j == k; }
 
 static __device__ __forceinline__ bool tm_skip(const GraphParams& p, int b) {
   return p.info_dev && (p.info_dev[b] == 1 || p.info_dev[b] == 4);
@@ -282,13 +183,15 @@ __global__ void __launch_bounds__(256) k_graph_pack(GraphParams p, int n_pad) {
   int64_t off;
   tm_geometry(p, b, &n, &off);
   const int k = p.k_dev[b];
-  if (tm_skip(p, b) || n < 1 || n > p.n_max || !tm_needs(k, p.p3_given, p.j)) return;
+  if (tm_skip(p, b) || n < 1 || n > p.n_max || !needs_product(k, p.p3_given, p.j)) return;
   const int tiles_x = n_pad / 32;
   const int ty0 = (blockIdx.x / tiles_x) * 32, tx0 = (blockIdx.x % tiles_x) * 32;
   if (ty0 >= n_pad) return;
-  float h[6], g[6];
-  int terms;
-  tm_factors(k, p.j, h, g, &terms);
+  Coeffs cf;
+  scheme_coeffs(k, p.j, cf);
+  const float* h = cf.h;
+  const float* g = cf.g;
+  const int terms = cf.terms;
   const int64_t nn_max = (int64_t)p.n_max * p.n_max;
   const float* P[6];
   for (int i = 0; i < 6; ++i) P[i] = p.gbuf + ((int64_t)b * 5 + (i < 4 ? i : 4)) * nn_max;
@@ -372,7 +275,7 @@ __global__ void __launch_bounds__(kTmThreads, 1)
   int64_t off;
   tm_geometry(p, b, &n, &off);
   const int k = p.k_dev[b];
-  if (tm_skip(p, b) || n < 1 || n > p.n_max || !tm_needs(k, p.p3_given, p.j)) return;
+  if (tm_skip(p, b) || n < 1 || n > p.n_max || !needs_product(k, p.p3_given, p.j)) return;
   const int n_tiles = (n_pad + nbox - 1) / nbox;
   const int m_tiles = (n + kTmM - 1) / kTmM;
   if ((int)blockIdx.x >= m_tiles * n_tiles) return;
@@ -457,13 +360,13 @@ __global__ void __launch_bounds__(kTmThreads, 1)
   const int failed = s_failed || !ok;
   if (!failed) {
     const int row = r0 + warp * 32 + lane;
-    const int last = tm_last(k, p.j);
+    const int last = is_last_product(k, p.j);
     const float scale = (last && p.s_dev) ? -ldexpf(1.0f, p.s_dev[b]) : 1.0f;
     float yv[6] = {0, 0, 0, 0, 0, 0};
     float ylast = 0.0f;
     if (last) {
-      for (int i = 0; i <= p.j - 1 && i < 5; ++i) yv[i] = tm_y(k, i);
-      ylast = tm_y(k, p.j);
+      for (int i = 0; i <= p.j - 1 && i < 5; ++i) yv[i] = scheme_y(k, i);
+      ylast = scheme_y(k, p.j);
     }
     const int64_t nn_max = (int64_t)p.n_max * p.n_max;
     const float* P[6];
