@@ -39,6 +39,53 @@ struct BlockOps {
     mat_vec(M, n, shift, x, y, trans);
   }
 
+  // Denman-Beavers update, eq. (ScalDB): X <- (mu X + Yi / mu) / 2, Y <- (mu Y +
+  // Xi / mu) / 2 (one thread per column); returns ||X_new - X_old||_1, ||X_new||_1.
+  __device__ void db_update(double* X, double* Y, const double* Xi, const double* Yi, double mu, double imu, int n,
+                            double* nd, double* nx) {
+    double sd = 0.0, sx = 0.0;
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      double cd = 0.0, cx = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const int64_t q = (int64_t)i * n + j;
+        const double xo = X[q];
+        const double xn = 0.5 * fma(mu, xo, Yi[q] * imu);
+        Y[q] = 0.5 * fma(mu, Y[q], Xi[q] * imu);
+        X[q] = xn;
+        cd += fabs(xn - xo);
+        cx += fabs(xn);
+      }
+      sd = nanmax(sd, cd);
+      sx = nanmax(sx, cx);
+    }
+    *nd = max(sd);
+    *nx = max(sx);
+  }
+
+  // Product-form update: X <- (mu X + XMi / mu) / 2 (XMi = I in the first step),
+  // M <- M^{-1}/(4 mu^2) + mu^2 M / 4 + I/2; returns ||X_new - X_old||_1, ||X_new||_1.
+  __device__ void db_update_product(double* X, double* Mk, const double* Mi, const double* XMi, bool first,
+                                    double mu, double imu, double mu2, double imu2, int n, double* nd, double* nx) {
+    double sd = 0.0, sx = 0.0;
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+      double cd = 0.0, cx = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const int64_t q = (int64_t)i * n + j;
+        const double xo = X[q];
+        const double xmi = first ? (i == j ? 1.0 : 0.0) : XMi[q];
+        const double xn = 0.5 * fma(mu, xo, xmi * imu);
+        Mk[q] = fma(0.25, fma(mu2, Mk[q], Mi[q] * imu2), i == j ? 0.5 : 0.0);
+        X[q] = xn;
+        cd += fabs(xn - xo);
+        cx += fabs(xn);
+      }
+      sd = nanmax(sd, cd);
+      sx = nanmax(sx, cx);
+    }
+    *nd = max(sd);
+    *nx = max(sx);
+  }
+
   __device__ void gemm(int n, const double* A, double as, const double* B, double bs, double alpha,
                        const EpiTerms& e, OutView out, bool ta = false, bool tb = false) {
     gemm_block(n, A, as, B, bs, alpha, e, out, S.u.gemm, ta, tb);

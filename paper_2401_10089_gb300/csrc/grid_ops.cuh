@@ -22,6 +22,7 @@
 namespace lg {
 
 constexpr int kGridPanel = 32;          // Gauss-Jordan panel width for large n
+constexpr int kColGroups = 16;          // row groups of the column passes (norms, transposed mat-vecs, updates)
 constexpr int kMaxGrid = 1024;          // upper bound on co-resident blocks
 constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s
 
@@ -48,6 +49,7 @@ struct GridWs {
   double* partial;   // [2][kMaxGrid] partial results of sum / max
   int* ipartial;     // [2][kMaxGrid] partial results of all / argmax indices
   double* vec;       // [4][n_max] estimator vectors
+  double* colpart;   // [2][kColGroups][n_max] partial column sums of the column passes
   double* misc;      // [8] broadcast slots
   GjGroup gj[2];     // the two inversion groups (gj[0] alone when one inversion uses the whole grid)
   int n_max;
@@ -186,18 +188,111 @@ struct GridOps {
 
   __device__ double* vec(int i) { return w.vec + (int64_t)i * w.n_max; }
 
+  // Column passes: with n columns and T threads, thread t takes column t % n
+  // and every R-th row from t / n (R = min(kColGroups, T / n) row groups), so
+  // that all threads work (one thread per column would leave most of a grid
+  // idle for n of a few thousand); the R partial sums per column meet in
+  // w.colpart after one barrier.
+  __device__ int col_groups(int n) const {
+    const int r = nthreads() / n;
+    return r < 1 ? 1 : (r > kColGroups ? kColGroups : r);
+  }
+
   __device__ double norm1(const double* M, int n, double shift) {
-    double best = 0.0;
-    for (int j = tid(); j < n; j += nthreads()) {
+    const int R = col_groups(n), t = tid();
+    if (t < n * R) {
+      const int j = t % n, r = t / n;
       double s = 0.0;
-      for (int i = 0; i < n; ++i) {
+      for (int i = r; i < n; i += R) {
         double v = M[(int64_t)i * n + j];
         if (i == j) v -= shift;
         s += fabs(v);
       }
+      w.colpart[(int64_t)r * n + j] = s;
+    }
+    sync();
+    double best = 0.0;
+    for (int j = t; j < n; j += nthreads()) {
+      double s = 0.0;
+      for (int r = 0; r < R; ++r) s += w.colpart[(int64_t)r * n + j];
       best = nanmax(best, s);
     }
     return max(best);
+  }
+
+  // Denman-Beavers update, eq. (ScalDB): X <- (mu X + Yi / mu) / 2, Y <- (mu Y +
+  // Xi / mu) / 2; returns ||X_new - X_old||_1 and ||X_new||_1.
+  __device__ void db_update(double* X, double* Y, const double* Xi, const double* Yi, double mu, double imu, int n,
+                            double* nd, double* nx) {
+    const int R = col_groups(n), t = tid();
+    double* cd_part = w.colpart;
+    double* cx_part = w.colpart + (int64_t)kColGroups * w.n_max;
+    if (t < n * R) {
+      const int j = t % n, r = t / n;
+      double cd = 0.0, cx = 0.0;
+      for (int i = r; i < n; i += R) {
+        const int64_t q = (int64_t)i * n + j;
+        const double xo = X[q];
+        const double xn = 0.5 * fma(mu, xo, Yi[q] * imu);
+        Y[q] = 0.5 * fma(mu, Y[q], Xi[q] * imu);
+        X[q] = xn;
+        cd += fabs(xn - xo);
+        cx += fabs(xn);
+      }
+      cd_part[(int64_t)r * n + j] = cd;
+      cx_part[(int64_t)r * n + j] = cx;
+    }
+    sync();
+    double sd = 0.0, sx = 0.0;
+    for (int j = t; j < n; j += nthreads()) {
+      double cd = 0.0, cx = 0.0;
+      for (int r = 0; r < R; ++r) {
+        cd += cd_part[(int64_t)r * n + j];
+        cx += cx_part[(int64_t)r * n + j];
+      }
+      sd = nanmax(sd, cd);
+      sx = nanmax(sx, cx);
+    }
+    *nd = max(sd);
+    *nx = max(sx);
+  }
+
+  // Product-form update: X <- (mu X + XMi / mu) / 2 (XMi = I in the first step),
+  // M <- M^{-1}/(4 mu^2) + mu^2 M / 4 + I/2; returns ||X_new - X_old||_1, ||X_new||_1.
+  __device__ void db_update_product(double* X, double* Mk, const double* Mi, const double* XMi, bool first,
+                                    double mu, double imu, double mu2, double imu2, int n, double* nd, double* nx) {
+    const int R = col_groups(n), t = tid();
+    double* cd_part = w.colpart;
+    double* cx_part = w.colpart + (int64_t)kColGroups * w.n_max;
+    if (t < n * R) {
+      const int j = t % n, r = t / n;
+      double cd = 0.0, cx = 0.0;
+      for (int i = r; i < n; i += R) {
+        const int64_t q = (int64_t)i * n + j;
+        const double xo = X[q];
+        const double xmi = first ? (i == j ? 1.0 : 0.0) : XMi[q];
+        const double xn = 0.5 * fma(mu, xo, xmi * imu);
+        Mk[q] = fma(0.25, fma(mu2, Mk[q], Mi[q] * imu2), i == j ? 0.5 : 0.0);
+        X[q] = xn;
+        cd += fabs(xn - xo);
+        cx += fabs(xn);
+      }
+      cd_part[(int64_t)r * n + j] = cd;
+      cx_part[(int64_t)r * n + j] = cx;
+    }
+    sync();
+    double sd = 0.0, sx = 0.0;
+    for (int j = t; j < n; j += nthreads()) {
+      double cd = 0.0, cx = 0.0;
+      for (int r = 0; r < R; ++r) {
+        cd += cd_part[(int64_t)r * n + j];
+        cx += cx_part[(int64_t)r * n + j];
+      }
+      sd = nanmax(sd, cd);
+      sx = nanmax(sx, cx);
+    }
+    *nd = max(sd);
+    *nx = max(sx);
   }
 
   __device__ void matvec(const double* M, int n, double shift, const double* x, double* y, int trans) {
@@ -212,15 +307,19 @@ struct GridOps {
         if (lane == 0) y[i] = s - shift * x[i];
       }
     } else {
-      for (int j = tid(); j < n; j += nthreads()) {
-        double s0 = 0.0, s1 = 0.0;
-        int i = 0;
-        for (; i + 1 < n; i += 2) {
-          s0 = fma(M[(int64_t)i * n + j], x[i], s0);
-          s1 = fma(M[(int64_t)(i + 1) * n + j], x[i + 1], s1);
-        }
-        if (i < n) s0 = fma(M[(int64_t)i * n + j], x[i], s0);
-        y[j] = (s0 + s1) - shift * x[j];
+      // y = M^T x - shift x as a column pass: partial sums over row groups
+      const int R = col_groups(n), t = tid();
+      if (t < n * R) {
+        const int j = t % n, r = t / n;
+        double s0 = 0.0;
+        for (int i = r; i < n; i += R) s0 = fma(M[(int64_t)i * n + j], x[i], s0);
+        w.colpart[(int64_t)r * n + j] = s0;
+      }
+      sync();
+      for (int j = t; j < n; j += nthreads()) {
+        double s0 = 0.0;
+        for (int r = 0; r < R; ++r) s0 += w.colpart[(int64_t)r * n + j];
+        y[j] = s0 - shift * x[j];
       }
     }
     sync();

@@ -431,23 +431,8 @@ static __device__ int db_sqrt(Ops& ops, Slot& M, int n, int max_db, int* iters_o
     const double mu = ops.bcast0(scale ? exp(-(ldx + ldy) / (2.0 * n)) : 1.0);
     const double imu = ops.bcast0(1.0 / mu);
     if (taped && ops.leader()) tape->mu[it - 1] = mu;
-    double sd = 0.0, sx = 0.0;
-    for (int j = ops.tid(); j < n; j += ops.nthreads()) {
-      double cd = 0.0, cx = 0.0;
-      for (int i = 0; i < n; ++i) {
-        const int64_t t = (int64_t)i * n + j;
-        const double xo = X[t];
-        const double xn = 0.5 * fma(mu, xo, Yi[t] * imu);
-        Y[t] = 0.5 * fma(mu, Y[t], Xi[t] * imu);
-        X[t] = xn;
-        cd += fabs(xn - xo);
-        cx += fabs(xn);
-      }
-      sd = nanmax(sd, cd);
-      sx = nanmax(sx, cx);
-    }
-    const double nd = ops.max(sd);
-    const double nx = ops.max(sx);
+    double nd, nx;
+    ops.db_update(X, Y, Xi, Yi, mu, imu, n, &nd, &nx);
     const double delta = nd / nx;
     if (!(delta == delta)) { status = 2; break; }
     if (delta <= tol) { status = 0; break; }
@@ -502,24 +487,8 @@ static __device__ int db_sqrt_product(Ops& ops, Slot& M, int n, int max_db, int*
       ops.tally(2, 1);
       ops.gemm(n, X, 0.0, Mi, 0.0, 1.0, none, OutView{XMi, 0});
     }
-    double sd = 0.0, sx = 0.0;
-    for (int j = ops.tid(); j < n; j += ops.nthreads()) {
-      double cd = 0.0, cx = 0.0;
-      for (int i = 0; i < n; ++i) {
-        const int64_t t = (int64_t)i * n + j;
-        const double xo = X[t];
-        const double xmi = (it > 1) ? XMi[t] : (i == j ? 1.0 : 0.0);
-        const double xn = 0.5 * fma(mu, xo, xmi * imu);
-        Mk[t] = fma(0.25, fma(mu2, Mk[t], Mi[t] * imu2), i == j ? 0.5 : 0.0);
-        X[t] = xn;
-        cd += fabs(xn - xo);
-        cx += fabs(xn);
-      }
-      sd = nanmax(sd, cd);
-      sx = nanmax(sx, cx);
-    }
-    const double nd = ops.max(sd);
-    const double nx = ops.max(sx);
+    double nd, nx;
+    ops.db_update_product(X, Mk, Mi, XMi, it == 1, mu, imu, mu2, imu2, n, &nd, &nx);
     const double delta = nd / nx;
     if (!(delta == delta)) { status = 2; break; }
     if (delta <= tol || pred <= tol) { status = 0; break; }

@@ -56,7 +56,7 @@ struct GroupLayout {
 };
 
 struct LargeLayout {
-  size_t bar, partial, ipartial, vec, misc, slot, total;
+  size_t bar, partial, ipartial, vec, colpart, misc, slot, total;
   GroupLayout g[2];
 };
 
@@ -68,6 +68,7 @@ LargeLayout large_layout(int n_max) {
   L.partial = o;  o = align256(o + sizeof(double) * 2 * kMaxGrid);
   L.ipartial = o; o = align256(o + sizeof(int) * 2 * kMaxGrid);
   L.vec = o;      o = align256(o + sizeof(double) * 4 * nm);
+  L.colpart = o;  o = align256(o + sizeof(double) * 2 * kColGroups * nm);
   L.misc = o;     o = align256(o + sizeof(double) * 16);
   for (int t = 0; t < 2; ++t) {
     GroupLayout& g = L.g[t];
@@ -99,6 +100,7 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
   w.partial = reinterpret_cast<double*>(ws + L.partial);
   w.ipartial = reinterpret_cast<int*>(ws + L.ipartial);
   w.vec = reinterpret_cast<double*>(ws + L.vec);
+  w.colpart = reinterpret_cast<double*>(ws + L.colpart);
   w.misc = reinterpret_cast<double*>(ws + L.misc);
   for (int t = 0; t < 2; ++t) {
     GjGroup& g = w.gj[t];
