@@ -73,3 +73,22 @@ def test_4096_triangular_similar_properties():
     print(f"n=4096 s={int(s[0])} k={int(k[0])} lower={lower:.3e} diag={dg:.3e}")
     # the FP64 path's bound (1e-12); measured 1.4e-13 and 5.5e-14 on GB300
     assert lower <= 1e-12 and dg <= 1e-12
+
+
+def test_large_status_codes():
+    """The whole-GPU kernel's per-matrix outcomes (n > 256): a zero matrix is
+    singular (info 1, NaN result), a NaN entry gives info 4, a square-root
+    cap that is too small gives info 3 with the capped s; the batch's other
+    matrices are unaffected."""
+    n = 260
+    good = workloads.identity_plus(1, n, seed=700, lo=0.5, hi=1.5)[0]
+    A = np.stack([good, np.zeros((n, n)), good.copy()])
+    A[2, 5, 7] = np.nan
+    L, s, k, info = lg().logm_execute(dev(A))
+    info = info.cpu().numpy()
+    assert info[0] == 0 and info[1] == 1 and info[2] == 4, info
+    Lh = L.cpu().numpy()
+    assert np.isnan(Lh[1]).all() and np.isnan(Lh[2]).all()
+    check_logm(A[0], Lh[0], int(s[0]), int(k[0]), int(info[0]))
+    L, s, k, info = lg().logm_execute(dev(A[:1]), max_sqrt=1)
+    assert int(info[0]) == 3 and int(s[0]) == 1
