@@ -410,7 +410,7 @@ struct GridOps {
   // log|det| and the status (0, or 1 for a zero / non-finite pivot) to
   // g.result.
   __device__ void inverse_group(GjGroup& g, int g0, int gn, unsigned long long* bar, unsigned long long* ep,
-                                const double* src, double* dst, int n, int first_jb = kGridPanel) {
+                                const double* src, double* dst, int n) {
     const int lb = blockIdx.x - g0;
     const int gt = lb * kThreads + threadIdx.x, gnt = gn * kThreads;
     const bool glead = lb == 0 && threadIdx.x == 0;
@@ -428,8 +428,8 @@ struct GridOps {
     double ld = 0.0;  // group leader
     int status = 0;
     bounded_barrier(bar, gn, w.err, ep);
-    for (int kb = 0, jw = first_jb; kb < n && !status; kb += jw, jw = kGridPanel) {
-      const int jb = min(jw, n - kb);
+    for (int kb = 0; kb < n && !status; kb += kGridPanel) {
+      const int jb = min(kGridPanel, n - kb);
       // own rows of W[:, J] -> shared memory; candidates of column kb; the
       // candidate's row and the row of pivot position kb are published
       {
