@@ -124,6 +124,19 @@ def test_plan_parity():
     assert (bool(fin[0]), int(k[0])) == (f_r, k_r) and abs(float(alpha[0]) - a_r) <= 1e-10 * a_r
 
 
+@pytest.mark.parametrize("k_max", [3, 5])
+def test_plan_parity_k_max(k_max):
+    # the order search's choice among k in {1, 2, 3, 5} (or {1, 2, 3}) near
+    # the identity, where every order is in play
+    rng = np.random.default_rng(31)
+    mats = [np.eye(30) + e * rng.standard_normal((30, 30)) / 30 for e in (1e-9, 1e-5, 3e-3, 8e-3, 0.05)]
+    A = np.stack(mats)
+    fin, k, alpha, info = lg().logm_plan(dev(A), k_max=k_max)
+    for b in range(A.shape[0]):
+        f_r, k_r, a_r = oracle.plan(A[b], k_max=k_max)
+        assert int(info[b]) == 0 and (bool(fin[b]), int(k[b])) == (f_r, k_r), (b, int(k[b]), k_r)
+
+
 def test_sqrt_parity():
     mats = np.stack([workloads.dense_32(seed=s) for s in range(4)])
     Ad = dev(mats)

@@ -477,3 +477,43 @@ def test_frechet_vs_finite_differences():
     h = 1e-6
     fd = (np.sum(W * oracle.logm(A + h * E)[0]) - np.sum(W * oracle.logm(A - h * E)[0])) / (2 * h)
     assert abs(np.sum(G * E) - fd) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_balance_zero_rows_and_columns_left_alone():
+    # a row or column whose off-diagonal part is zero gives no scaling factor
+    # (c = 0 or r = 0): such an index keeps d_i = 1; triangular 2 x 2 is the
+    # smallest case (column 0 and row 1 have zero off-diagonal parts).
+    A = np.array([[2.0, 1e6], [0.0, 3.0]])
+    B, d = oracle.balance(A)
+    assert np.array_equal(d, [1.0, 1.0]) and np.array_equal(B, A)
+    D = np.diag([4.0, 1.0, 0.25])
+    A = D @ np.array([[1.0, 2.0, 0.0], [3.0, 1.0, 0.0], [0.0, 0.0, 5.0]]) @ np.linalg.inv(D)
+    B, d = oracle.balance(A)
+    assert d[2] == 1.0 and B[2, 2] == 5.0
+
+
+def test_product_form_status_codes():
+    X, it, st = oracle.sqrtm_db(np.zeros((4, 4)), form=1)
+    assert st == oracle.SINGULAR
+    A = np.eye(3)
+    A[0, 1] = np.nan
+    assert oracle.logm(A, db_form=1)[1]["info"] == oracle.NONFINITE
+    assert oracle.logm(workloads.dense_32(), db_form=1, max_sqrt=1)[1]["info"] == oracle.MAX_SQRT
+
+
+def test_k3_forced_plan_matches_series():
+    # with s and k = 3 forced, the result is -2^s T_8(X) with X = I - A^{1/2^s}
+    # (the closed-form scheme, checked against the defining series of the
+    # square root's logarithm: for s = 0 directly against T_8)
+    rng = np.random.default_rng(55)
+    E = rng.standard_normal((10, 10))
+    E *= 0.01 / np.abs(E).sum(axis=0).max()
+    A = np.eye(10) + E
+    L, d = oracle.logm(A, force_s=0, force_k=3)
+    X = -(A - np.eye(10))  # exact (Sterbenz): the stored A, not E, is the input
+    T8 = np.zeros_like(X)
+    P = np.eye(10)
+    for i in range(1, 9):
+        P = P @ X
+        T8 += P / i
+    assert (d["s"], d["k"]) == (0, 3) and rel(L, -T8) < 1e-14
