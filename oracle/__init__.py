@@ -111,6 +111,7 @@ def lib():
             L.orc_inverse.argtypes = [i, p, p, p]
             L.orc_sqrtm_db.argtypes = [i, p, p, i, p]
             L.orc_sqrtm_db_product.argtypes = [i, p, p, i, p]
+            L.orc_sqrtm_db_reuse.argtypes = [i, p, p, i, p, p, d]
             L.orc_balance.argtypes = [i, p, p]
             L.orc_coeffs_k3.argtypes = [p]
             L.orc_graph_eval.argtypes = [i, i, p, p, p]
@@ -197,6 +198,17 @@ def sqrtm_db(A, max_iter=50, form=0):
     it = ctypes.c_int32()
     f = lib().orc_sqrtm_db_product if form == 1 else lib().orc_sqrtm_db
     st = f(A.shape[0], _ptr(A), _ptr(X), max_iter, ctypes.byref(it))
+    return X, it.value, st
+
+
+def sqrtm_db_reuse(A, Ainv, logabsdet, max_iter=50):
+    """(A^{1/2}, iterations, status) by eq. (ScalDB) with A^{-1} and log|det A|
+    given for the first step (as Algorithm 1's later roots have them)."""
+    A, Ainv = _c(A), _c(Ainv)
+    X = np.empty_like(A)
+    it = ctypes.c_int32()
+    st = lib().orc_sqrtm_db_reuse(A.shape[0], _ptr(A), _ptr(X), max_iter, ctypes.byref(it), _ptr(Ainv),
+                                   float(logabsdet))
     return X, it.value, st
 
 

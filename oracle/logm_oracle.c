@@ -37,6 +37,9 @@
  *    coefficients solved here in closed form; k = 5 is Table
  *    table_simple_experiment. k = 4 and k >= 6 have no coefficients in the
  *    paper, so the available orders are k in {1, 2, 3, 5};
+ *  - a root of a root: from the second level on, the first Denman-Beavers
+ *    step takes the previous level's converged Y as X_0^{-1} = A^{-1} (and
+ *    half the previous log|det|) instead of inverting A (eq. ScalDB form);
  *  - the balancing T of Algorithm 1 (optional) is diagonal scaling by powers
  *    of 2 (the Parlett-Reinsch iteration with 1-norms of the off-diagonal
  *    parts of rows and columns, no permutations), so that T^{-1} A T and
@@ -306,7 +309,13 @@ int orc_inverse(int n, const double* A, double* Ainv, double* logabsdet) {
 /* Y_{k+1} = (mu_k Y_k + mu_k^{-1} X_k^{-1}) / 2,                           */
 /* X_0 = A, Y_0 = I, mu_k = |det X_k det Y_k|^{-1/(2n)}.                    */
 /* ------------------------------------------------------------------------ */
-int orc_sqrtm_db(int n, const double* A, double* Xout, int max_iter, int32_t* iters) {
+/* The iteration of eq. (ScalDB). With x0inv given, it is taken as X_0^{-1}
+ * = A^{-1} and ld0 as log|det A| in the first step instead of inverting A
+ * (Algorithm 1 takes a root of the previous level's root: the previous
+ * level's Y converged to that root's inverse). Yout (or NULL) receives the
+ * final Y, *ld0_out the log|det A| used. */
+static int db_core(int n, const double* A, double* Xout, int max_iter, int32_t* iters, const double* x0inv,
+                   double ld0, double* Yout, double* ld0_out) {
   double* X = alloc_mat(n);
   double* Y = alloc_mat(n);
   double* Xi = alloc_mat(n);
@@ -321,10 +330,16 @@ int orc_sqrtm_db(int n, const double* A, double* Xout, int max_iter, int32_t* it
   const size_t nn = (size_t)n * n;
   for (it = 1; it <= max_iter; ++it) {
     double ldx, ldy;
-    if (orc_inverse(n, X, Xi, &ldx) != ORC_OK || orc_inverse(n, Y, Yi, &ldy) != ORC_OK) {
+    if (it == 1 && x0inv) {
+      memcpy(Xi, x0inv, sizeof(double) * nn);
+      ldx = ld0;
+      set_identity(n, Yi);
+      ldy = 0.0;
+    } else if (orc_inverse(n, X, Xi, &ldx) != ORC_OK || orc_inverse(n, Y, Yi, &ldy) != ORC_OK) {
       status = ORC_SINGULAR;
       break;
     }
+    if (it == 1 && ld0_out) *ld0_out = ldx;
     /* mu = |det X det Y|^{-1/(2n)} = exp(-(log|det X| + log|det Y|)/(2n)). */
     double mu = scale ? exp(-(ldx + ldy) / (2.0 * n)) : 1.0;
     for (size_t t = 0; t < nn; ++t) {
@@ -358,6 +373,7 @@ int orc_sqrtm_db(int n, const double* A, double* Xout, int max_iter, int32_t* it
   }
   if (iters) *iters = it > max_iter ? max_iter : it;
   memcpy(Xout, X, sizeof(double) * nn);
+  if (Yout) memcpy(Yout, Y, sizeof(double) * nn);
   free(X);
   free(Y);
   free(Xi);
@@ -365,6 +381,15 @@ int orc_sqrtm_db(int n, const double* A, double* Xout, int max_iter, int32_t* it
   free(Xn);
   free(D);
   return status;
+}
+
+int orc_sqrtm_db(int n, const double* A, double* Xout, int max_iter, int32_t* iters) {
+  return db_core(n, A, Xout, max_iter, iters, NULL, 0.0, NULL, NULL);
+}
+
+int orc_sqrtm_db_reuse(int n, const double* A, double* Xout, int max_iter, int32_t* iters, const double* Ainv,
+                       double logabsdet) {
+  return db_core(n, A, Xout, max_iter, iters, Ainv, logabsdet, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -880,6 +905,9 @@ static int logm_core(int n, const double* A, double* L, const orc_opts* o, orc_d
   double* B = alloc_mat(n);
   double* AI2 = alloc_mat(n);
   double* Z = alloc_mat(n);
+  double* Yprev = alloc_mat(n);
+  int have_yprev = 0;
+  double ld_prev = 0.0;
   memcpy(Acur, A, sizeof(double) * nn);
   memcpy(B, A, sizeof(double) * nn);
   for (int i = 0; i < n; ++i) B[(size_t)i * n + i] -= 1.0;
@@ -902,11 +930,21 @@ static int logm_core(int n, const double* A, double* L, const orc_opts* o, orc_d
       last = st;
       if (finish) break;
     }
-    /* A_2 <- A; A <- A^{1/2} by eq. (ScalDB); A_I2 = A_2 - 2A + I (eq. AI2). */
+    /* A_2 <- A; A <- A^{1/2} by eq. (ScalDB); A_I2 = A_2 - 2A + I (eq. AI2).
+     * From the second level on, the first step's A^{-1} is the previous
+     * level's Y (converged to A_2^{-1/2} = A^{-1} of this level's A) and
+     * log|det A| is half the previous level's. */
     memcpy(A2, Acur, sizeof(double) * nn);
     int32_t it = 0;
-    int r = o->db_form == 1 ? orc_sqrtm_db_product(n, A2, Acur, o->max_db_iter, &it)
-                            : orc_sqrtm_db(n, A2, Acur, o->max_db_iter, &it);
+    int r;
+    if (o->db_form == 1) {
+      r = orc_sqrtm_db_product(n, A2, Acur, o->max_db_iter, &it);
+    } else {
+      double ld_used = 0.0;
+      r = db_core(n, A2, Acur, o->max_db_iter, &it, have_yprev ? Yprev : NULL, ld_prev, Yprev, &ld_used);
+      have_yprev = (r == ORC_OK);
+      ld_prev = 0.5 * ld_used;
+    }
     dd.db_iters += it;
     if (r == ORC_SINGULAR) {
       info = ORC_SINGULAR;
@@ -959,6 +997,7 @@ static int logm_core(int n, const double* A, double* L, const orc_opts* o, orc_d
   free(B);
   free(AI2);
   free(Z);
+  free(Yprev);
   return info;
 }
 

@@ -67,6 +67,9 @@ int orc_lu(int n, double* LU, int32_t* piv);
 int orc_inverse(int n, const double* A, double* Ainv, double* logabsdet);
 int orc_sqrtm_db(int n, const double* A, double* X, int max_iter, int32_t* iters);
 int orc_sqrtm_db_product(int n, const double* A, double* X, int max_iter, int32_t* iters);
+/* eq. (ScalDB) with a known A^{-1} and log|det A| for the first step. */
+int orc_sqrtm_db_reuse(int n, const double* A, double* X, int max_iter, int32_t* iters, const double* Ainv,
+                       double logabsdet);
 void orc_balance(int n, double* A, double* d);
 double orc_normest_pow(int n, const double* B, const double* AI2, int p);
 int orc_graph_eval(int n, int k, const double* X, const double* P3, double* Z);

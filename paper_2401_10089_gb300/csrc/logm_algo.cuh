@@ -406,9 +406,14 @@ struct DbTape {
 };
 
 template <class Ops>
-static __device__ int db_sqrt(Ops& ops, Slot& M, int n, int max_db, int* iters_out, const DbTape* tape = nullptr) {
+static __device__ int db_sqrt(Ops& ops, Slot& M, int n, int max_db, int* iters_out, const DbTape* tape = nullptr,
+                              int reuse = 0, double* ld_io = nullptr) {
   double* X = M.Acur;
   double* Y = M.Y;
+  // reuse (a root of the previous level's root, no tape): M.Y still holds the
+  // previous level's converged Y, which is A^{-1} of this level's A; it stands
+  // in for the first step's inversion, and *ld_io holds log|det A|
+  if (reuse) copy_matrix(ops, M.W1, Y, n);
   identity_matrix(ops, Y, n);
   const double tol = 10.0 * sqrt((double)n) * kUnitRoundoff;
   int scale = 1, status = 2, it;
@@ -416,12 +421,18 @@ static __device__ int db_sqrt(Ops& ops, Slot& M, int n, int max_db, int* iters_o
   for (it = 1; it <= max_db; ++it) {
     double ldx, ldy;
     ops.tally(0, 1);
-    ops.tally(1, (it == 1) ? 1 : 2);
+    ops.tally(1, (it == 1) ? (reuse ? 0 : 1) : 2);
     const bool taped = tape && it - 1 < tape->cap;
     double* Xi = taped ? tape->inv + (int64_t)(2 * (it - 1)) * tape->stride : M.W1;
     double* Yi = taped ? tape->inv + (int64_t)(2 * (it - 1) + 1) * tape->stride : M.W2;
     if (it == 1) {
-      if (ops.inverse(X, Xi, n, &ldx)) { status = 1; break; }
+      if (reuse) {
+        ldx = *ld_io;  // Xi (= M.W1) was filled above
+      } else if (ops.inverse(X, Xi, n, &ldx)) {
+        status = 1;
+        break;
+      }
+      if (ld_io) *ld_io = 0.5 * ldx;  // log|det| of the root, for the next level
       // Y_0 = I: its inverse is I and log|det Y_0| = 0 exactly.
       identity_matrix(ops, Yi, n);
       ldy = 0.0;
@@ -681,6 +692,8 @@ static __device__ void run_execute(Ops& ops, const SmallParams& p, int b, int n,
   int s = 0, have_ai2 = 0, info = 0, finish = nB <= th;
   double alpha = nB;
   EstState last{-1.0, -1.0, m, 0};
+  int reuse = 0;          // the previous level's Y can replace the next first inversion
+  double ld_carry = 0.0;  // log|det| of the next level's A
   while (!finish && s < p.max_sqrt) {
     EstState st{-1.0, -1.0, m, 0};
     finish = alpha_test(ops, M.Acur, have_ai2 ? M.A2 : nullptr, n, nB, nI2, m, th, st, &alpha);
@@ -692,7 +705,9 @@ static __device__ void run_execute(Ops& ops, const SmallParams& p, int b, int n,
     }
     copy_matrix(ops, M.A2, M.Acur, n);
     int it;
-    const int r = p.db_form == 1 ? db_sqrt_product(ops, M, n, p.max_db, &it) : db_sqrt(ops, M, n, p.max_db, &it);
+    const int r = p.db_form == 1 ? db_sqrt_product(ops, M, n, p.max_db, &it)
+                                 : db_sqrt(ops, M, n, p.max_db, &it, nullptr, reuse, &ld_carry);
+    reuse = p.db_form != 1 && r == 0;
     if (r == 1) { info = 1; break; }
     if (r == 2 && info == 0) info = 2;
     ai2_from(ops, M, n);

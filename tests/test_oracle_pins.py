@@ -517,3 +517,16 @@ def test_k3_forced_plan_matches_series():
         P = P @ X
         T8 += P / i
     assert (d["s"], d["k"]) == (0, 3) and rel(L, -T8) < 1e-14
+
+
+def test_sqrt_with_known_inverse():
+    # Algorithm 1's second and later roots start from the previous level's
+    # converged Y as A^{-1}: the same iteration as inverting A, to rounding
+    A = workloads.spd(1, 30, seed=56, lo=0.05, hi=20.0)[0]
+    Ainv, ld, st = oracle.inverse(A)
+    X0, it0, st0 = oracle.sqrtm_db(A)
+    X1, it1, st1 = oracle.sqrtm_db_reuse(A, Ainv, ld)
+    assert st0 == st1 == oracle.OK and it0 == it1 and rel(X1, X0) < 1e-14
+    # and the previous root's Y is that inverse: sqrt(sqrt(A)) via the chain
+    L0, d0 = oracle.logm(A)
+    assert d0["s"] >= 2 and rel(L0, sla.logm(A).real) < 1e-12
