@@ -40,7 +40,7 @@ typedef struct {
 
 typedef struct {
   int32_t s;              /* square roots taken */
-  int32_t k;              /* graph products used (1, 2 or 5) */
+  int32_t k;              /* graph products used (1, 2, 3 or 5) */
   int32_t info;           /* ORC_* status */
   int32_t db_iters;       /* total Denman-Beavers iterations over all levels */
   int32_t n_estimates;    /* calls of the 1-norm power estimator */
