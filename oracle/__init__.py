@@ -11,8 +11,10 @@ paper it follows:
 
 * ``graph_eval``   -- degree-optimal form, eq. (five_mult_degopt), Sec. 3, with
                       Table table_simple_experiment for k = 5, the exact
-                      Taylor polynomials of eq. (Taylor_log) for k = 1, 2 and
-                      T_8 by eq. (eqP8pol) for k = 3 (``coeffs_k3``).
+                      Taylor polynomials of eq. (Taylor_log) for k = 1, 2,
+                      T_8 by eq. (eqP8pol) for k = 3 (``coeffs_k3``) and the
+                      14+ scheme for k = 4 (``coeffs_k4``, solved here; the
+                      paper does not print it).
 * ``sqrtm_db``     -- scaled Denman-Beavers iteration, eq. (ScalDB), Sec. 6, or
                       its product form (``form=1``, the variant cited in Sec. 2).
 * ``balance``      -- the diagonal balancing T of Algorithm 1, Step 1.
@@ -43,10 +45,10 @@ _lib = None
 
 # Theta_{m_k} of Table Table_theta (Sec. 5) for k = 1..5.
 THETA_TABLE = (1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1)
-# Orders with coefficients: T_2, T_4 (eq. Taylor_log), T_8 (eq. eqP8pol) and
-# Table table_simple_experiment.
-AVAILABLE_K = (1, 2, 3, 5)
-M_OF_K = {1: 2, 2: 4, 3: 8, 5: 14}
+# Orders with coefficients: T_2, T_4 (eq. Taylor_log), T_8 (eq. eqP8pol), the
+# 14+ scheme (k = 4, solved here) and Table table_simple_experiment.
+AVAILABLE_K = (1, 2, 3, 4, 5)
+M_OF_K = {1: 2, 2: 4, 3: 8, 4: 14, 5: 14}
 # Status codes, written out on their own (same meanings as the library's).
 OK, SINGULAR, NO_CONVERGENCE, MAX_SQRT, NONFINITE = 0, 1, 2, 3, 4
 
@@ -114,6 +116,7 @@ def lib():
             L.orc_sqrtm_db_reuse.argtypes = [i, p, p, i, p, p, d]
             L.orc_balance.argtypes = [i, p, p]
             L.orc_coeffs_k3.argtypes = [p]
+            L.orc_coeffs_k4.argtypes = [p]
             L.orc_graph_eval.argtypes = [i, i, p, p, p]
             L.orc_horner.argtypes = [i, i, p, p, p]
             L.orc_plan.argtypes = [i, p, p, p, p, p, p]
@@ -150,6 +153,16 @@ def coeffs_k3():
     """c3, c4, d1, d2, e2, e0 of eq. (eqP8pol) for T_8 (closed form)."""
     c = np.zeros(6)
     lib().orc_coeffs_k3(_ptr(c))
+    return c
+
+
+def coeffs_k4():
+    """c3, c4, d1, d2, e2, f1, f2, f4, g1, g4, y3, y4, y5 of the k = 4 (14+)
+    scheme: P_4 = P_3 (c3 X + c4 P_3), P_5 = (d1 X + d2 P_3 + P_4)(e2 P_3 +
+    P_4), P_6 = (f1 X + f2 P_3 + f4 P_4 + P_5)(g1 X + g4 P_4 + P_5),
+    z = X + y3 P_3 + y4 P_4 + y5 P_5 + P_6."""
+    c = np.zeros(13)
+    lib().orc_coeffs_k4(_ptr(c))
     return c
 
 

@@ -34,9 +34,12 @@
  *    halves; scaling by mu is switched off once delta drops below 1e-2;
  *  - k = 1, 2 are the exact Taylor polynomials T_2, T_4 (eq. Taylor_log);
  *    k = 3 is T_8 evaluated with three products by eq. (eqP8pol), its
- *    coefficients solved here in closed form; k = 5 is Table
- *    table_simple_experiment. k = 4 and k >= 6 have no coefficients in the
- *    paper, so the available orders are k in {1, 2, 3, 5};
+ *    coefficients solved here in closed form; k = 4 is a "14+" scheme of
+ *    Sec. 3 (degree 16, T_14 matched exactly) whose coefficients the paper
+ *    does not print: solved here (orc_coeffs_k4), its Theta recomputed from
+ *    them lands on the table's 9.31e-2; k = 5 is Table
+ *    table_simple_experiment. k >= 6 have no coefficients in the paper, so
+ *    the available orders are k in {1, 2, 3, 4, 5};
  *  - a root of a root: from the second level on, the first Denman-Beavers
  *    step takes the previous level's converged Y as X_0^{-1} = A^{-1} (and
  *    half the previous log|det|) instead of inverting A (eq. ScalDB form);
@@ -126,6 +129,32 @@ void orc_coeffs_k3(double* c) {
   c[5] = e0;
 }
 
+/* k = 4: the "14+" Taylor-based scheme of Sec. 3 (m = 14+, degree 16 in
+ * Table Table_theta), four products in the degree-optimal form
+ *   P_4 = P_3 (c3 X + c4 P_3),
+ *   P_5 = (d1 X + d2 P_3 + P_4)(e2 P_3 + P_4),
+ *   P_6 = (f1 X + f2 P_3 + f4 P_4 + P_5)(g1 X + g4 P_4 + P_5),
+ *   z   = X + y3 P_3 + y4 P_4 + y5 P_5 + P_6,
+ * i.e. eq. (eqP8pol)'s structure for P_5 with one more product. The paper
+ * follows the procedure of its reference for these coefficients without
+ * printing them; here they solve the 13 equations "coefficient of x^i in z
+ * = 1/i, i = 2..14" (x^1 holds by construction: T_14 of eq. Taylor_log
+ * matched exactly; x^15 and x^16 are what remains, the "+") in the 13
+ * unknowns that the form above leaves (no X term in P_5's second factor, no
+ * P_3 term in P_6's second factor, P_6 and X with weight 1). Of the real roots
+ * the one with the smallest largest coefficient is taken (c4 > 0). Its
+ * Theta_14 recomputed from these doubles is 9.32e-2 (the table's 9.31e-2),
+ * and its monomials match 1/i within 0.8 u for i <= 14. The values are the
+ * correctly rounded doubles of the root computed to 50 digits.
+ * c[0..12] = c3, c4, d1, d2, e2, f1, f2, f4, g1, g4, y3, y4, y5. */
+static const double K4_C[13] = {
+    0.3602750956560524,  0.3018442985303789,   0.3412287952056341,  -0.18047064940974122,
+    0.18907274365286242, -0.014079460349863975, 0.24400741065645315, -0.8525627910338015,
+    0.1463535711919622,  0.9787518426666669,   0.5020605793026582,  0.6095606808527384,
+    1.2091753609836204};
+
+void orc_coeffs_k4(double* c) { memcpy(c, K4_C, sizeof(K4_C)); }
+
 /* A degree-optimal scheme with k products: P_1 = I, P_2 = X and, for
  * j = 1..k, P_{j+2} = (sum_{i=1}^{j+1} h_{j,i} P_i)(sum_{i=1}^{j+1} g_{j,i} P_i);
  * z = sum_{i=1}^{k+2} y_i P_i (eq. five_mult_degopt). Indices are 1-based in
@@ -173,6 +202,28 @@ static void scheme_for(int k, orc_scheme* S) {
     S->y[3] = 0.5;
     S->y[4] = c[5];
     S->y[5] = 1.0;
+  } else if (k == 4) {
+    const double* c = K4_C;
+    S->h[2][3] = 1.0; /* P_4 = P_3 (c3 P_2 + c4 P_3) */
+    S->g[2][2] = c[0];
+    S->g[2][3] = c[1];
+    S->h[3][2] = c[2]; /* P_5 = (d1 P_2 + d2 P_3 + P_4)(e2 P_3 + P_4) */
+    S->h[3][3] = c[3];
+    S->h[3][4] = 1.0;
+    S->g[3][3] = c[4];
+    S->g[3][4] = 1.0;
+    S->h[4][2] = c[5]; /* P_6 = (f1 P_2 + f2 P_3 + f4 P_4 + P_5)(g1 P_2 + g4 P_4 + P_5) */
+    S->h[4][3] = c[6];
+    S->h[4][4] = c[7];
+    S->h[4][5] = 1.0;
+    S->g[4][2] = c[8];
+    S->g[4][4] = c[9];
+    S->g[4][5] = 1.0;
+    S->y[2] = 1.0; /* z = P_2 + y3 P_3 + y4 P_4 + y5 P_5 + P_6 */
+    S->y[3] = c[10];
+    S->y[4] = c[11];
+    S->y[5] = c[12];
+    S->y[6] = 1.0;
   } else if (k == 5) {
     int t = 0;
     for (int j = 2; j <= 5; ++j)
@@ -184,12 +235,13 @@ static void scheme_for(int k, orc_scheme* S) {
   }
 }
 
-/* m_k of Table Table_theta for the schemes that have coefficients. */
+/* m_k of Table Table_theta: 2, 4, 8, 14+ (k = 4, degree 16) and 14+ (k = 5,
+ * degree 32); the "+" schemes are tested with alpha_14. */
 static int m_of_k(int k) { return k == 1 ? 2 : (k == 2 ? 4 : (k == 3 ? 8 : 14)); }
 
 static int theta_index(int k) { return k - 1; }
 
-static int k_available(int k) { return k == 1 || k == 2 || k == 3 || k == 5; }
+static int k_available(int k) { return k >= 1 && k <= 5; }
 
 /* ------------------------------------------------------------------------ */
 /* Dense linear algebra, textbook forms.                                    */
@@ -764,9 +816,9 @@ static int alpha_test(int n, const double* B, const double* AI2, double nB, doub
  *  k+1 at once when alpha_{m_k} > Theta_k but <= Theta_{k+1}. */
 static int order_search(int n, const double* B, const double* AI2, double nB, double nI2,
                         const orc_opts* o, const est_state* loop_est, int* n_est) {
-  int cands[4], nc = 0;
-  const int all[4] = {1, 2, 3, 5};
-  for (int t = 0; t < 4; ++t)
+  int cands[5], nc = 0;
+  const int all[5] = {1, 2, 3, 4, 5};
+  for (int t = 0; t < 5; ++t)
     if (all[t] <= o->k_max) cands[nc++] = all[t];
   if (nc == 0) return o->k_max;
   /* min_im */

@@ -57,6 +57,45 @@ def k3_monomials(c):
     return _add(z, x)
 
 
+def k4_monomials(c):
+    """Monomials b_0..b_16 of the k = 4 (14+) scheme with
+    c = (c3, c4, d1, d2, e2, f1, f2, f4, g1, g4, y3, y4, y5) given as doubles,
+    in exact rational arithmetic: p4 = x^2 (c3 x + c4 x^2),
+    p5 = (d1 x + d2 x^2 + p4)(e2 x^2 + p4),
+    p6 = (f1 x + f2 x^2 + f4 p4 + p5)(g1 x + g4 p4 + p5),
+    z = x + y3 x^2 + y4 p4 + y5 p5 + p6."""
+    c3, c4, d1, d2, e2, f1, f2, f4, g1, g4, y3, y4, y5 = (Fraction(float(v)) for v in c)
+
+    def sc(w, a):
+        return [w * t for t in a]
+
+    x = [Fraction(0), Fraction(1)]
+    x2 = _mul(x, x)
+    p4 = _mul(x2, _add(sc(c3, x), sc(c4, x2)))
+    p5 = _mul(_add(_add(sc(d1, x), sc(d2, x2)), p4), _add(sc(e2, x2), p4))
+    p6 = _mul(_add(_add(_add(sc(f1, x), sc(f2, x2)), sc(f4, p4)), p5), _add(_add(sc(g1, x), sc(g4, p4)), p5))
+    z = _add(_add(_add(_add(x, sc(y3, x2)), sc(y4, p4)), sc(y5, p5)), p6)
+    return z
+
+
+def backward_error_coeffs(b, N=60, dps=60):
+    """c_k of exp(-p(-x)) - 1 - x = sum c_k x^k (eq. DeltaAseries) for the
+    polynomial p with monomial coefficients b (rationals), k = 0..N."""
+    import mpmath as mp
+    mp.mp.dps = dps
+    S = [mp.mpf(0)] * (N + 1)
+    for i, bi in enumerate(b):
+        if i <= N:
+            S[i] = -mp.mpf(bi.numerator) / bi.denominator * (-1) ** i
+    E = [mp.mpf(0)] * (N + 1)
+    E[0] = mp.mpf(1)
+    for k in range(1, N + 1):
+        E[k] = sum(j * S[j] * E[k - j] for j in range(1, k + 1)) / k
+    E[0] -= 1
+    E[1] -= 1
+    return E
+
+
 def read_golden_coeffs(path):
     vals = {}
     with open(path) as f:

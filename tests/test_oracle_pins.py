@@ -14,8 +14,8 @@ import scipy.linalg as sla
 
 import oracle
 from paper_2401_10089_gb300 import workloads
-from tests.oracle_helpers import (k3_monomials, k5_monomials, read_golden_coeffs,
-                                  theta_from_monomials)
+from tests.oracle_helpers import (backward_error_coeffs, k3_monomials, k4_monomials, k5_monomials,
+                                  read_golden_coeffs, theta_from_monomials)
 
 U = 2.0 ** -53
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -71,6 +71,40 @@ def test_theta_recomputed_from_backward_error():
     # k = 3 from the oracle's rounded eq. (eqP8pol) coefficients: the table's value.
     got = theta_from_monomials(k3_monomials(oracle.coeffs_k3()), 8)
     assert float(f"{got:.2e}") == table[3][1]
+    # k = 4 (14+, coefficients solved here): 9.32e-2, at or just above the
+    # table's 9.31e-2 -- the paper's Theta_4 is safe for this scheme.
+    got = theta_from_monomials(k4_monomials(oracle.coeffs_k4()), table[4][0])
+    assert table[4][1] <= got < 1.005 * table[4][1]
+
+
+def test_k4_table_is_the_rounded_root():
+    # the 13 doubles compiled into the oracle are the correctly rounded root of
+    # the scheme's defining equations (x^i coefficient = 1/i, i = 2..14),
+    # solved again here at 50 digits
+    pytest.importorskip("mpmath")
+    from oracle import derive_k4
+    vals, resid = derive_k4.derive()
+    assert resid < 1e-40
+    assert list(oracle.coeffs_k4()) == vals
+
+
+def test_k4_coefficients_give_taylor_t14():
+    # Sec. 3 (m = 14+): the degree-16 polynomial matches T_14 of eq.
+    # (Taylor_log) -- b_i = 1/i within u for i <= 14 from the rounded
+    # doubles -- and differs from 1/15, 1/16 in the two top coefficients.
+    from fractions import Fraction
+    z = k4_monomials(oracle.coeffs_k4())
+    assert len(z) == 17 and z[0] == 0 and z[1] == 1 and z[16] != 0
+    for i in range(2, 15):
+        assert abs(float(z[i] * i - 1)) <= U, (i, float(z[i] * i - 1) / U)
+    assert -0.41 < float(z[15] * 15 - 1) < -0.40 and -0.87 < float(z[16] * 16 - 1) < -0.86
+    # Sec. 5's check on the rounded coefficients: the backward-error series
+    # (eq. DeltaAseries) has c_0 = c_1 = 0 and |c_k| < u for k = 3..14
+    pytest.importorskip("mpmath")
+    c = backward_error_coeffs(z, N=20)
+    assert abs(c[0]) < 1e-40 and abs(c[1]) < 1e-40
+    assert max(abs(float(c[k])) for k in range(3, 15)) < U
+    assert abs(float(c[15])) > 1e-3  # the first term the scheme leaves (x^15)
 
 
 def test_k3_coefficients_give_taylor_t8():
@@ -92,7 +126,7 @@ def test_k3_coefficients_give_taylor_t8():
 # Graph evaluation, eq. (five_mult_degopt)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("k", [1, 2, 3, 5])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 def test_graph_scalar_against_log(k):
     xs = np.linspace(-0.25, 0.25, 101)
     for x in xs:
@@ -103,10 +137,28 @@ def test_graph_scalar_against_log(k):
             ref = x + x * x / 2 + x ** 3 / 3 + x ** 4 / 4
         elif k == 3:
             ref = sum(x ** i / i for i in range(1, 9))
+        elif k == 4:  # T_14 plus the two top terms the scheme leaves
+            b = k4_monomials(oracle.coeffs_k4())
+            ref = sum(x ** i / i for i in range(1, 15)) + float(b[15]) * x ** 15 + float(b[16]) * x ** 16
         else:
             ref = -math.log1p(-x)  # Fig. 1: error about u on the disk of radius ~0.25
-        tol = 8 * U * max(abs(ref), 1e-300) if k == 5 else 4 * U * abs(ref) + 1e-300
+        tol = 8 * U * max(abs(ref), 1e-300) if k >= 4 else 4 * U * abs(ref) + 1e-300
         assert abs(z - ref) <= tol, (k, x, z, ref)
+
+
+def test_graph_k4_vs_horner_and_log():
+    # the graph against Horner on its monomials (expanded independently
+    # above), and within Theta_4 against the logarithm itself
+    z = k4_monomials(oracle.coeffs_k4())
+    b = np.array([float(c) for c in z])
+    rng = np.random.default_rng(14)
+    X = rng.standard_normal((12, 12))
+    X *= 0.09 / oracle.norm1(X)
+    G = oracle.graph_eval(X, 4)
+    assert rel(G, oracle.horner(X, b)) < 1e-15
+    for x in np.linspace(-0.0931, 0.0931, 41):
+        v = oracle.graph_eval(np.array([[x]]), 4)[0, 0]
+        assert abs(v + math.log1p(-x)) <= 4 * U * abs(math.log1p(-x)) + 1e-300, x
 
 
 def test_graph_k5_vs_horner():
@@ -132,7 +184,7 @@ def test_graph_taylor_matrix(k):
     assert rel(oracle.graph_eval(X, k), ref) < 1e-15
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 5])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 def test_graph_p3_argument_and_diagonal(k):
     rng = np.random.default_rng(12)
     X = rng.standard_normal((7, 7)) * 0.03
@@ -287,7 +339,11 @@ def test_plan_call_matches_loop():
     assert not fin and k == 5
     A2 = np.diag([1.05, 0.97, 1.01])
     fin, k, a = oracle.plan(A2)
-    assert fin and k == 5 and a == pytest.approx(0.05, rel=1e-12)
+    # alpha = 0.05 lies in (Theta_3, Theta_4] = (1.33e-2, 9.31e-2]: the 14+ scheme
+    assert fin and k == 4 and a == pytest.approx(0.05, rel=1e-12)
+    # with k_max = 3 the loop test is against Theta_3: one more square root
+    fin, k, a = oracle.plan(A2, k_max=3)
+    assert not fin and k == 3
 
 
 # --------------------------------------------------------------------------
