@@ -89,14 +89,16 @@ typedef struct logm_batch {
                                  A <- T^{-1} A T before, L <- T L T^{-1} after, both exact */
 
 typedef struct logm_options {
-  int32_t k_max;          /* largest number of graph products: 1, 2, 3 or 5 (Table Table_theta;
-                             k = 3 is T_8 by eq. eqP8pol, k = 4 has no scheme) */
+  int32_t k_max;          /* largest number of graph products, 1..5 (Table Table_theta;
+                             k = 3 is T_8 by eq. eqP8pol, k = 4 the 14+ scheme of Sec. 3
+                             with coefficients solved from T_14, k = 5 Table
+                             table_simple_experiment) */
   int32_t precision;      /* LOGM_PREC_* of the graph products */
   int32_t max_sqrt;       /* maxiter of Algorithm 1 (default 40) */
   int32_t max_db_iter;    /* cap on Denman-Beavers iterations per root (default 50) */
   int32_t db_form;        /* LOGM_DB_* (default LOGM_DB_TWO_INVERSE) */
   int32_t balance;        /* LOGM_BALANCE_*, logm_execute / logm_backward only (default NONE) */
-  double theta[5];        /* Theta_{m_k} for k = 1..5 (theta[3], k = 4, is unused); 0 selects
+  double theta[5];        /* Theta_{m_k} for k = 1..5; 0 selects
                              the paper's 1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1
                              (Table Table_theta) */
 } logm_options;
@@ -142,12 +144,13 @@ int logm_sqrt(const logm_batch* batch, const logm_options* opts, void* A, void* 
  * (Sec. 3, eq. five_mult_degopt): P_1 = I, P_2 = X, P_3 = X^2 and
  * P_{j+2} = (sum_i h_{j,i} P_i)(sum_i g_{j,i} P_i), z = sum_i y_i P_i, with
  * Table table_simple_experiment for k = 5, exact Taylor T_2, T_4 (eq.
- * Taylor_log) for k = 1, 2 and T_8 with three products (eq. eqP8pol, its
- * coefficients solved in closed form) for k = 3.
+ * Taylor_log) for k = 1, 2, T_8 with three products (eq. eqP8pol, its
+ * coefficients solved in closed form) for k = 3 and the 14+ scheme (degree
+ * 16, T_14 matched, coefficients solved numerically) for k = 4.
  *   X    : device (dtype per batch).
  *   P3   : device or NULL; X^2 if the caller has it (saves one product, as
  *          Algorithm 1 does with A_I2 when s >= 1).
- *   k_dev: device int32[count], each 1, 2, 3 or 5.
+ *   k_dev: device int32[count], each 1..5.
  *   Z    : device output (dtype per batch).
  *   precision: LOGM_PREC_* for the products. */
 int logm_graph_eval(const logm_batch* batch, int32_t precision, const void* X, const void* P3,

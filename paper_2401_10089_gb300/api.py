@@ -82,7 +82,7 @@ _DB_FORM = {"two_inverse": 0, "product": 1}
 
 def _options(k_max=5, precision="fp64", max_sqrt=40, max_db_iter=50, theta=None, db_form="two_inverse",
              balance=False) -> _lib.LogmOptions:
-    """k_max in (1, 2, 3, 5); db_form "two_inverse" (eq. ScalDB) or "product";
+    """k_max in 1..5; db_form "two_inverse" (eq. ScalDB) or "product";
     balance: diagonal balancing of Algorithm 1, Step 1; theta: Theta_{m_k} for
     k = 1..5 (0 = the paper's Table Table_theta)."""
     o = _lib.LogmOptions()

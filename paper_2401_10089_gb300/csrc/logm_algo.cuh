@@ -40,6 +40,20 @@ static __constant__ double c_y5[7] = {0.0, 1.0, 5.065546620208965e-01, 3.8325120
                                1.088307723749078e+00, 2.787461897212877e-01,
                                8.157421998489228e-01};
 
+// k = 4, the 14+ scheme of Sec. 3 (m = 14+, degree 16; the paper gives no
+// coefficients): P_4 = P_3 (c3 X + c4 P_3), P_5 = (d1 X + d2 P_3 + P_4)
+// (e2 P_3 + P_4), P_6 = (f1 X + f2 P_3 + f4 P_4 + P_5)(g1 X + g4 P_4 + P_5),
+// z = X + y3 P_3 + y4 P_4 + y5 P_5 + P_6. The 13 values solve "coefficient of
+// x^i = 1/i" for i = 2..14 (T_14 of eq. Taylor_log matched; x^15, x^16 are
+// the "+"), the real root with the smallest coefficients, correctly rounded
+// from a 50-digit solution; Theta_14 recomputed from them is 9.32e-2 (Table
+// Table_theta: 9.31e-2). Order: c3 c4 d1 d2 e2 f1 f2 f4 g1 g4 y3 y4 y5.
+static __constant__ double c_k4[13] = {
+    0.3602750956560524,  0.3018442985303789,   0.3412287952056341,  -0.18047064940974122,
+    0.18907274365286242, -0.014079460349863975, 0.24400741065645315, -0.8525627910338015,
+    0.1463535711919622,  0.9787518426666669,   0.5020605793026582,  0.6095606808527384,
+    1.2091753609836204};
+
 constexpr double kUnitRoundoff = 0x1p-53;
 
 struct Slot {
@@ -337,10 +351,9 @@ static __device__ int alpha_test(Ops& ops, const double* Acur, const double* AI2
 template <class Ops>
 static __device__ int order_search(Ops& ops, const double* Acur, const double* AI2, int n, double nB, double nI2,
                             int k_max, const double* theta, const EstState* loop_est) {
-  int cands[4], nc = 0;
-  const int all[4] = {1, 2, 3, 5};
-  for (int t = 0; t < 4; ++t)
-    if (all[t] <= k_max) cands[nc++] = all[t];
+  int cands[5], nc = 0;
+  for (int kk = 1; kk <= 5; ++kk)
+    if (kk <= k_max) cands[nc++] = kk;
   if (nc == 0) return k_max;
   int lo = 0;
   if (loop_est && loop_est->t_m >= 0.0) {
@@ -511,6 +524,64 @@ static __device__ int db_sqrt_product(Ops& ops, Slot& M, int n, int max_db, int*
   return status;
 }
 
+// Factor coefficients h_{j,i}, g_{j,i} of P_i (i = 2..j+1) in product j >= 2.
+static __device__ __forceinline__ void scheme64(int k, int j, int i, double* h, double* g) {
+  *h = 0.0;
+  *g = 0.0;
+  if (k == 2) {
+    if (j == 2) {
+      *h = (i == 3) ? 1.0 : 0.0;
+      *g = (i == 2) ? 1.0 / 3.0 : (i == 3 ? 0.25 : 0.0);
+    }
+    return;
+  }
+  if (k == 3) {  // eq. (eqP8pol) in the degree-optimal form
+    double c[6];
+    k3_coeffs(c);
+    if (j == 2) {  // P_4 = P_3 (c3 P_2 + c4 P_3)
+      *h = (i == 3) ? 1.0 : 0.0;
+      *g = (i == 2) ? c[0] : (i == 3 ? c[1] : 0.0);
+    } else if (j == 3) {  // P_5 = (d1 P_2 + d2 P_3 + P_4)(e2 P_3 + P_4)
+      *h = (i == 2) ? c[2] : (i == 3 ? c[3] : 1.0);
+      *g = (i == 2) ? 0.0 : (i == 3 ? c[4] : 1.0);
+    }
+    return;
+  }
+  if (k == 4) {  // the 14+ scheme (c_k4)
+    const double* c = c_k4;
+    if (j == 2) {  // P_4 = P_3 (c3 P_2 + c4 P_3)
+      *h = (i == 3) ? 1.0 : 0.0;
+      *g = (i == 2) ? c[0] : (i == 3 ? c[1] : 0.0);
+    } else if (j == 3) {  // P_5 = (d1 P_2 + d2 P_3 + P_4)(e2 P_3 + P_4)
+      *h = (i == 2) ? c[2] : (i == 3 ? c[3] : 1.0);
+      *g = (i == 2) ? 0.0 : (i == 3 ? c[4] : 1.0);
+    } else if (j == 4) {  // P_6 = (f1 P_2 + f2 P_3 + f4 P_4 + P_5)(g1 P_2 + g4 P_4 + P_5)
+      *h = (i == 2) ? c[5] : (i == 3 ? c[6] : (i == 4 ? c[7] : 1.0));
+      *g = (i == 2) ? c[8] : (i == 3 ? 0.0 : (i == 4 ? c[9] : 1.0));
+    }
+    return;
+  }
+  int t = 0;
+  for (int jj = 2; jj < j; ++jj) t += jj;
+  *h = c_h5[t + i - 2];
+  *g = c_g5[t + i - 2];
+}
+
+static __device__ __forceinline__ double y64(int k, int i) {  // y_i, i = 2..k+2
+  if (k == 1) return i == 2 ? 1.0 : 0.5;
+  if (k == 2) return i == 2 ? 1.0 : (i == 3 ? 0.5 : 1.0);
+  if (k == 3) {
+    if (i == 4) {
+      double c[6];
+      k3_coeffs(c);
+      return c[5];
+    }
+    return i == 2 ? 1.0 : (i == 3 ? 0.5 : 1.0);
+  }
+  if (k == 4) return i == 2 ? 1.0 : (i == 6 ? 1.0 : c_k4[10 + i - 3]);  // y3, y4, y5 at i = 3, 4, 5
+  return c_y5[i - 1];
+}
+
 // ---------------------------------------------------------------------------
 // Graph evaluation, eq. (five_mult_degopt): out = scale * z(X) with P_2 = X
 // (Acur), P_3 = X^2 (A2) given. For Algorithm 1, scale = -2^s (eq. logipASTM
@@ -552,33 +623,36 @@ static __device__ void graph_eval(Ops& ops, int k, int n, Slot& M, double scale,
     ops.gemm(n, M.T1, 0.0, M.T2, 0.0, scale, e, out);
     return;
   }
-  // k = 5: P_4 .. P_7 from Table table_simple_experiment
+  // k = 4 (the 14+ scheme, P_4 .. P_6) and k = 5 (Table table_simple_experiment,
+  // P_4 .. P_7): factors from scheme64, the last product's epilogue adds
+  // sum_{i <= k+1} y_i P_i and scales
   double* P[8] = {nullptr, nullptr, P2, P3, M.Y, M.W1, M.W2, nullptr};
-  int t = 0;
-  for (int j = 2; j <= 5; ++j) {
+  for (int j = 2; j <= k; ++j) {
     EpiTerms hl, gl;
     hl.count = gl.count = j;
-    for (int i = 2; i <= j + 1; ++i, ++t) {
+    for (int i = 2; i <= j + 1; ++i) {
+      double h, g;
+      scheme64(k, j, i, &h, &g);
       hl.M[i - 2] = P[i];
-      hl.c[i - 2] = c_h5[t];
+      hl.c[i - 2] = h;
       gl.M[i - 2] = P[i];
-      gl.c[i - 2] = c_g5[t];
+      gl.c[i - 2] = g;
     }
     ops.lincomb(n, hl, M.T1);
     ops.lincomb(n, gl, M.T2);
     ops.tally(2, 1);
-    if (j < 5) {
+    if (j < k) {
       EpiTerms none;
       none.count = 0;
       ops.gemm(n, M.T1, 0.0, M.T2, 0.0, 1.0, none, OutView{P[j + 2], 0});
     } else {
       EpiTerms e;
-      e.count = 5;
-      for (int i = 2; i <= 6; ++i) {
+      e.count = k;
+      for (int i = 2; i <= k + 1; ++i) {
         e.M[i - 2] = P[i];
-        e.c[i - 2] = scale * c_y5[i - 1];
+        e.c[i - 2] = scale * y64(k, i);
       }
-      ops.gemm(n, M.T1, 0.0, M.T2, 0.0, scale * c_y5[6], e, out);
+      ops.gemm(n, M.T1, 0.0, M.T2, 0.0, scale * y64(k, k + 2), e, out);
     }
   }
 }
@@ -830,7 +904,7 @@ static __device__ void run_sqrt(Ops& ops, const SmallParams& p, int b, int n, in
 template <class Ops>
 static __device__ void run_graph(Ops& ops, const SmallParams& p, int b, int n, int64_t off, Slot& M) {
   const int k = p.k_in[b];
-  if (!(k == 1 || k == 2 || k == 3 || k == 5)) {
+  if (!(k >= 1 && k <= 5)) {
     if (ops.leader() && p.info) p.info[b] = -1;
     return;
   }
@@ -864,49 +938,6 @@ struct BwdSlot {
   DbTape tape;
 };
 
-// Factor coefficients h_{j,i}, g_{j,i} of P_i (i = 2..j+1) in product j >= 2.
-static __device__ __forceinline__ void scheme64(int k, int j, int i, double* h, double* g) {
-  *h = 0.0;
-  *g = 0.0;
-  if (k == 2) {
-    if (j == 2) {
-      *h = (i == 3) ? 1.0 : 0.0;
-      *g = (i == 2) ? 1.0 / 3.0 : (i == 3 ? 0.25 : 0.0);
-    }
-    return;
-  }
-  if (k == 3) {  // eq. (eqP8pol) in the degree-optimal form
-    double c[6];
-    k3_coeffs(c);
-    if (j == 2) {  // P_4 = P_3 (c3 P_2 + c4 P_3)
-      *h = (i == 3) ? 1.0 : 0.0;
-      *g = (i == 2) ? c[0] : (i == 3 ? c[1] : 0.0);
-    } else if (j == 3) {  // P_5 = (d1 P_2 + d2 P_3 + P_4)(e2 P_3 + P_4)
-      *h = (i == 2) ? c[2] : (i == 3 ? c[3] : 1.0);
-      *g = (i == 2) ? 0.0 : (i == 3 ? c[4] : 1.0);
-    }
-    return;
-  }
-  int t = 0;
-  for (int jj = 2; jj < j; ++jj) t += jj;
-  *h = c_h5[t + i - 2];
-  *g = c_g5[t + i - 2];
-}
-
-static __device__ __forceinline__ double y64(int k, int i) {  // y_i, i = 2..k+2
-  if (k == 1) return i == 2 ? 1.0 : 0.5;
-  if (k == 2) return i == 2 ? 1.0 : (i == 3 ? 0.5 : 1.0);
-  if (k == 3) {
-    if (i == 4) {
-      double c[6];
-      k3_coeffs(c);
-      return c[5];
-    }
-    return i == 2 ? 1.0 : (i == 3 ? 0.5 : 1.0);
-  }
-  return c_y5[i - 1];
-}
-
 template <class Ops>
 static __device__ void factor_terms(int k, int j, double* const* P, EpiTerms& hl, EpiTerms& gl) {
   hl.count = gl.count = j;
@@ -923,7 +954,7 @@ template <class Ops>
 static __device__ void run_backward(Ops& ops, const SmallParams& p, int b, int n, int64_t off, BwdSlot& W) {
   const int s = p.ctx_hdr[2 * b], k = p.ctx_hdr[2 * b + 1];
   const int64_t nn = (int64_t)n * n;
-  if (k != 1 && k != 2 && k != 3 && k != 5) {  // the forward produced no result
+  if (k < 1 || k > 5) {  // the forward produced no result
     fill_nan(ops, p.dA, p.dtype, off, n);
     if (ops.leader()) p.info[b] = 1;
     return;

@@ -9,7 +9,7 @@
 
 namespace {
 
-// Table Table_theta, k = 1..5 (k = 4 has no scheme here)
+// Table Table_theta, k = 1..5
 constexpr double kThetaPaper[5] = {1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1};
 
 // Kernel configuration per size bucket (logm_set_tuning).
@@ -39,7 +39,7 @@ int batch_n_max(const logm_batch* b) {
 
 int opts_ok(const logm_options* o) {
   if (!o) return 0;
-  if (o->k_max != 1 && o->k_max != 2 && o->k_max != 3 && o->k_max != 5) return 0;
+  if (o->k_max < 1 || o->k_max > 5) return 0;
   if (o->precision < LOGM_PREC_FP64 || o->precision > LOGM_PREC_BF16X3) return 0;
   if (o->max_sqrt < 0 || o->max_sqrt > 1000) return 0;
   if (o->max_db_iter < 1 || o->max_db_iter > 1000) return 0;

@@ -66,7 +66,7 @@ struct GraphParams {
   int count, n_uniform, n_max;
   const int32_t* n_dev;
   const int64_t* off_dev;
-  const int32_t* k_dev;     // products per matrix (1, 2, 3, 5)
+  const int32_t* k_dev;     // products per matrix (1..5)
   const int32_t* s_dev;     // square roots per matrix (scale -2^s), NULL: scale 1
   const int32_t* info_dev;  // matrices with info 1 or 4 are skipped; may be NULL
   float* gbuf;              // per matrix 5 slots of n_max^2 floats: P_2 .. P_6

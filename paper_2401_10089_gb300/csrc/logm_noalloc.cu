@@ -22,7 +22,7 @@ namespace {
 
 constexpr size_t kNoallocScratchBytes = size_t(32) << 20;
 constexpr int kMaxDevices = 64;
-// Table Table_theta, k = 1..5 (k = 4 has no scheme here)
+// Table Table_theta, k = 1..5
 constexpr double kThetaPaperNoalloc[5] = {1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1};
 
 // The scratch array. Host code must not pass `g_noalloc_scratch` itself to a
@@ -64,7 +64,7 @@ extern "C" int logm_execute_noalloc(const logm_batch* batch, const logm_options*
       return LOGM_ERR_INVALID_ARG;
     n_max = batch->n_max;
   }
-  if (opts->k_max != 1 && opts->k_max != 2 && opts->k_max != 3 && opts->k_max != 5) return LOGM_ERR_INVALID_ARG;
+  if (opts->k_max < 1 || opts->k_max > 5) return LOGM_ERR_INVALID_ARG;
   if (opts->max_sqrt < 0 || opts->max_sqrt > 1000) return LOGM_ERR_INVALID_ARG;
   if (opts->max_db_iter < 1 || opts->max_db_iter > 1000) return LOGM_ERR_INVALID_ARG;
   if (opts->db_form != LOGM_DB_TWO_INVERSE && opts->db_form != LOGM_DB_PRODUCT) return LOGM_ERR_INVALID_ARG;

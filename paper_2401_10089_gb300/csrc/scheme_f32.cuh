@@ -11,7 +11,8 @@ namespace lg {
 // Scheme tables (Sec. 3): index j = product number (1: P_3 = X X, 2..5), terms
 // i = 2..j+1 of the factors, y_i of the output. Table table_simple_experiment
 // for k = 5; exact Taylor T_4 (eq. Taylor_log) for k = 2; T_8 by eq.
-// (eqP8pol) for k = 3, its coefficients solved in closed form below.
+// (eqP8pol) for k = 3, its coefficients solved in closed form below; the 14+
+// scheme for k = 4.
 static __constant__ float c_tc_h5[14] = {
     7.363757032799957e-02f, -1.050281301619960e+00f, 8.897468955192446e-02f,
     -1.599651928992725e-01f, 9.577281350989334e-01f, 5.394999133948797e-01f,
@@ -27,6 +28,18 @@ static __constant__ float c_tc_g5[14] = {
 static __constant__ float c_tc_y5[7] = {0.0f, 1.0f, 5.065546620208965e-01f, 3.832512052972577e-01f,
                                         1.088307723749078e+00f, 2.787461897212877e-01f,
                                         8.157421998489228e-01f};
+
+// k = 4, the 14+ scheme of Sec. 3 (degree 16, T_14 matched; the paper prints
+// no coefficients): the real root of "coefficient of x^i = 1/i, i = 2..14"
+// with the smallest coefficients. P_4 = P_3 (c3 X + c4 P_3), P_5 = (d1 X +
+// d2 P_3 + P_4)(e2 P_3 + P_4), P_6 = (f1 X + f2 P_3 + f4 P_4 + P_5)(g1 X +
+// g4 P_4 + P_5), z = X + y3 P_3 + y4 P_4 + y5 P_5 + P_6.
+// Order: c3 c4 d1 d2 e2 f1 f2 f4 g1 g4 y3 y4 y5.
+static __constant__ float c_tc_k4[13] = {
+    0.3602750956560524f,  0.3018442985303789f,   0.3412287952056341f,  -0.18047064940974122f,
+    0.18907274365286242f, -0.014079460349863975f, 0.24400741065645315f, -0.8525627910338015f,
+    0.1463535711919622f,  0.9787518426666669f,   0.5020605793026582f,  0.6095606808527384f,
+    1.2091753609836204f};
 
 struct Coeffs {
   float h[6], g[6];  // factor coefficients for P_2 .. P_{j+1}
@@ -85,6 +98,29 @@ static __device__ __forceinline__ void scheme_coeffs(int k, int j, Coeffs& c) {
     }
     return;
   }
+  if (k == 4) {
+    const float* q = c_tc_k4;
+    if (j == 2) {  // P_4 = P_3 (c3 X + c4 P_3)
+      c.h[1] = 1.0f;
+      c.g[0] = q[0];
+      c.g[1] = q[1];
+    } else if (j == 3) {  // P_5 = (d1 X + d2 P_3 + P_4)(e2 P_3 + P_4)
+      c.h[0] = q[2];
+      c.h[1] = q[3];
+      c.h[2] = 1.0f;
+      c.g[1] = q[4];
+      c.g[2] = 1.0f;
+    } else {  // P_6 = (f1 X + f2 P_3 + f4 P_4 + P_5)(g1 X + g4 P_4 + P_5)
+      c.h[0] = q[5];
+      c.h[1] = q[6];
+      c.h[2] = q[7];
+      c.h[3] = 1.0f;
+      c.g[0] = q[8];
+      c.g[2] = q[9];
+      c.g[3] = 1.0f;
+    }
+    return;
+  }
   int t = 0;
   for (int jj = 2; jj < j; ++jj) t += jj;
   for (int i = 0; i < j; ++i) {
@@ -105,6 +141,7 @@ static __device__ __forceinline__ float scheme_y(int k, int i2) {
     }
     return i2 == 0 ? 1.0f : (i2 == 1 ? 0.5f : (i2 == 3 ? 1.0f : 0.0f));
   }
+  if (k == 4) return (i2 == 0 || i2 == 4) ? 1.0f : c_tc_k4[10 + i2 - 1];  // y3, y4, y5 at i2 = 1, 2, 3
   return c_tc_y5[i2 + 1];
 }
 
@@ -112,12 +149,13 @@ static __device__ __forceinline__ int needs_product(int k, int p3_given, int j) 
   if (j == 1) return !p3_given;    // P_3 = X X only when the caller did not supply it
   if (k == 2) return j == 2;
   if (k == 3) return j <= 3;
+  if (k == 4) return j <= 4;
   if (k == 5) return j <= 5;
   return 0;
 }
 
 static __device__ __forceinline__ int is_last_product(int k, int j) {
-  return (k == 2 || k == 3 || k == 5) && j == k;
+  return k >= 2 && k <= 5 && j == k;
 }
 
 }  // namespace lg

@@ -92,10 +92,10 @@ def test_execute_f32_storage():
 # With k_max = 1 or 2 the loop takes roots until ||A^{1/2^s} - I|| is about
 # Theta_1 = 1.83e-8 or Theta_2 = 1.53e-4, so X = I - A^{1/2^s} carries a
 # relative cancellation error of about u / Theta on either side.
-KMAX_TOL = {1: 1e-7, 2: 1e-10, 3: 1e-11, 5: TOL}
+KMAX_TOL = {1: 1e-7, 2: 1e-10, 3: 1e-11, 4: TOL, 5: TOL}
 
 
-@pytest.mark.parametrize("k_max", [1, 2, 3, 5])
+@pytest.mark.parametrize("k_max", [1, 2, 3, 4, 5])
 def test_execute_k_max(k_max):
     mats = workloads.identity_plus(4, 20, seed=21, lo=0.05, hi=0.5)
     L, s, k, info = lg().logm_execute(dev(mats), k_max=k_max)
@@ -124,9 +124,9 @@ def test_plan_parity():
     assert (bool(fin[0]), int(k[0])) == (f_r, k_r) and abs(float(alpha[0]) - a_r) <= 1e-10 * a_r
 
 
-@pytest.mark.parametrize("k_max", [3, 5])
+@pytest.mark.parametrize("k_max", [3, 4, 5])
 def test_plan_parity_k_max(k_max):
-    # the order search's choice among k in {1, 2, 3, 5} (or {1, 2, 3}) near
+    # the order search's choice among k in 1..k_max near
     # the identity, where every order is in play
     rng = np.random.default_rng(31)
     mats = [np.eye(30) + e * rng.standard_normal((30, 30)) / 30 for e in (1e-9, 1e-5, 3e-3, 8e-3, 0.05)]
@@ -151,7 +151,7 @@ def test_sqrt_parity():
         assert rel(AI2.cpu().numpy()[b], mats[b] - 2 * Xr + np.eye(32)) <= 1e-11
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 5])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("n", [1, 9, 64, 100, 256])
 def test_graph_parity(k, n):
     rng = np.random.default_rng(40 + n)

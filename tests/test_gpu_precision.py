@@ -20,7 +20,7 @@ PREC_TOL = {"tf32x3": 5e-6, "bf16x3": 5e-6}
 
 
 @pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
-@pytest.mark.parametrize("k", [1, 2, 3, 5])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("n", [8, 64, 100, 256, 300])
 def test_graph_eval_split_precision(precision, k, n):
     rng = np.random.default_rng(70 + n + k)

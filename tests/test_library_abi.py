@@ -45,7 +45,7 @@ def test_invalid_arguments_rejected_before_launch():
     b = _lib.LogmBatch()
     b.count, b.dtype, b.n_uniform, b.n_max = 1, 0, 8, 8
     o = _lib.LogmOptions()
-    o.k_max, o.precision, o.max_sqrt, o.max_db_iter = 4, 0, 40, 50  # k_max = 4 has no scheme
+    o.k_max, o.precision, o.max_sqrt, o.max_db_iter = 6, 0, 40, 50  # k_max = 6 has no scheme
     rc = L.logm_execute(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, None, None, 0, None)
     assert rc == _lib.ERR_INVALID_ARG
     o.k_max, o.db_form = 5, 2  # no such Denman-Beavers form
