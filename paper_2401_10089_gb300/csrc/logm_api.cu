@@ -22,6 +22,8 @@ size_t small_slots_bytes_all_variants(int count, int small_nmax) {
   const size_t m1 = lg_v1::small_workspace_bytes(count, small_nmax < 64 ? small_nmax : 64);
   const size_t m2 = lg_v2::small_workspace_bytes(count, small_nmax < 32 ? small_nmax : 32);
   const size_t m3 = lg_v3::small_workspace_bytes(count, small_nmax);
+  const size_t m4 = lg_v4::small_workspace_bytes(count, small_nmax < 64 ? small_nmax : 64);
+  if (m4 > m) m = m4;
   if (m1 > m) m = m1;
   if (m2 > m) m = m2;
   if (m3 > m) m = m3;
@@ -164,8 +166,14 @@ cudaError_t launch_small_variants(lg::Mode mode, const lg::SmallParams& q, int s
       e = lg::launch_small(mode, r, st);
     } else if (v == 1) {
       r.n_max = q.n_max < 64 ? q.n_max : 64;
-      r.n_slots = lg_v1::small_kernel_slots(count);
-      e = lg_v1::launch_small(mode, r, st);
+      const int s1 = lg_v1::small_kernel_slots(count), s4 = lg_v4::small_kernel_slots(count);
+      if (q.n_uniform > 0 && count > s1 && count <= s4) {  // one round at 7 per SM instead of two at 5
+        r.n_slots = s4;
+        e = lg_v4::launch_small(mode, r, st);
+      } else {
+        r.n_slots = s1;
+        e = lg_v1::launch_small(mode, r, st);
+      }
     } else if (v == 2) {
       r.n_max = q.n_max < 32 ? q.n_max : 32;
       r.n_slots = lg_v2::small_kernel_slots(count);
@@ -275,7 +283,9 @@ size_t logm_backward_workspace_size(const logm_batch* batch, const logm_options*
   const size_t m1 = lg_v1::small_bwd_workspace_bytes(batch->count, n_max < 64 ? n_max : 64);
   const size_t m2 = lg_v2::small_bwd_workspace_bytes(batch->count, n_max < 32 ? n_max : 32);
   const size_t m3 = lg_v3::small_bwd_workspace_bytes(batch->count, n_max);
+  const size_t m4 = lg_v4::small_bwd_workspace_bytes(batch->count, n_max < 64 ? n_max : 64);
   size_t r = m > m1 ? m : m1;
+  r = r > m4 ? r : m4;
   r = r > m2 ? r : m2;
   return r > m3 ? r : m3;
 }

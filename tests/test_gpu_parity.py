@@ -195,3 +195,13 @@ def test_full_size_sampled():
             assert rel(L[b], Ls[j]) <= TOL
         else:
             check_logm(A[b], L[b], int(s[b]), int(k[b]), int(info[b]))
+
+
+def test_uniform_batch_one_round_configuration():
+    # 800 matrices of 40 x 40: more than the 5-per-SM configuration holds at
+    # once, fewer than its 7-per-SM twin, which then runs them in one round
+    A = workloads.identity_plus(800, 40, seed=810, lo=0.2, hi=3.0)
+    L, s, k, info = lg().logm_execute(dev(A))
+    L, s, k, info = L.cpu().numpy(), s.cpu().numpy(), k.cpu().numpy(), info.cpu().numpy()
+    for b in range(0, 800, 7):
+        check_logm(A[b], L[b], int(s[b]), int(k[b]), int(info[b]))
