@@ -14,7 +14,7 @@ constexpr double kThetaPaper[5] = {1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1};
 
 // Kernel configuration per size bucket (logm_set_tuning).
 int g_variant[lg::kBuckets] = {0, 0, 0, 0, 0, 0};
-constexpr int kVariants = 4;
+constexpr int kVariants = 4;  // tunable configurations; configuration 1's 7-per-SM twin is picked by batch size
 constexpr int kVariantMaxBucket[kVariants] = {5, 3, 2, 5};  // largest bucket each configuration serves
 
 size_t small_slots_bytes_all_variants(int count, int small_nmax) {
