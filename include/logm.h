@@ -222,7 +222,9 @@ int logm_execute_noalloc(const logm_batch* batch, const logm_options* opts, cons
  *           1 = 128-thread blocks, 32 x 32 tiles, n <= 64 (buckets 0-3);
  *           2 = 64-thread blocks, 32 x 32 tiles, n <= 32 (buckets 0-2);
  *           3 = 256-thread blocks as 0, three per SM (registers capped), any n <= 256.
- * Smaller configurations keep more small matrices in flight per SM. The
+ * Smaller configurations keep more small matrices in flight per SM; a
+ * uniform batch that variant 1 would run in two rounds of five blocks per SM
+ * but that fits one round of seven runs on its 7-per-SM build instead. The
  * project's autotuner (paper_2401_10089_gb300.autotune) times the candidates
  * on a sample of each bucket and writes the table it picks to JSON. */
 typedef struct logm_tuning {
@@ -239,6 +241,21 @@ int logm_get_tuning(logm_tuning* t);
 
 /* Library version (major * 10000 + minor * 100 + patch). */
 int logm_version(void);
+
+/* logm_probe_barrier -- self-test of the bound on the whole-GPU kernel's grid
+ * barrier (the only spin-wait in the library). Two co-resident blocks (one
+ * cooperative launch) wait at a barrier that expects 2 + missing arrivals, so
+ * with missing > 0 it never completes: each block gives up after timeout_s
+ * seconds and the status word becomes 1 (in logm_execute that is
+ * LOGM_INFO_TIMEOUT); with missing = 0 both arrive and it stays 0.
+ *   missing   : 0..8 arrivals that never come.
+ *   timeout_s : 1e-6 .. 60 seconds.
+ *   ws        : device, >= 16 bytes, 8-byte aligned, owned by the caller:
+ *               [0, 8) the arrival counter, [8, 12) int32 status written by the
+ *               kernel (read it after the stream has finished).
+ * Returns LOGM_SUCCESS, LOGM_ERR_INVALID_ARG, LOGM_ERR_WORKSPACE or
+ * LOGM_ERR_CUDA (launch failure). Does not synchronise the host. */
+int logm_probe_barrier(int32_t missing, double timeout_s, void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

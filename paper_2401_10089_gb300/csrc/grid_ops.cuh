@@ -25,6 +25,7 @@ constexpr int kGridPanel = 32;          // Gauss-Jordan panel width for large n
 constexpr int kColGroups = 16;          // row groups of the column passes (norms, transposed mat-vecs, updates)
 constexpr int kMaxGrid = 1024;          // upper bound on co-resident blocks
 constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s
+constexpr unsigned long long kBarrierMaxPolls = 1ull << 26;  // backstop should the clock not advance
 
 // Buffers of one Gauss-Jordan inversion running on a group of blocks.
 struct GjGroup {
@@ -89,8 +90,10 @@ static __device__ __forceinline__ void red_release_add(unsigned long long* p, un
 
 // Barrier over `nblocks` blocks sharing the arrival counter *bar; *ep is this
 // block's episode count for that counter (shared memory, thread 0 only).
+// Gives up after timeout_ns (or kBarrierMaxPolls polls), setting *err = 1.
 static __device__ void bounded_barrier(unsigned long long* bar, unsigned nblocks, int* err,
-                                       unsigned long long* ep) {
+                                       unsigned long long* ep,
+                                       unsigned long long timeout_ns = kBarrierTimeoutNs) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile int* verr = err;
@@ -99,10 +102,11 @@ static __device__ void bounded_barrier(unsigned long long* bar, unsigned nblocks
     if (*verr == 0) {
       red_release_add(bar, 1ull);  // publishes this block's writes (release, gpu scope)
       const unsigned long long t0 = global_ns();
-      int polls = 0;
+      unsigned long long polls = 0;
       while (ld_acquire(bar) < target) {
         if (*verr) break;
-        if ((++polls & 63) == 0 && global_ns() - t0 > kBarrierTimeoutNs) {
+        ++polls;
+        if (((polls & 63) == 0 && global_ns() - t0 > timeout_ns) || polls > kBarrierMaxPolls) {
           atomicExch(err, 1);
           break;
         }

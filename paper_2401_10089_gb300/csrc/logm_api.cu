@@ -236,6 +236,15 @@ extern "C" {
 
 int logm_version(void) { return 200; }
 
+int logm_probe_barrier(int32_t missing, double timeout_s, void* ws, size_t ws_bytes, void* stream) {
+  if (missing < 0 || missing > 8 || !(timeout_s >= 1e-6 && timeout_s <= 60.0)) return LOGM_ERR_INVALID_ARG;
+  if (!ws || ws_bytes < 16 || reinterpret_cast<uintptr_t>(ws) % 8 != 0) return LOGM_ERR_WORKSPACE;
+  const unsigned long long ns = static_cast<unsigned long long>(timeout_s * 1e9);
+  if (lg::launch_barrier_probe(missing, ns, ws, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return LOGM_ERR_CUDA;
+  return LOGM_SUCCESS;
+}
+
 int logm_set_tuning(const logm_tuning* t) {
   if (!t) {
     for (int b = 0; b < lg::kBuckets; ++b) g_variant[b] = 0;

@@ -107,6 +107,7 @@ __host__ __device__ inline int size_bucket(int n) {
 size_t large_workspace_bytes(int n_max);
 int large_grid_size();
 cudaError_t launch_large(Mode mode, const SmallParams& p, void* ws, cudaStream_t stream);
+cudaError_t launch_barrier_probe(int missing, unsigned long long timeout_ns, void* ws, cudaStream_t stream);
 size_t small_workspace_bytes(int count, int n_max);
 size_t small_order_bytes(int count);
 cudaError_t launch_small(Mode mode, const SmallParams& p, cudaStream_t stream);

@@ -163,6 +163,28 @@ size_t large_workspace_bytes(int n_max) { return large_layout(n_max).total; }
 
 int large_grid_size() { return g_large_grid; }
 
+// Self-test of the grid barrier's bound: two co-resident blocks wait at a
+// barrier for 2 + missing arrivals; with missing > 0 nobody completes it, so
+// both give up after timeout_ns and the status word reads 1 (the whole-GPU
+// kernel reports that as LOGM_INFO_TIMEOUT); with missing = 0 it reads 0.
+__global__ void k_barrier_probe(unsigned long long* bar, int* status, unsigned nwait,
+                                unsigned long long timeout_ns) {
+  __shared__ unsigned long long ep;
+  if (threadIdx.x == 0) ep = 0;
+  __syncthreads();
+  bounded_barrier(bar, nwait, status, &ep, timeout_ns);
+}
+
+cudaError_t launch_barrier_probe(int missing, unsigned long long timeout_ns, void* ws, cudaStream_t st) {
+  unsigned long long* bar = static_cast<unsigned long long*>(ws);
+  int* status = reinterpret_cast<int*>(static_cast<char*>(ws) + 8);
+  cudaError_t e = cudaMemsetAsync(ws, 0, 16, st);
+  if (e != cudaSuccess) return e;
+  unsigned nwait = 2u + static_cast<unsigned>(missing);
+  void* args[] = {&bar, &status, &nwait, &timeout_ns};
+  return cudaLaunchCooperativeKernel((const void*)k_barrier_probe, dim3(2), dim3(32), args, 0, st);
+}
+
 cudaError_t launch_large(Mode mode, const SmallParams& p, void* ws, cudaStream_t st) {
   if (p.count <= 0) return cudaSuccess;
   char* w = static_cast<char*>(ws);
