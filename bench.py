@@ -405,11 +405,11 @@ def main():
         # DRAM bytes of the dominant kernel from ncu (dram__bytes_read.sum +
         # dram__bytes_write.sum). The 4096^2 launch is too long to capture; its
         # 2048^2 case (same plan: 27 iterations, 45 inversions, 4 products) moved
-        # 96.90 GB, mostly the working matrix written back by every rank-32
+        # 96.62 GB, mostly the working matrix written back by every rank-32
         # update, which scales with n^3: x 8 for one 4096^2 launch.
         traffic, traffic_note = None, "not captured for this configuration"
         if big and args.big_n == NBIG:
-            traffic = 8 * (7.779641e9 + 89.122285e9)
+            traffic = 8 * (7.813095e9 + 88.806196e9)
             traffic_note = ("bytes per launch: 8 x the DRAM bytes ncu measured on the 2048^2 case of the same "
                             "kernel and plan (traffic grows with n^3); far below HBM bandwidth, FP64-pipe bound")
         else:

@@ -122,6 +122,7 @@ void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o)
   p.dtype = b->dtype;
   p.n_uniform = b->n_uniform > 0 ? b->n_uniform : 0;
   p.n_max = batch_n_max(b);
+  p.batch_nmax = p.n_max;
   p.n_dev = b->n;
   p.off_dev = b->offset;
   if (o) {

@@ -15,6 +15,7 @@ enum Mode : int { kModeExecute = 0, kModePlan = 1, kModeSqrt = 2, kModeGraph = 3
 struct SmallParams {
   // batch
   int count, dtype, n_uniform, n_max;
+  int batch_nmax;  // n_max of the whole batch (n_max may be a configuration's smaller limit)
   const int32_t* n_dev;
   const int64_t* off_dev;
   // options

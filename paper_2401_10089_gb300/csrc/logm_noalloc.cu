@@ -91,6 +91,7 @@ extern "C" int logm_execute_noalloc(const logm_batch* batch, const logm_options*
   p.dtype = batch->dtype;
   p.n_uniform = batch->n_uniform > 0 ? batch->n_uniform : 0;
   p.n_max = n_max;
+  p.batch_nmax = n_max;
   p.n_dev = batch->n;
   p.off_dev = batch->offset;
   p.k_max = opts->k_max;

@@ -120,9 +120,21 @@ __global__ void __launch_bounds__(kThreads, LG_MINBLOCKS) k_logm_small(SmallPara
     int n;
     int64_t off;
     matrix_geometry(p, b, &n, &off);
+    if (n < 1 || n > p.batch_nmax) {
+      // a size no kernel may take: refused once, by the configuration that
+      // owns the smallest bucket (the whole-GPU kernel refuses n > n_max when
+      // it runs), and never read
+      const bool owner = p.bucket_mask == 0 || (p.bucket_mask & 1);
+      if (owner && !(n > kMaxN && p.large_pass) && threadIdx.x == 0) {
+        if (p.info) p.info[b] = -1;
+        if (p.s_out) p.s_out[b] = 0;
+        if (p.k_out) p.k_out[b] = p.k_max;
+      }
+      continue;
+    }
     if (p.bucket_mask && !((p.bucket_mask >> size_bucket(n)) & 1)) continue;  // another configuration's
     if (n > kMaxN && p.large_pass) continue;  // handled by the whole-GPU kernel
-    if (n < 1 || n > kMaxN || n > p.n_max) {
+    if (n > kMaxN || n > p.n_max) {
       if (threadIdx.x == 0) {
         if (p.info) p.info[b] = -1;
         if (p.s_out) p.s_out[b] = 0;
