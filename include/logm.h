@@ -17,7 +17,8 @@
  *  - Matrices are dense, square, row-major. A batch holds `count` matrices.
  *    With n_uniform > 0 matrix b starts at element b * n_uniform^2. With
  *    n_uniform == 0 the sizes and element offsets come from the device arrays
- *    `n` and `offset`, and n_max must bound every n.
+ *    `n` and `offset`, and n_max must bound every n (a matrix whose n lies
+ *    outside [1, n_max] is not read and gets LOGM_INFO_BAD_SIZE).
  *  - Pointers named *_dev, and every matrix pointer, are DEVICE pointers that
  *    the caller allocates and owns; the library never allocates, frees or
  *    keeps them after the call returns.
@@ -48,6 +49,7 @@ extern "C" {
 #define LOGM_ERR_CUDA (-4)
 
 /* Per-matrix status written to info_dev. */
+#define LOGM_INFO_BAD_SIZE (-1)    /* ragged batch: this matrix's n is outside [1, n_max] */
 #define LOGM_INFO_OK 0
 #define LOGM_INFO_SINGULAR 1       /* exact zero (or non-finite) pivot in a left division */
 #define LOGM_INFO_NO_CONVERGENCE 2 /* Denman-Beavers iteration hit max_db_iter */

@@ -1,6 +1,6 @@
 """Edge cases through the C ABI: empty batches on every entry point (uniform
 and ragged), and ragged batches with sizes a kernel must refuse (n < 1 or
-n > n_max: info -1 for that matrix, the others unaffected). The refusals are
+n > n_max: LOGM_INFO_BAD_SIZE = -1 for that matrix, the others unaffected). The refusals are
 the kernels' own size checks (every kernel reads n before touching a
 matrix); no invalid memory is addressed."""
 import numpy as np
