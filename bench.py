@@ -387,7 +387,7 @@ def main():
             entry[prec] = {"ms": ms_r, "matrices_per_s": 20000 / (ms_r * 1e-3), "tflops": fl / (ms_r * 1e-3) / 1e12,
                            "info_nonzero": int((ir_.cpu().numpy() != 0).sum()),
                            "s_hist": np.bincount(sr_.cpu().numpy()).tolist()}
-        entry["workload"] = ("20000 SPD, n uniform in {4..256}, lambda log-uniform [1e-3, 1e3], FP32 storage, "
+        entry["workload"] = ("20000 SPD, n uniform over {4, 8, 16, 32, 64, 128, 256}, lambda log-uniform [1e-3, 1e3], FP32 storage, "
                              "one call (persistent FP64 stage + tcgen05 graph stage)")
         entry["speedup_tf32x3_vs_fp64"] = entry["fp64"]["ms"] / entry["tf32x3"]["ms"]
         forms["batching"] = entry

@@ -107,7 +107,7 @@ def autotune(A, precision: str = "fp64", sample: int = 4096, reps: int = 3, path
 def main():
     from . import workloads
     ap = argparse.ArgumentParser()
-    ap.add_argument("--count", type=int, default=7000, help="ragged SPD matrices, n uniform in {4..256}")
+    ap.add_argument("--count", type=int, default=7000, help="ragged SPD matrices, n uniform over {4, 8, ..., 256} (powers of two)")
     ap.add_argument("--precision", default="fp64")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()

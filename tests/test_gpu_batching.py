@@ -104,3 +104,30 @@ def test_autotuner_picks_a_valid_table():
         assert (info.cpu().numpy() == 0).all()
     finally:
         lg().set_tuning(old)
+
+
+def test_full_size_batching_configuration():
+    """The batching configuration at full size, as the benchmark runs it: 20,000
+    SPD matrices, n uniform over {4, 8, ..., 256}, FP32 storage, TF32x3 graph
+    products, one call. Every matrix: info 0, L symmetric (log of an SPD
+    matrix) and trace(L) = log det A; two matrices of every size against the
+    oracle."""
+    vals, ns, offs = workloads.ragged_spd(20000, seed=4)
+    R = lg().Ragged(torch.tensor(vals, device="cuda"), torch.tensor(ns, device="cuda"),
+                    torch.tensor(offs, device="cuda"), 256)
+    L, s, k, info = lg().logm_execute(R, precision="tf32x3")
+    out = L.values.cpu().numpy()
+    assert (info.cpu().numpy() == 0).all()
+    for n in SIZES:
+        idx = np.nonzero(ns == n)[0]
+        A = np.stack([vals[offs[b]:offs[b] + n * n].reshape(n, n) for b in idx]).astype(np.float64)
+        Lg = np.stack([out[offs[b]:offs[b] + n * n].reshape(n, n) for b in idx]).astype(np.float64)
+        nrm = np.linalg.norm(Lg, axis=(1, 2))
+        assert (np.linalg.norm(Lg - Lg.transpose(0, 2, 1), axis=(1, 2)) <= 1e-5 * nrm).all(), n
+        sign, logdet = np.linalg.slogdet(A)
+        assert (sign > 0).all()
+        tr = np.trace(Lg, axis1=1, axis2=2)
+        assert (np.abs(tr - logdet) <= 1e-5 * (np.abs(logdet) + n * nrm / np.sqrt(n))).all(), n
+        for j in np.random.default_rng(44 + n).choice(len(idx), 2, replace=False):
+            Lr, d = oracle.logm(A[j])
+            assert rel(Lg[j], Lr) <= 1e-5, (n, int(idx[j]), rel(Lg[j], Lr))
