@@ -218,6 +218,24 @@ int logm_backward(const logm_batch* batch, const logm_options* opts, const void*
 int logm_execute_noalloc(const logm_batch* batch, const logm_options* opts, const void* A, void* L,
                          int32_t* s_dev, int32_t* k_dev, int32_t* info_dev, void* stream);
 
+/* logm_execute_host -- logm_execute on HOST buffers, for callers whose data
+ * lives in host memory: copies A to the device, runs logm_execute and copies
+ * L, s, k and info back, all enqueued on `stream` (one cudaMemcpyAsync per
+ * buffer; the results are in the host buffers once the stream has finished).
+ * Uniform batches only (n_uniform > 0; a ragged batch returns
+ * LOGM_ERR_UNSUPPORTED). Host buffers should be page-locked for the copies to
+ * be asynchronous; pageable memory works but the copies then block the host.
+ *   A_host   : host, count * n^2 elements of the batch dtype, row-major.
+ *   L_host   : host, same size; s_host, k_host (may be NULL), info_host: host int32[count].
+ *   ws       : device, >= logm_host_workspace_size() bytes, 256-byte aligned:
+ *              device copies of A and L, the three int32 arrays, then the
+ *              workspace of logm_execute.
+ * Returns as logm_execute, or LOGM_ERR_CUDA if a copy cannot be enqueued. */
+size_t logm_host_workspace_size(const logm_batch* batch, const logm_options* opts);
+int logm_execute_host(const logm_batch* batch, const logm_options* opts, const void* A_host, void* L_host,
+                      int32_t* s_host, int32_t* k_host, int32_t* info_host, void* ws, size_t ws_bytes,
+                      void* stream);
+
 /* Per-size-bucket choice of the one-block-per-matrix kernel configuration
  * used by logm_execute (batching form). Buckets: n <= 8, 16, 32, 64, 128, 256.
  * Variants: 0 = 256-thread blocks, 64 x 64 DMMA tiles, any n <= 256;

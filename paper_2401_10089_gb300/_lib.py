@@ -22,7 +22,8 @@ _ERRORS = {ERR_INVALID_ARG: "invalid argument", ERR_UNSUPPORTED: "unsupported", 
 # Every symbol include/logm.h declares.
 EXPORTS = ("logm_workspace_size", "logm_context_size", "logm_backward_workspace_size", "logm_plan", "logm_sqrt",
            "logm_graph_eval", "logm_execute", "logm_backward", "logm_execute_noalloc", "logm_set_tuning",
-           "logm_get_tuning", "logm_version", "logm_probe_barrier")
+           "logm_get_tuning", "logm_version", "logm_probe_barrier", "logm_host_workspace_size",
+           "logm_execute_host")
 
 
 class LogmBatch(ctypes.Structure):
@@ -82,11 +83,15 @@ def load(build_if_missing: bool = True):
         L.logm_get_tuning.argtypes = [P(LogmTuning)]
         L.logm_version.argtypes = []
         L.logm_probe_barrier.argtypes = [I32, ctypes.c_double, V, SZ, V]
+        L.logm_host_workspace_size.restype = SZ
+        L.logm_host_workspace_size.argtypes = [B, O]
+        L.logm_execute_host.argtypes = [B, O, V, V, V, V, V, V, SZ, V]
         for name in EXPORTS:
             getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
         L.logm_workspace_size.restype = SZ
         L.logm_context_size.restype = SZ
         L.logm_backward_workspace_size.restype = SZ
+        L.logm_host_workspace_size.restype = SZ
         _lib = L
         _apply_shipped_tuning(L)
         return _lib

@@ -116,6 +116,7 @@ class _Workspace:
 
 
 _ws = _Workspace()
+_ws_host = _Workspace()
 
 
 def logm_workspace_size(A, **opts) -> int:
@@ -214,6 +215,60 @@ def logm_execute(A, with_ctx=False, stats=None, **opts):
     Lout = out if not isinstance(A, Ragged) else Ragged(out, A.n, A.offset, A.n_max)
     if with_ctx:
         return Lout, s, k, info, ctx
+    return Lout, s, k, info
+
+
+def _host_batch(A):
+    if A.is_cuda:
+        raise ValueError("logm_execute_host takes host (CPU) tensors")
+    A3 = A.unsqueeze(0) if A.dim() == 2 else A
+    if A3.dim() != 3 or A3.shape[1] != A3.shape[2] or not A3.is_contiguous():
+        raise ValueError("expected a contiguous (count, n, n) or (n, n) CPU tensor")
+    b = _lib.LogmBatch()
+    b.count, b.dtype, b.n_uniform, b.n_max = A3.shape[0], _dtype_code(A3.dtype), A3.shape[1], A3.shape[1]
+    b.n = b.offset = None
+    return A3, b
+
+
+def logm_host_workspace_size(A, **opts) -> int:
+    """Device bytes ``logm_execute_host`` needs for the host tensor A."""
+    L = _lib.load()
+    _, b = _host_batch(A)
+    return int(L.logm_host_workspace_size(ctypes.byref(b), ctypes.byref(_options(**opts))))
+
+
+def logm_execute_host(A, out=None, device=None, workspace=None, **opts):
+    """L = log(A) for host matrices through ``logm_execute_host`` (the copies to
+    and from the device happen inside the call): A is a (count, n, n) or
+    (n, n) CPU tensor (page-locked for asynchronous copies), ``out`` an
+    optional CPU tensor of the same shape for L, ``workspace`` an optional
+    uint8 CUDA tensor of at least ``logm_host_workspace_size(A)`` bytes.
+    Returns (L, s, k, info) as CPU tensors once the stream has finished."""
+    L = _lib.load()
+    A3, b = _host_batch(A)
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    o = _options(**opts)
+    nb = int(L.logm_host_workspace_size(ctypes.byref(b), ctypes.byref(o)))
+    if nb == 0:
+        raise _lib.LogmError("logm_execute_host: unsupported batch")
+    if workspace is not None:
+        if workspace.numel() * workspace.element_size() < nb:
+            raise ValueError("workspace too small")
+        w, nb = workspace, workspace.numel() * workspace.element_size()
+    else:
+        w = _ws_host.get(dev, nb)
+    pin = A3.is_pinned()
+    Lout = out if out is not None else torch.empty(A3.shape, dtype=A3.dtype, pin_memory=pin)
+    s = torch.empty(b.count, dtype=torch.int32, pin_memory=pin)
+    k = torch.empty_like(s)
+    info = torch.empty_like(s)
+    stream = torch.cuda.current_stream(dev)
+    rc = L.logm_execute_host(ctypes.byref(b), ctypes.byref(o), _ptr(A3), _ptr(Lout), _ptr(s), _ptr(k), _ptr(info),
+                             _ptr(w), nb, ctypes.c_void_p(stream.cuda_stream))
+    _lib.check(rc, "logm_execute_host")
+    stream.synchronize()
+    if A.dim() == 2 and out is None:
+        Lout = Lout[0]
     return Lout, s, k, info
 
 

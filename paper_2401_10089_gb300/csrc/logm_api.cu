@@ -237,6 +237,51 @@ extern "C" {
 
 int logm_version(void) { return 200; }
 
+// Host-buffer entry: [A copy | L copy | s | k | info | logm_execute workspace].
+static size_t host_matrix_bytes(const logm_batch* b) {
+  const size_t esz = b->dtype == LOGM_DTYPE_F64 ? 8 : 4;
+  return (size_t)b->count * (size_t)b->n_uniform * (size_t)b->n_uniform * esz;
+}
+
+size_t logm_host_workspace_size(const logm_batch* batch, const logm_options* opts) {
+  if (!batch || batch->n_uniform <= 0 || batch_n_max(batch) <= 0) return 0;
+  const size_t inner = logm_workspace_size(batch, opts);
+  if (inner == 0) return 0;
+  return 2 * round256(host_matrix_bytes(batch)) + round256(3 * sizeof(int32_t) * (size_t)batch->count) + inner;
+}
+
+int logm_execute_host(const logm_batch* batch, const logm_options* opts, const void* A_host, void* L_host,
+                      int32_t* s_host, int32_t* k_host, int32_t* info_host, void* ws, size_t ws_bytes,
+                      void* stream) {
+  if (batch_n_max(batch) <= 0 || !opts_ok(opts)) return LOGM_ERR_INVALID_ARG;
+  if (batch->n_uniform <= 0) return LOGM_ERR_UNSUPPORTED;
+  if (batch->count == 0) return LOGM_SUCCESS;
+  if (!A_host || !L_host || !info_host) return LOGM_ERR_INVALID_ARG;
+  const size_t need = logm_host_workspace_size(batch, opts);
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256 != 0 || ws_bytes < need) return LOGM_ERR_WORKSPACE;
+  const size_t mb = host_matrix_bytes(batch), mr = round256(mb);
+  const size_t cnt = (size_t)batch->count;
+  char* w = static_cast<char*>(ws);
+  void* A_dev = w;
+  void* L_dev = w + mr;
+  int32_t* s_dev = reinterpret_cast<int32_t*>(w + 2 * mr);
+  int32_t* k_dev = s_dev + cnt;
+  int32_t* info_dev = k_dev + cnt;
+  char* inner = w + 2 * mr + round256(3 * sizeof(int32_t) * cnt);
+  const size_t inner_bytes = ws_bytes - (size_t)(inner - w);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(A_dev, A_host, mb, cudaMemcpyHostToDevice, st) != cudaSuccess) return LOGM_ERR_CUDA;
+  const int r = logm_execute(batch, opts, A_dev, L_dev, s_dev, k_dev, info_dev, nullptr, nullptr, inner,
+                             inner_bytes, stream);
+  if (r != LOGM_SUCCESS) return r;
+  if (cudaMemcpyAsync(L_host, L_dev, mb, cudaMemcpyDeviceToHost, st) != cudaSuccess) return LOGM_ERR_CUDA;
+  const size_t ib = sizeof(int32_t) * cnt;
+  if (s_host && cudaMemcpyAsync(s_host, s_dev, ib, cudaMemcpyDeviceToHost, st) != cudaSuccess) return LOGM_ERR_CUDA;
+  if (k_host && cudaMemcpyAsync(k_host, k_dev, ib, cudaMemcpyDeviceToHost, st) != cudaSuccess) return LOGM_ERR_CUDA;
+  if (cudaMemcpyAsync(info_host, info_dev, ib, cudaMemcpyDeviceToHost, st) != cudaSuccess) return LOGM_ERR_CUDA;
+  return LOGM_SUCCESS;
+}
+
 int logm_probe_barrier(int32_t missing, double timeout_s, void* ws, size_t ws_bytes, void* stream) {
   if (missing < 0 || missing > 8 || !(timeout_s >= 1e-6 && timeout_s <= 60.0)) return LOGM_ERR_INVALID_ARG;
   if (!ws || ws_bytes < 16 || reinterpret_cast<uintptr_t>(ws) % 8 != 0) return LOGM_ERR_WORKSPACE;

@@ -60,3 +60,18 @@ def test_ragged_sizes_out_of_range_are_refused(precision):
         if n in mats:
             Lr, d = oracle.logm(mats[n])
             assert rel(out[offs[b]:offs[b] + n * n].reshape(n, n), Lr) <= tol, n
+
+
+@pytest.mark.parametrize("dtype,pinned", [(torch.float64, True), (torch.float64, False), (torch.float32, True)])
+def test_execute_host_matches_device_call(dtype, pinned):
+    # logm_execute_host (copies inside the C-ABI call) against logm_execute on
+    # device copies of the same matrices: identical results
+    A = torch.from_numpy(workloads.identity_plus(20, 48, seed=960, lo=0.2, hi=3.0)).to(dtype)
+    if pinned:
+        A = A.pin_memory()
+    Lh, sh, kh, ih = lg().logm_execute_host(A)
+    Ld, sd, kd, idv = lg().logm_execute(A.cuda())
+    assert not Lh.is_cuda and torch.equal(Lh, Ld.cpu())
+    assert torch.equal(sh, sd.cpu()) and torch.equal(kh, kd.cpu()) and torch.equal(ih, idv.cpu())
+    L1, _, _, _ = lg().logm_execute_host(A[3].contiguous())  # a single (n, n) matrix
+    assert torch.equal(L1, Ld[3].cpu())

@@ -57,3 +57,25 @@ def test_invalid_arguments_rejected_before_launch():
     o.balance = 0
     rc = L.logm_execute(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, None, None, 0, None)
     assert rc == _lib.ERR_INVALID_ARG
+
+
+def test_execute_host_argument_checks():
+    # refusals that happen before any CUDA call
+    from paper_2401_10089_gb300 import _lib
+    L = _lib.load()
+    b = _lib.LogmBatch()
+    b.count, b.dtype, b.n_uniform, b.n_max = 2, 0, 0, 8  # ragged: not supported on host buffers
+    o = _lib.LogmOptions()
+    o.k_max, o.precision, o.max_sqrt, o.max_db_iter = 5, 0, 40, 50
+    n = (ctypes.c_int32 * 2)(8, 8)
+    b.n = ctypes.cast(n, ctypes.c_void_p)
+    b.offset = ctypes.cast((ctypes.c_int64 * 2)(0, 64), ctypes.c_void_p)
+    rc = L.logm_execute_host(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, 0, None)
+    assert rc == _lib.ERR_UNSUPPORTED
+    b.n_uniform = 8
+    b.count = 0
+    rc = L.logm_execute_host(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, 0, None)
+    assert rc == _lib.SUCCESS  # empty batch: nothing to do
+    o.k_max = 6
+    rc = L.logm_execute_host(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, 0, None)
+    assert rc == _lib.ERR_INVALID_ARG
