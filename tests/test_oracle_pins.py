@@ -103,8 +103,26 @@ def test_k4_coefficients_give_taylor_t14():
     pytest.importorskip("mpmath")
     c = backward_error_coeffs(z, N=20)
     assert abs(c[0]) < 1e-40 and abs(c[1]) < 1e-40
-    assert max(abs(float(c[k])) for k in range(3, 15)) < U
+    # Sec. 5 states |c_k| <= 3.95e-17 (k = 3..14) for the paper's own 14+
+    # coefficients; this root meets the same bound (measured 2.0e-17)
+    assert max(abs(float(c[k])) for k in range(3, 15)) <= 3.95e-17
     assert abs(float(c[15])) > 1e-3  # the first term the scheme leaves (x^15)
+
+
+def test_k5_rounded_coefficient_backward_error_claim():
+    # Sec. 5 states 0 < |c_k| < 4.76e-17 for k = 3..14 with the k = 5
+    # coefficients rounded to doubles. For the printed decimals (Table
+    # table_simple_experiment) it does not hold: c_3 = 1.1e-16, c_13 = 1.2e-15,
+    # c_14 = 5.9e-14 -- the same deviation as the monomial claim (b_13, b_14).
+    # Pinned at the measured values (within 10 %).
+    pytest.importorskip("mpmath")
+    c = backward_error_coeffs(k5_monomials(*oracle.coeffs_k5()), N=20)
+    assert abs(c[0]) < 1e-40 and abs(c[1]) < 1e-40
+    got = [abs(float(c[k])) for k in range(3, 15)]
+    assert max(got[:10]) < 1.2e-16                      # k = 3..12: within about u
+    assert 1.0e-16 < got[0] < 1.2e-16                    # c_3
+    assert 1.07e-15 < got[10] < 1.31e-15                 # c_13
+    assert 5.3e-14 < got[11] < 6.5e-14                   # c_14
 
 
 def test_k3_coefficients_give_taylor_t8():
