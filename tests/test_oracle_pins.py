@@ -109,6 +109,19 @@ def test_k4_coefficients_give_taylor_t14():
     assert abs(float(c[15])) > 1e-3  # the first term the scheme leaves (x^15)
 
 
+def test_coefficients_beyond_m_k_within_one():
+    # Sec. 5: the monomial coefficients past m_k differ from the Taylor
+    # coefficients 1/i by at most 100 % -- |(1/i - b_i) i| <= 1 for i > m_k --
+    # for the k = 5 graph, like those of the 14+ scheme for i > 14.
+    from fractions import Fraction
+    z5 = k5_monomials(*oracle.coeffs_k5())
+    dev5 = [abs(float((Fraction(1, i) - z5[i]) * i)) for i in range(15, 33)]
+    assert max(dev5) <= 1.0 and dev5[-1] > 0.99  # the top coefficients are nearly free
+    z4 = k4_monomials(oracle.coeffs_k4())
+    dev4 = [abs(float((Fraction(1, i) - z4[i]) * i)) for i in (15, 16)]
+    assert max(dev4) <= 1.0
+
+
 def test_k5_rounded_coefficient_backward_error_claim():
     # Sec. 5 states 0 < |c_k| < 4.76e-17 for k = 3..14 with the k = 5
     # coefficients rounded to doubles. For the printed decimals (Table
