@@ -120,12 +120,15 @@ _ws_host = _Workspace()
 
 
 def logm_workspace_size(A, **opts) -> int:
+    """Device workspace bytes of logm_plan / logm_sqrt / logm_graph_eval / logm_execute for batch A."""
     L = _lib.load()
     b, o = _batch(A), _options(**opts)
     return int(L.logm_workspace_size(ctypes.byref(b), ctypes.byref(o)))
 
 
 def logm_context_size(A, **opts) -> int:
+    """Bytes of the context logm_execute(with_ctx=True) saves for the backward: (s, k), the balancing
+    diagonal and every square-root level's input per matrix."""
     L = _lib.load()
     b, o = _batch(A), _options(**opts)
     return int(L.logm_context_size(ctypes.byref(b), ctypes.byref(o)))
@@ -273,6 +276,7 @@ def logm_execute_host(A, out=None, device=None, workspace=None, **opts):
 
 
 def logm_backward_workspace_size(A, **opts) -> int:
+    """Device workspace bytes of logm_backward for batch A (0: unsupported, n_max > 256)."""
     L = _lib.load()
     b, o = _batch(A), _options(**opts)
     return int(L.logm_backward_workspace_size(ctypes.byref(b), ctypes.byref(o)))
