@@ -47,15 +47,40 @@ def measured_peaks():
         return {}
 
 
-def fp64_peak_tflops(sustained: bool = False):
-    """FP64 dense peak = measured BF16 dense peak x nominal FP64/BF16 ratio (1.25 / 2250);
-    the sustained BF16 figure for a kernel that runs for seconds."""
-    pk = measured_peaks()
-    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
-    if key in pk:
-        what = "sustained" if sustained else "burst"
-        return pk[key] * 1.25 / 2250.0, f"of measured (bf16 {what} x nominal fp64/bf16 ratio)"
-    return (1700.0 if sustained else 1900.0) * 1.25 / 2250.0, "of fallback (bf16 x nominal fp64/bf16 ratio)"
+def measure_gemm_peak(torch, dev, dtype, clocks_index, n=8192, seconds=2.5, tf32=False):
+    """Dense peak measured here, outside the timed region: torch.matmul of two
+    n x n matrices (cuBLAS DGEMM for float64, TF32 tensor cores for float32
+    with TF32 allowed) back to back for about `seconds`, CUDA events on the
+    current stream, nvidia-smi clocks sampled meanwhile. 2 n^3 flops per call."""
+    old = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = bool(tf32)
+    try:
+        g = torch.Generator(device=dev)
+        g.manual_seed(7)
+        a = torch.randn((n, n), generator=g, device=dev, dtype=dtype)
+        b = torch.randn((n, n), generator=g, device=dev, dtype=dtype)
+        c = torch.empty((n, n), device=dev, dtype=dtype)
+        torch.matmul(a, b, out=c)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        reps = max(3, int(seconds / max(e0.elapsed_time(e1) * 1e-3, 1e-6)))
+        with Clocks(clocks_index) as clk:
+            torch.cuda.synchronize(dev)
+            e0.record()
+            for _ in range(reps):
+                torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) * 1e-3
+        del a, b, c
+        return {"tflops": 2.0 * n ** 3 * reps / t / 1e12, "n": n, "reps": reps, "seconds": t,
+                "clocks": clk.summary()}
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
 
 
 class Clocks:
@@ -121,13 +146,12 @@ def algorithmic_flops(stats: np.ndarray, n: int) -> float:
 
 def oracle_flops(diags, n: int) -> float:
     """Algorithmic work of the oracle's executed plans, counted like the GPU's:
-    2n^3 per inverse (Y_0 = I needs none) and per graph product; the
+    2n^3 per inversion (the oracle's own count) and per graph product; the
     estimator's 2n^2 matrix-vector products are left out (negligible)."""
     tot = 0.0
     for d in diags:
-        inverses = 2 * d["db_iters"] - d["s"]
         products = (d["k"] - 1) + (1 if d["s"] == 0 else 0)
-        tot += 2.0 * n ** 3 * (inverses + products)
+        tot += 2.0 * n ** 3 * (d["n_inv"] + products)
     return tot
 
 
@@ -136,20 +160,22 @@ def cpu_baseline(A_np, sample: int):
     import oracle
     cores = len(os.sched_getaffinity(0))
     mats = [A_np[i] for i in range(sample)]
-    oracle.logm_batch(mats[:1], nthreads=cores)  # build/load outside the timing
+    oracle.logm_batch(mats[:1], nthreads=cores, reuse_root=1)  # build/load outside the timing
     t0 = time.perf_counter()
-    Ls, ds = oracle.logm_batch(mats, nthreads=cores)
+    Ls, ds = oracle.logm_batch(mats, nthreads=cores, reuse_root=1)
     dt = time.perf_counter() - t0
     return {"value": oracle_flops(ds, A_np.shape[1]) / dt / 1e12, "unit": UNIT, "matrices_per_s": sample / dt,
             "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} of the {COUNT} 256x256 matrices (same seed), one OpenMP thread per matrix",
+            "sample": (f"first {sample} of the {COUNT} 256x256 matrices (same seed), one OpenMP thread per matrix, "
+                       "later square roots started from the previous root's Y as the CUDA path does"),
             "seconds": dt}, Ls, ds
 
 
 def arm_config(count, big, big_n, world):
-    """The `config` of the JSON line (the same for both arms at the default sizes)."""
+    """The `config` of the JSON line: what the arm runs each step."""
     return {"workload": WORKLOAD if (count == COUNT and big and big_n == NBIG) else
-            f"{count} x 256x256 A = I + E" + (f" + one {big_n}^2 Q T Q^T" if big else "") + ", FP64 path",
+            f"{count} x 256x256 A = I + E (||E||_1 ~ U[0.2, 5])" + (f" + one {big_n}^2 Q T Q^T" if big else "")
+            + ", seeded, FP64 path",
             "count": count, "n": N, "n_big": big_n if big else None, "precision": "fp64",
             "l2": "inputs larger than the 129 MB L2; no flush", "parallelism": f"batch-sharded x{world}"}
 
@@ -165,23 +191,24 @@ def run_reference(args, rank, world):
     import oracle
     cores = cb["cores"]
     for _ in range(args.warmup):
-        oracle.logm_batch([A[0]], nthreads=cores)
+        oracle.logm_batch([A[0]], nthreads=cores, reuse_root=1)
     times, flops = [], 0.0
     for s in range(args.steps):
         t0 = time.perf_counter()
-        _, ds_s = oracle.logm_batch([A[(s * sample + i) % COUNT] for i in range(sample)], nthreads=cores)
+        _, ds_s = oracle.logm_batch([A[(s * sample + i) % COUNT] for i in range(sample)], nthreads=cores,
+                                    reuse_root=1)
         times.append(time.perf_counter() - t0)
         flops += oracle_flops(ds_s, N)
     value = flops / sum(times) / 1e12
     cb["value"] = value
     cb["sample"] = (f"each step the oracle on {sample} of the 512 256x256 matrices (same seed), one OpenMP thread "
-                    "per matrix; the 4096x4096 matrix is not in the sample (the oracle would need hours for it)")
+                    "per matrix; the 4096x4096 matrix is not run (the oracle would need hours for it)")
     cb["matrices_per_s"] = sample * len(times) / sum(times)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "matrices_per_s": cb["matrices_per_s"],
-           "config": arm_config(COUNT, True, NBIG, world),
+           "config": arm_config(sample, False, None, world),
            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -196,7 +223,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the precision and differentiation forms")
-    ap.add_argument("--batching", action="store_true", help="also time the 20,000-matrix ragged batching form")
+    ap.add_argument("--no-batching", action="store_true", help="skip the 20,000-matrix ragged batching form")
     ap.add_argument("--count", type=int, default=COUNT, help="matrices per rank (smaller for profiling)")
     ap.add_argument("--no-big", action="store_true", help="leave out the 4096 x 4096 matrix")
     ap.add_argument("--big-n", type=int, default=NBIG, help="size of the large matrix (smaller for profiling)")
@@ -373,13 +400,13 @@ def main():
             "matrices_per_s_fwd_bwd": 1024 / ((fwd_ms + bwd_ms) * 1e-3),
             "forward_tflops": algorithmic_flops(st_d.cpu().numpy(), 64) / (fwd_ms * 1e-3) / 1e12,
             "backward_info_nonzero": int((bi.cpu().numpy() != 0).sum())}
-    # batching form (opt-in, input generation takes ~30 s): 20,000 SPD matrices,
-    # n uniform in {4, 8, ..., 256}, lambda log-uniform in [1e-3, 1e3], FP32 storage,
-    # TF32x3 graph products, one logm_execute call
-    if args.batching:
-        vals, ns_r, offs_r = workloads.ragged_spd(20000, seed=4 + rank)
-        R = lg.Ragged(torch.from_numpy(vals).to(dev), torch.from_numpy(ns_r).to(dev),
-                      torch.from_numpy(offs_r).to(dev), 256)
+    # batching form: 20,000 SPD matrices, n uniform in {4, 8, ..., 256}, lambda
+    # log-uniform in [1e-3, 1e3], FP32 storage, one logm_execute call (TF32x3 and
+    # FP64 graph products); the inputs are drawn on the device
+    if not args.no_batching and not args.no_forms:
+        vals_d, ns_d, offs_d = workloads.ragged_spd_device(20000, dev, seed=4 + rank)
+        ns_r = ns_d.cpu().numpy()
+        R = lg.Ragged(vals_d, ns_d, offs_d, 256)
         st_r = torch.zeros(4 * 20000, dtype=torch.int32, device=dev)
         entry = {}
         for prec in ("tf32x3", "fp64"):
@@ -403,13 +430,18 @@ def main():
         forms["batching"] = entry
 
     if rank == 0:
-        # dominant kernel: the whole-GPU 4096 kernel (seconds long -> sustained peak)
+        # FP64 and TF32 dense peaks measured on this GPU (cuBLAS GEMM loops of a
+        # few seconds, outside the timed region, clocks sampled meanwhile)
+        peaks = {"fp64": measure_gemm_peak(torch, dev, torch.float64, local),
+                 "tf32": measure_gemm_peak(torch, dev, torch.float32, local, tf32=True)}
+        peak = peak_a = peaks["fp64"]["tflops"]
+        peak_note = ("of measured: cuBLAS DGEMM 8192^3 (torch.matmul float64) back to back for "
+                     f"{peaks['fp64']['seconds']:.1f} s in this run")
+        # dominant kernel: the whole-GPU 4096 kernel
         if big:
-            peak, peak_note = fp64_peak_tflops(sustained=True)
             ach = flops_b / (ms_b * 1e-3) / 1e12
             kname, fpl = "k_logm_large<execute> (cooperative, whole GPU on the 4096 matrix)", flops_b
         else:
-            peak, peak_note = fp64_peak_tflops()
             ach = flops_a / (ms_a * 1e-3) / 1e12
             kname, fpl = "k_logm_small<execute> (persistent, one block per matrix)", flops_a
         # DRAM bytes of the dominant kernel from ncu (dram__bytes_read.sum +
@@ -424,10 +456,9 @@ def main():
                             "kernel and plan (traffic grows with n^3); far below HBM bandwidth, FP64-pipe bound")
         else:
             traffic = None
-        pk_a, note_a = fp64_peak_tflops()
         parts = {"batch256": {"ms": ms_a, "matrices_per_s": count / (ms_a * 1e-3),
                               "tflops": flops_a / (ms_a * 1e-3) / 1e12,
-                              "frac": flops_a / (ms_a * 1e-3) / 1e12 / pk_a, "peak_note": "FP64 " + note_a,
+                              "frac": flops_a / (ms_a * 1e-3) / 1e12 / peak_a, "peak_note": "FP64 dense " + peak_note,
                               "s_hist": np.bincount(s_np).tolist(), "k_hist": np.bincount(k_np, minlength=6).tolist(),
                               "info_nonzero": int((info_np != 0).sum()),
                               "work": dict(zip(("db_iterations", "inverses", "products"),
@@ -447,6 +478,7 @@ def main():
                          "frac": ach / peak, "traffic": traffic, "traffic_note": traffic_note,
                          "peak_note": "FP64 dense " + peak_note,
                          "kernel": kname, "flops_per_launch": fpl},
+            "peaks_measured": peaks,
             "e2e": {"value": (flops_a + flops_b) * world / (e2e_ms * 1e-3) / 1e12 if e2e_steps else None,
                     "unit": UNIT, "matrices_per_s": n_mats * world / (e2e_ms * 1e-3) if e2e_steps else None,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -458,7 +490,7 @@ def main():
             Lg = L.cpu().numpy()
             errs = [np.linalg.norm(Lg[i] - Ls[i]) / np.linalg.norm(Ls[i]) for i in range(len(Ls))
                     if (ds[i]["s"], ds[i]["k"]) == (int(s_np[i]), int(k_np[i]))]
-            cb["sample"] += "; the 4096 matrix is not in the sample (the oracle would need hours for it)"
+            cb["sample"] += "; the 4096 matrix is not run (the oracle would need hours for it)"
             out["cpu_baseline"] = cb
             out["rel_err_vs_oracle"] = {"max": float(max(errs)) if errs else None, "matrices": len(errs)}
         print(json.dumps(out), flush=True)

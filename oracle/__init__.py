@@ -16,7 +16,9 @@ paper it follows:
                       14+ scheme for k = 4 (``coeffs_k4``, solved here; the
                       paper does not print it).
 * ``sqrtm_db``     -- scaled Denman-Beavers iteration, eq. (ScalDB), Sec. 6, or
-                      its product form (``form=1``, the variant cited in Sec. 2).
+                      its product form (``form=1``, the variant cited in Sec. 2);
+                      ``logm`` runs eq. (ScalDB) as written at every level unless
+                      ``reuse_root=1`` (later levels start from the previous Y).
 * ``balance``      -- the diagonal balancing T of Algorithm 1, Step 1.
 * ``normest_pow``  -- 1-norm power estimate (Higham 1988, cited in Sec. 6),
                       with A_I2 of eq. (AI2) for even powers.
@@ -62,7 +64,7 @@ class Opts(ctypes.Structure):
         ("force_k", ctypes.c_int32),
         ("db_form", ctypes.c_int32),
         ("balance", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("reuse_root", ctypes.c_int32),
         ("theta", ctypes.c_double * 5),
     ]
 
@@ -74,10 +76,13 @@ class Diag(ctypes.Structure):
         ("info", ctypes.c_int32),
         ("db_iters", ctypes.c_int32),
         ("n_estimates", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("n_inv", ctypes.c_int32),
         ("alpha", ctypes.c_double),
         ("norm_b", ctypes.c_double),
         ("norm_ai2", ctypes.c_double),
+        ("margin", ctypes.c_double),
+        ("margin_s", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -138,11 +143,15 @@ def _ptr(a):
 
 
 def make_opts(k_max=5, max_sqrt=40, max_db_iter=50, force_s=-1, force_k=0, theta=None,
-              db_form=0, balance=0) -> Opts:
+              db_form=0, balance=0, reuse_root=0) -> Opts:
+    """Options of Algorithm 1. ``reuse_root=0`` (default) runs eq. (ScalDB)
+    as written at every square-root level; ``reuse_root=1`` starts later
+    levels from the previous level's Y as A^{-1} (one inversion fewer per
+    level, the same iterates in exact arithmetic)."""
     o = Opts()
     o.k_max, o.max_sqrt, o.max_db_iter = k_max, max_sqrt, max_db_iter
     o.force_s, o.force_k = force_s, force_k
-    o.db_form, o.balance = db_form, balance
+    o.db_form, o.balance, o.reuse_root = db_form, balance, reuse_root
     th = THETA_TABLE if theta is None else theta
     for t in range(5):
         o.theta[t] = th[t]
@@ -261,7 +270,9 @@ def plan(A, AI2=None, **kw):
 
 
 def logm(A, **kw):
-    """(L, diag dict) by Algorithm 1."""
+    """(L, diag dict) by Algorithm 1. The diag's ``margin`` is the smallest
+    relative distance of a plan quantity from the threshold it was compared
+    with, ``margin_s`` the square-root level of that comparison."""
     A = _c(A)
     L = np.empty_like(A)
     o = make_opts(**kw)

@@ -40,9 +40,11 @@
  *    them lands on the table's 9.31e-2; k = 5 is Table
  *    table_simple_experiment. k >= 6 have no coefficients in the paper, so
  *    the available orders are k in {1, 2, 3, 4, 5};
- *  - a root of a root: from the second level on, the first Denman-Beavers
- *    step takes the previous level's converged Y as X_0^{-1} = A^{-1} (and
- *    half the previous log|det|) instead of inverting A (eq. ScalDB form);
+ *  - every square-root level runs eq. (ScalDB) as written (X_0 = A,
+ *    Y_0 = I; Y_0 needs no inversion). Opt-in (orc_opts.reuse_root), a root
+ *    of a root: from the second level on, the first Denman-Beavers step
+ *    takes the previous level's converged Y as X_0^{-1} = A^{-1} (and half
+ *    the previous log|det|) instead of inverting A;
  *  - the balancing T of Algorithm 1 (optional) is diagonal scaling by powers
  *    of 2 (the Parlett-Reinsch iteration with 1-norms of the off-diagonal
  *    parts of rows and columns, no permutations), so that T^{-1} A T and
@@ -60,7 +62,7 @@
 
 #define ORC_U 0x1p-53 /* unit roundoff of IEEE binary64 */
 
-int orc_version(void) { return 2; }
+int orc_version(void) { return 3; }
 
 /* ------------------------------------------------------------------------ */
 /* Coefficients of the degree-optimal form, eq. (five_mult_degopt).         */
@@ -361,13 +363,15 @@ int orc_inverse(int n, const double* A, double* Ainv, double* logabsdet) {
 /* Y_{k+1} = (mu_k Y_k + mu_k^{-1} X_k^{-1}) / 2,                           */
 /* X_0 = A, Y_0 = I, mu_k = |det X_k det Y_k|^{-1/(2n)}.                    */
 /* ------------------------------------------------------------------------ */
-/* The iteration of eq. (ScalDB). With x0inv given, it is taken as X_0^{-1}
- * = A^{-1} and ld0 as log|det A| in the first step instead of inverting A
- * (Algorithm 1 takes a root of the previous level's root: the previous
- * level's Y converged to that root's inverse). Yout (or NULL) receives the
- * final Y, *ld0_out the log|det A| used. */
+/* The iteration of eq. (ScalDB). Y_0 = I is its own inverse (log|det Y_0|
+ * = 0), so the first step inverts X_0 = A only. With x0inv given, it is
+ * taken as X_0^{-1} = A^{-1} and ld0 as log|det A| in the first step instead
+ * of inverting A (the opt-in shortcut for Algorithm 1's later roots, whose
+ * A's inverse the previous level's Y converged to). Yout (or NULL) receives
+ * the final Y, *ld0_out the log|det A| used; *ninv (or NULL) counts the
+ * inversions performed. */
 static int db_core(int n, const double* A, double* Xout, int max_iter, int32_t* iters, const double* x0inv,
-                   double ld0, double* Yout, double* ld0_out) {
+                   double ld0, double* Yout, double* ld0_out, int32_t* ninv) {
   double* X = alloc_mat(n);
   double* Y = alloc_mat(n);
   double* Xi = alloc_mat(n);
@@ -382,12 +386,22 @@ static int db_core(int n, const double* A, double* Xout, int max_iter, int32_t* 
   const size_t nn = (size_t)n * n;
   for (it = 1; it <= max_iter; ++it) {
     double ldx, ldy;
-    if (it == 1 && x0inv) {
-      memcpy(Xi, x0inv, sizeof(double) * nn);
-      ldx = ld0;
-      set_identity(n, Yi);
+    int sing = 0;
+    if (it == 1) {
+      set_identity(n, Yi); /* Y_0 = I */
       ldy = 0.0;
-    } else if (orc_inverse(n, X, Xi, &ldx) != ORC_OK || orc_inverse(n, Y, Yi, &ldy) != ORC_OK) {
+      if (x0inv) {
+        memcpy(Xi, x0inv, sizeof(double) * nn);
+        ldx = ld0;
+      } else {
+        sing = orc_inverse(n, X, Xi, &ldx) != ORC_OK;
+        if (ninv) *ninv += 1;
+      }
+    } else {
+      sing = orc_inverse(n, X, Xi, &ldx) != ORC_OK || orc_inverse(n, Y, Yi, &ldy) != ORC_OK;
+      if (ninv) *ninv += 2;
+    }
+    if (sing) {
       status = ORC_SINGULAR;
       break;
     }
@@ -436,12 +450,12 @@ static int db_core(int n, const double* A, double* Xout, int max_iter, int32_t* 
 }
 
 int orc_sqrtm_db(int n, const double* A, double* Xout, int max_iter, int32_t* iters) {
-  return db_core(n, A, Xout, max_iter, iters, NULL, 0.0, NULL, NULL);
+  return db_core(n, A, Xout, max_iter, iters, NULL, 0.0, NULL, NULL, NULL);
 }
 
 int orc_sqrtm_db_reuse(int n, const double* A, double* Xout, int max_iter, int32_t* iters, const double* Ainv,
                        double logabsdet) {
-  return db_core(n, A, Xout, max_iter, iters, Ainv, logabsdet, NULL, NULL);
+  return db_core(n, A, Xout, max_iter, iters, Ainv, logabsdet, NULL, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -467,7 +481,13 @@ static double norm1_shift(int n, const double* A, double s) {
   return best;
 }
 
+static int db_product_core(int n, const double* A, double* Xout, int max_iter, int32_t* iters, int32_t* ninv);
+
 int orc_sqrtm_db_product(int n, const double* A, double* Xout, int max_iter, int32_t* iters) {
+  return db_product_core(n, A, Xout, max_iter, iters, NULL);
+}
+
+static int db_product_core(int n, const double* A, double* Xout, int max_iter, int32_t* iters, int32_t* ninv) {
   double* X = alloc_mat(n);
   double* M = alloc_mat(n);
   double* Mi = alloc_mat(n);
@@ -482,6 +502,7 @@ int orc_sqrtm_db_product(int n, const double* A, double* Xout, int max_iter, int
   double dprev = INFINITY;
   for (it = 1; it <= max_iter; ++it) {
     double ldm;
+    if (ninv) *ninv += 1;
     if (orc_inverse(n, M, Mi, &ldm) != ORC_OK) {
       status = ORC_SINGULAR;
       break;
@@ -770,8 +791,31 @@ typedef struct {
 /* Returns 1 when alpha_m <= theta. *alpha gets max(term1^{1/m},
  * term2^{1/(m+1)}) of the values used (estimates or bounds; term2 only if it
  * was needed). AI2 NULL means s = 0: powers are applied with B. */
+/* Every comparison of a plan quantity with its threshold goes through le_th,
+ * which also records how close the two were: mt->margin is the smallest
+ * relative distance |x - t| / t seen so far and mt->level the square-root
+ * level (mt->cur) where it was seen. A second implementation that decides
+ * differently from this one is only right when such a comparison was within
+ * rounding of its threshold (mt may be NULL). */
+typedef struct {
+  double margin;
+  int level;
+  int cur;
+} margin_t;
+
+static int le_th(double x, double t, margin_t* mt) {
+  if (mt && t > 0.0) {
+    const double r = fabs(x - t) / t;
+    if (!(r >= mt->margin)) { /* also takes a NaN distance as the closest */
+      mt->margin = r;
+      mt->level = mt->cur;
+    }
+  }
+  return x <= t;
+}
+
 static int alpha_test(int n, const double* B, const double* AI2, double nB, double nI2, int m,
-                      double theta, est_state* st, double* alpha) {
+                      double theta, est_state* st, double* alpha, margin_t* mt) {
   const double th_m = ipow(theta, m), th_m1 = ipow(theta, m + 1);
   double t1, t2;
   int have_est1 = 0;
@@ -781,7 +825,7 @@ static int alpha_test(int n, const double* B, const double* AI2, double nB, doub
   /* First term ||B^m||: with A_I2, bounded by ||A_I2||^{m/2} (eq. normAm9). */
   if (AI2 && m == 2) {
     t1 = nI2; /* B^2 = A_I2 exactly */
-  } else if (AI2 && ipow(nI2, m / 2) <= th_m) {
+  } else if (AI2 && le_th(ipow(nI2, m / 2), th_m, mt)) {
     t1 = ipow(nI2, m / 2); /* eq. (alpha2term1): no estimate needed */
   } else {
     t1 = orc_normest_pow(n, B, AI2, m);
@@ -789,14 +833,14 @@ static int alpha_test(int n, const double* B, const double* AI2, double nB, doub
     st->t_m = t1;
     have_est1 = 1;
   }
-  if (!(t1 <= th_m)) {
+  if (!le_th(t1, th_m, mt)) {
     *alpha = pow(t1, 1.0 / m);
     return 0;
   }
   /* Second term ||B^{m+1}|| <= ||B^m|| ||B|| (eq. normAm9plus1), with the
    * estimate of ||B^m|| when there is one, else ||A_I2||^{m/2}. */
   double base = have_est1 ? t1 : (AI2 ? ipow(nI2, m / 2) : t1);
-  if (base * nB <= th_m1) {
+  if (le_th(base * nB, th_m1, mt)) {
     t2 = base * nB;
   } else {
     t2 = orc_normest_pow(n, B, AI2, m + 1);
@@ -805,7 +849,7 @@ static int alpha_test(int n, const double* B, const double* AI2, double nB, doub
   }
   double a1 = pow(t1, 1.0 / m), a2 = pow(t2, 1.0 / (m + 1));
   *alpha = a1 > a2 ? a1 : a2;
-  return t2 <= th_m1;
+  return le_th(t2, th_m1, mt);
 }
 
 /* Order search of Sec. 6 (Step 'StepFinminm' of Algorithm 1), read as:
@@ -815,7 +859,7 @@ static int alpha_test(int n, const double* B, const double* AI2, double nB, doub
  *  if min_im >= max_in take max_in, else test k = min_im.. in turn, taking
  *  k+1 at once when alpha_{m_k} > Theta_k but <= Theta_{k+1}. */
 static int order_search(int n, const double* B, const double* AI2, double nB, double nI2,
-                        const orc_opts* o, const est_state* loop_est, int* n_est) {
+                        const orc_opts* o, const est_state* loop_est, int* n_est, margin_t* mt) {
   int cands[5], nc = 0;
   const int all[5] = {1, 2, 3, 4, 5};
   for (int t = 0; t < 5; ++t)
@@ -827,8 +871,8 @@ static int order_search(int n, const double* B, const double* AI2, double nB, do
     int mm = loop_est->m;
     while (lo < nc - 1) {
       double th = o->theta[theta_index(cands[lo])];
-      int ok = loop_est->t_m <= ipow(th, mm);
-      if (ok && loop_est->t_m1 >= 0.0) ok = loop_est->t_m1 <= ipow(th, mm + 1);
+      int ok = le_th(loop_est->t_m, ipow(th, mm), mt);
+      if (ok && loop_est->t_m1 >= 0.0) ok = le_th(loop_est->t_m1, ipow(th, mm + 1), mt);
       if (ok) break;
       ++lo;
     }
@@ -838,7 +882,7 @@ static int order_search(int n, const double* B, const double* AI2, double nB, do
   for (int t = 0; t < nc; ++t) {
     int m = m_of_k(cands[t]);
     double th = o->theta[theta_index(cands[t])];
-    if (ipow(nI2, m / 2) * nB <= ipow(th, m + 1)) {
+    if (le_th(ipow(nI2, m / 2) * nB, ipow(th, m + 1), mt)) {
       hi = t;
       break;
     }
@@ -849,23 +893,23 @@ static int order_search(int n, const double* B, const double* AI2, double nB, do
     double th = o->theta[theta_index(cands[t])];
     est_state st = {-1.0, -1.0, m, 0};
     double a;
-    int ok = alpha_test(n, B, AI2, nB, nI2, m, th, &st, &a);
+    int ok = alpha_test(n, B, AI2, nB, nI2, m, th, &st, &a, mt);
     *n_est += st.n_est;
     if (ok) return cands[t];
     /* alpha_{m_k} <= Theta_{k+1} gives alpha_{m_{k+1}} <= Theta_{k+1}. */
     double thn = o->theta[theta_index(cands[t + 1])];
     double t1 = (st.t_m >= 0.0) ? st.t_m : (m == 2 ? nI2 : ipow(nI2, m / 2));
-    if (t1 <= ipow(thn, m)) {
+    if (le_th(t1, ipow(thn, m), mt)) {
       double t2 = st.t_m1;
       if (t2 < 0.0) {
-        if (t1 * nB <= ipow(thn, m + 1)) {
+        if (le_th(t1 * nB, ipow(thn, m + 1), mt)) {
           t2 = t1 * nB;
         } else {
           t2 = orc_normest_pow(n, B, AI2, m + 1);
           *n_est += 1;
         }
       }
-      if (t2 <= ipow(thn, m + 1)) return cands[t + 1];
+      if (le_th(t2, ipow(thn, m + 1), mt)) return cands[t + 1];
     }
   }
   return cands[hi];
@@ -901,7 +945,7 @@ int orc_plan(int n, const double* A, const double* AI2in, const orc_opts* o, int
     a = nB;
   } else {
     double nI2 = AI2in ? orc_norm1(n, AI2in) : 0.0;
-    fin = alpha_test(n, B, AI2in, nB, nI2, m, th, &st, &a);
+    fin = alpha_test(n, B, AI2in, nB, nI2, m, th, &st, &a, NULL);
   }
   *finish = fin;
   *alpha = a;
@@ -910,7 +954,7 @@ int orc_plan(int n, const double* A, const double* AI2in, const orc_opts* o, int
   else
     orc_gemm(n, B, B, AI2);
   int ne = 0;
-  *k = fin ? order_search(n, B, AI2, nB, orc_norm1(n, AI2), o, &st, &ne) : o->k_max;
+  *k = fin ? order_search(n, B, AI2, nB, orc_norm1(n, AI2), o, &st, &ne, NULL) : o->k_max;
   free(B);
   free(AI2);
   return ORC_OK;
@@ -968,32 +1012,36 @@ static int logm_core(int n, const double* A, double* L, const orc_opts* o, orc_d
   const int m = m_of_k(o->k_max);
   const double th = o->theta[theta_index(o->k_max)];
   est_state last = {-1.0, -1.0, m, 0};
+  margin_t mt = {INFINITY, -1, 0};
   int finish;
   double alpha = nB;
   if (o->force_s >= 0)
     finish = (o->force_s == 0);
   else
-    finish = nB <= th; /* finish = ||A - I|| <= Theta_{m_kmax} */
+    finish = le_th(nB, th, &mt); /* finish = ||A - I|| <= Theta_{m_kmax} */
   while (!finish && s < o->max_sqrt) {
+    mt.cur = s;
     if (o->force_s < 0) {
       est_state st = {-1.0, -1.0, m, 0};
-      finish = alpha_test(n, B, have_ai2 ? AI2 : NULL, nB, nI2, m, th, &st, &alpha);
+      finish = alpha_test(n, B, have_ai2 ? AI2 : NULL, nB, nI2, m, th, &st, &alpha, &mt);
       dd.n_estimates += st.n_est;
       last = st;
       if (finish) break;
     }
     /* A_2 <- A; A <- A^{1/2} by eq. (ScalDB); A_I2 = A_2 - 2A + I (eq. AI2).
-     * From the second level on, the first step's A^{-1} is the previous
-     * level's Y (converged to A_2^{-1/2} = A^{-1} of this level's A) and
-     * log|det A| is half the previous level's. */
+     * As written, every level starts from X_0 = A, Y_0 = I and inverts A.
+     * With o->reuse_root (opt-in), from the second level on the first step's
+     * A^{-1} is the previous level's Y (converged to A_2^{-1/2} = A^{-1} of
+     * this level's A) and log|det A| is half the previous level's. */
     memcpy(A2, Acur, sizeof(double) * nn);
     int32_t it = 0;
     int r;
     if (o->db_form == 1) {
-      r = orc_sqrtm_db_product(n, A2, Acur, o->max_db_iter, &it);
+      r = db_product_core(n, A2, Acur, o->max_db_iter, &it, &dd.n_inv);
     } else {
       double ld_used = 0.0;
-      r = db_core(n, A2, Acur, o->max_db_iter, &it, have_yprev ? Yprev : NULL, ld_prev, Yprev, &ld_used);
+      const int reuse = o->reuse_root && have_yprev;
+      r = db_core(n, A2, Acur, o->max_db_iter, &it, reuse ? Yprev : NULL, ld_prev, Yprev, &ld_used, &dd.n_inv);
       have_yprev = (r == ORC_OK);
       ld_prev = 0.5 * ld_used;
     }
@@ -1028,7 +1076,8 @@ static int logm_core(int n, const double* A, double* L, const orc_opts* o, orc_d
       k = o->k_max;
     } else {
       int ne = 0;
-      k = order_search(n, B, AI2, nB, nI2, o, (last.t_m >= 0.0) ? &last : NULL, &ne);
+      mt.cur = s;
+      k = order_search(n, B, AI2, nB, nI2, o, (last.t_m >= 0.0) ? &last : NULL, &ne, &mt);
       dd.n_estimates += ne;
     }
     /* L = -2^s z(X) with X = -(A - I) and P_3 = X^2 = A_I2 (eq. logipASTM). */
@@ -1040,6 +1089,8 @@ static int logm_core(int n, const double* A, double* L, const orc_opts* o, orc_d
   }
   dd.s = s;
   dd.info = info;
+  dd.margin = mt.margin;
+  dd.margin_s = mt.level;
   dd.alpha = alpha;
   dd.norm_b = nB;
   dd.norm_ai2 = nI2;

@@ -34,7 +34,8 @@ typedef struct {
   int32_t force_k;     /* <= 0: order search; else evaluate with this k */
   int32_t db_form;     /* 0: eq. (ScalDB), two inversions; 1: product form */
   int32_t balance;     /* 0: T = I; 1: diagonal balancing (Algorithm 1, Step 1) */
-  int32_t reserved;
+  int32_t reuse_root;  /* 0: eq. (ScalDB) as written at every level; 1: later levels
+                          start from the previous level's Y as A^{-1} (opt-in) */
   double theta[5];     /* Theta_{m_k} for k = 1..5 (Table Table_theta) */
 } orc_opts;
 
@@ -44,10 +45,13 @@ typedef struct {
   int32_t info;           /* ORC_* status */
   int32_t db_iters;       /* total Denman-Beavers iterations over all levels */
   int32_t n_estimates;    /* calls of the 1-norm power estimator */
-  int32_t reserved;
+  int32_t n_inv;          /* matrix inversions performed by the square roots */
   double alpha;           /* alpha_{m_kmax} value of the pass that set finish */
   double norm_b;          /* ||A^{1/2^s} - I||_1 on exit */
   double norm_ai2;        /* ||(A^{1/2^s} - I)^2||_1 on exit */
+  double margin;          /* smallest |x - t| / t over the plan's comparisons x <= t */
+  int32_t margin_s;       /* square-root level of that comparison (-1: none made) */
+  int32_t reserved;
 } orc_diag;
 
 int orc_version(void);

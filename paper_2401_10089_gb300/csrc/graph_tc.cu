@@ -409,18 +409,14 @@ cudaError_t launch_graph_tc(const GraphParams& p, cudaStream_t st) {
   const int n_pad = ((p.n_max + 15) / 16) * 16;
   const int tiles = ((p.n_max + kTcM - 1) / kTcM) * ((n_pad + kTcN - 1) / kTcN);
   const size_t smem = sizeof(TcSmem);
-  static bool attr_tf32 = false, attr_bf16 = false;
-  cudaError_t e;
-  if (!attr_tf32) {
-    e = cudaFuncSetAttribute(k_graph_tc<LOGM_PREC_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_tf32 = true;
-  }
-  if (!attr_bf16) {
-    e = cudaFuncSetAttribute(k_graph_tc<LOGM_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_bf16 = true;
-  }
+  static DeviceOnce attr;
+  cudaError_t e = attr.run([&] {
+    cudaError_t r =
+        cudaFuncSetAttribute(k_graph_tc<LOGM_PREC_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (r != cudaSuccess) return r;
+    return cudaFuncSetAttribute(k_graph_tc<LOGM_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
   const dim3 grid(tiles, p.count);
   for (int j = 1; j <= 5; ++j) {
     GraphParams q = p;

@@ -419,17 +419,17 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encoder() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  // the driver's entry point is the same for every device; looked up once
+  // (a function-local static is initialised once even with several threads)
+  static const EncodeTiledFn fn = [] {
     void* f = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(f);
-  }
+      return reinterpret_cast<EncodeTiledFn>(f);
+    return static_cast<EncodeTiledFn>(nullptr);
+  }();
   return fn;
 }
 
@@ -462,13 +462,11 @@ cudaError_t run_tma(const GraphParams& p, cudaStream_t st) {
   CUtensorMap ta, tb;
   if (!make_map(&ta, A, PREC, n_pad, planes, kTmM)) return cudaErrorNotSupported;
   if (!make_map(&tb, B, PREC, n_pad, planes, nbox)) return cudaErrorNotSupported;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_graph_tma<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static DeviceOnce attr;
+  cudaError_t ea = attr.run([] {
+    return cudaFuncSetAttribute(k_graph_tma<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmSmemBytes);
+  });
+  if (ea != cudaSuccess) return ea;
   const int tiles = ((n + kTmM - 1) / kTmM) * ((n_pad + nbox - 1) / nbox);
   const dim3 pgrid((n_pad / 32) * (n_pad / 32), p.count);
   for (int j = 1; j <= 5; ++j) {

@@ -7,10 +7,26 @@
 #include "../../include/logm.h"
 #include "logm_internal.h"
 
-namespace {
+namespace lg {
 
-// Table Table_theta, k = 1..5
-constexpr double kThetaPaper[5] = {1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1};
+int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  const bool cached = dev >= 0 && dev < 64;
+  if (cached) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 1;
+  if (cached) cache[dev].store(sms, std::memory_order_relaxed);
+  return sms;
+}
+
+}  // namespace lg
+
+namespace {
 
 // Kernel configuration per size bucket (logm_set_tuning).
 int g_variant[lg::kBuckets] = {0, 0, 0, 0, 0, 0};
@@ -129,7 +145,7 @@ void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o)
     p.k_max = o->k_max;
     p.max_sqrt = o->max_sqrt;
     p.max_db = o->max_db_iter;
-    for (int t = 0; t < 5; ++t) p.theta[t] = o->theta[t] > 0.0 ? o->theta[t] : kThetaPaper[t];
+    for (int t = 0; t < 5; ++t) p.theta[t] = o->theta[t] > 0.0 ? o->theta[t] : lg::kThetaPaper[t];
     p.precision = o->precision;
     p.db_form = o->db_form;
     p.balance = o->balance;
@@ -137,7 +153,7 @@ void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o)
     p.k_max = 5;
     p.max_sqrt = 40;
     p.max_db = 50;
-    for (int t = 0; t < 5; ++t) p.theta[t] = kThetaPaper[t];
+    for (int t = 0; t < 5; ++t) p.theta[t] = lg::kThetaPaper[t];
   }
   p.ctx_nmax = p.n_max;
   p.bal_stride = p.n_max;

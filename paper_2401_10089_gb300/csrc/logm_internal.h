@@ -2,11 +2,39 @@
 // the kernel launchers. Not installed; the public surface is include/logm.h.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace lg {
+
+// Theta_{m_k} of the paper's backward-error table (Sec. 5), k = 1..5: the
+// default bounds of the loop test and the order search (each entry point's
+// options may override them).
+constexpr double kThetaPaper[5] = {1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1};
+
+// Host set-up done once per device (e.g. a kernel's shared-memory attribute),
+// safe when several threads drive several devices: run() calls f() with the
+// caller's device current unless it already succeeded on that device
+// (devices 64 and up: every time).
+struct DeviceOnce {
+  std::atomic<unsigned long long> done{0};
+  template <class F>
+  cudaError_t run(F f) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = f();
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+  }
+};
+
+// Multiprocessor count of the current device (cached per device, thread safe).
+int device_sm_count();
 
 enum Mode : int { kModeExecute = 0, kModePlan = 1, kModeSqrt = 2, kModeGraph = 3, kModeBackward = 4 };
 
@@ -106,7 +134,6 @@ __host__ __device__ inline int size_bucket(int n) {
   return n <= 8 ? 0 : (n <= 16 ? 1 : (n <= 32 ? 2 : (n <= 64 ? 3 : (n <= 128 ? 4 : 5))));
 }
 size_t large_workspace_bytes(int n_max);
-int large_grid_size();
 cudaError_t launch_large(Mode mode, const SmallParams& p, void* ws, cudaStream_t stream);
 cudaError_t launch_barrier_probe(int missing, unsigned long long timeout_ns, void* ws, cudaStream_t stream);
 size_t small_workspace_bytes(int count, int n_max);

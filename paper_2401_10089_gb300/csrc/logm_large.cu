@@ -89,8 +89,6 @@ LargeLayout large_layout(int n_max) {
   return L;
 }
 
-int g_large_grid = 0;
-
 template <int MODE>
 cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
   const LargeLayout L = large_layout(p.n_max);
@@ -148,7 +146,6 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
     }
   }
   if (grid < 1) return cudaErrorLaunchOutOfResources;
-  g_large_grid = grid;
 
   e = cudaMemsetAsync(ws + L.bar, 0, 64, st);
   if (e != cudaSuccess) return e;
@@ -160,8 +157,6 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
 }  // namespace
 
 size_t large_workspace_bytes(int n_max) { return large_layout(n_max).total; }
-
-int large_grid_size() { return g_large_grid; }
 
 // Self-test of the grid barrier's bound: two co-resident blocks wait at a
 // barrier for 2 + missing arrivals; with missing > 0 nobody completes it, so

@@ -22,8 +22,6 @@ namespace {
 
 constexpr size_t kNoallocScratchBytes = size_t(32) << 20;
 constexpr int kMaxDevices = 64;
-// Table Table_theta, k = 1..5
-constexpr double kThetaPaperNoalloc[5] = {1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1};
 
 // The scratch array. Host code must not pass `g_noalloc_scratch` itself to a
 // kernel: on the host that name is a stand-in, not a device address. The
@@ -97,7 +95,7 @@ extern "C" int logm_execute_noalloc(const logm_batch* batch, const logm_options*
   p.k_max = opts->k_max;
   p.max_sqrt = opts->max_sqrt;
   p.max_db = opts->max_db_iter;
-  for (int t = 0; t < 5; ++t) p.theta[t] = opts->theta[t] > 0.0 ? opts->theta[t] : kThetaPaperNoalloc[t];
+  for (int t = 0; t < 5; ++t) p.theta[t] = opts->theta[t] > 0.0 ? opts->theta[t] : lg::kThetaPaper[t];
   p.precision = opts->precision;
   p.db_form = opts->db_form;
   p.A = A;

@@ -161,21 +161,9 @@ __global__ void __launch_bounds__(kThreads, LG_MINBLOCKS) k_logm_small(SmallPara
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-static int g_sm_count = 0;
-
-static int sm_count() {
-  if (g_sm_count == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sm_count <= 0) g_sm_count = 1;
-  }
-  return g_sm_count;
-}
-
 int small_kernel_slots(int count) {
   const int per_sm = LG_MINBLOCKS;  // blocks resident per SM (shared memory and registers)
-  const int cap = sm_count() * per_sm;
+  const int cap = lg::device_sm_count() * per_sm;
   return count < cap ? (count > 0 ? count : 1) : cap;
 }
 
@@ -197,20 +185,18 @@ size_t small_workspace_bytes(int count, int n_max) {
 
 template <int MODE>
 static cudaError_t launch_mode(const SmallParams& p, cudaStream_t st) {
-  static bool attr_set = false;
+  static lg::DeviceOnce attr;
   const size_t smem = sizeof(BlockSmem);
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_logm_small<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  cudaError_t e = cudaMemsetAsync(p.queue, 0, sizeof(int32_t), st);
+  cudaError_t e = attr.run([&] {
+    return cudaFuncSetAttribute(k_logm_small<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(p.queue, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   if (MODE == kModeExecute && p.order && p.order_aux && p.count > 1) {
     e = cudaMemsetAsync(p.order_aux, 0, sizeof(int32_t) * 2 * kOrderBuckets, st);
     if (e != cudaSuccess) return e;
-    const int kb = p.count < 4 * sm_count() ? p.count : 4 * sm_count();
+    const int kb = p.count < 4 * lg::device_sm_count() ? p.count : 4 * lg::device_sm_count();
     k_order_keys<<<kb, kThreads, 0, st>>>(p);
     k_order_scan<<<1, 32, 0, st>>>(p);
     k_order_scatter<<<(p.count + kThreads - 1) / kThreads, kThreads, 0, st>>>(p);

@@ -14,7 +14,9 @@ are not available, so these seeded families stand in for them:
                          entries of standard deviation ``offdiag_std``
                          (0.1 literally, 0.1/n for the well-conditioned variant).
 * ``spd``             -- A = Q diag(lam) Q^T with lam log-uniform in a range.
-* ``ragged_spd``      -- many SPD matrices with n drawn from a size set.
+* ``ragged_spd``      -- many SPD matrices with n drawn from a size set
+                         (``ragged_spd_device``: the same recipe drawn on a
+                         torch device).
 """
 from __future__ import annotations
 
@@ -89,6 +91,39 @@ def ragged_spd(count: int, sizes=(4, 8, 16, 32, 64, 128, 256), seed: int = 4,
         for j, b in enumerate(idx):
             out[offs[b]:offs[b] + n * n] = mats[j].ravel()
     return out, ns, offs
+
+
+def ragged_spd_device(count: int, device, sizes=(4, 8, 16, 32, 64, 128, 256), seed: int = 4,
+                      lo: float = 1e-3, hi: float = 1e3):
+    """The ``ragged_spd`` recipe drawn on a torch device (for the 20,000-matrix
+    batch, whose host generation takes half a minute): n per matrix from
+    ``ragged_sizes``, A = Q diag(lam) Q^T with Q from the QR of a seeded
+    Gaussian matrix and lam log-uniform in [lo, hi], FP32 storage. Returns
+    (packed values, n per matrix, element offsets) as device tensors. The
+    matrices differ from ``ragged_spd``'s (another generator), the recipe is
+    the same."""
+    import torch
+    ns = ragged_sizes(count, sizes, seed)
+    offs = np.zeros(count, dtype=np.int64)
+    offs[1:] = np.cumsum(ns.astype(np.int64) ** 2)[:-1]
+    total = int((ns.astype(np.int64) ** 2).sum())
+    out = torch.empty(total, dtype=torch.float32, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed + 1000)
+    offs_d = torch.from_numpy(offs).to(device)
+    for n in np.unique(ns):
+        n = int(n)
+        idx = np.nonzero(ns == n)[0]
+        g = torch.randn((len(idx), n, n), generator=gen, device=device, dtype=torch.float64)
+        q, r = torch.linalg.qr(g)
+        q = q * torch.sign(torch.diagonal(r, dim1=1, dim2=2))[:, None, :]
+        u = torch.rand((len(idx), n), generator=gen, device=device, dtype=torch.float64)
+        lam = torch.exp(np.log(lo) + (np.log(hi) - np.log(lo)) * u)
+        a = (q * lam[:, None, :]) @ q.transpose(1, 2)
+        a = (0.5 * (a + a.transpose(1, 2))).to(torch.float32).reshape(len(idx), n * n)
+        pos = offs_d[torch.from_numpy(idx).to(device)][:, None] + torch.arange(n * n, device=device)[None, :]
+        out[pos.reshape(-1)] = a.reshape(-1)
+    return out, torch.from_numpy(ns).to(device), offs_d
 
 
 def gaussian(shape, seed: int = 5) -> np.ndarray:

@@ -3,16 +3,19 @@ launch for the FP64 stage, one tensor-core launch per graph product), FP32
 storage, split-precision products, checked against the FP64 oracle; and the
 whole call captured once in a CUDA graph and replayed.
 
-Tolerance 1e-5 relative: FP32 storage of A and L (6e-8), TF32x3 products and
-FP32 lin-combs (about 1e-7 per product), amplified by the conditioning of the
-logarithm for SPD inputs with eigenvalues in [1e-3, 1e3].
+Tolerance against the oracle ``SPLIT_TOL_F32`` (tests/parity.py): the split
+products' bound plus the FP32 rounding of the stored L. The oracle runs on the
+same FP32 values of A (read as FP64), so the storage of A adds nothing. The
+property checks (symmetry, trace = log det) keep 1e-5: they compare FP32
+results with FP64 quantities of matrices whose eigenvalues span [1e-3, 1e3].
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_2401_10089_gb300 import workloads
-from tests.test_gpu_parity import lg, rel
+from tests.parity import SPLIT_TOL_F32
+from tests.test_gpu_parity import check_logm, lg, rel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -40,7 +43,7 @@ def test_ragged_spd_fp32_storage(precision):
             A = vals[offs[b]:offs[b] + n * n].reshape(n, n).astype(np.float64)
             Lr, d = oracle.logm(A)
             Lg = out[offs[b]:offs[b] + n * n].reshape(n, n).astype(np.float64)
-            assert rel(Lg, Lr) <= 1e-5, (precision, n, b, rel(Lg, Lr))
+            assert rel(Lg, Lr) <= SPLIT_TOL_F32, (precision, n, b, rel(Lg, Lr))
 
 
 def test_execute_captured_in_cuda_graph():
@@ -85,9 +88,7 @@ def test_kernel_configurations_agree_with_oracle(variant):
     for b in range(len(ns)):
         n = int(ns[b])
         A = vals[offs[b]:offs[b] + n * n].reshape(n, n)
-        Lr, d = oracle.logm(A)
-        if (d["s"], d["k"]) == (int(s[b]), int(k[b])):
-            assert rel(out[offs[b]:offs[b] + n * n].reshape(n, n), Lr) <= 1e-12, (variant, n)
+        check_logm(A, out[offs[b]:offs[b] + n * n].reshape(n, n), int(s[b]), int(k[b]), int(info[b]))
 
 
 def test_autotuner_picks_a_valid_table():
@@ -130,4 +131,4 @@ def test_full_size_batching_configuration():
         assert (np.abs(tr - logdet) <= 1e-5 * (np.abs(logdet) + n * nrm / np.sqrt(n))).all(), n
         for j in np.random.default_rng(44 + n).choice(len(idx), 2, replace=False):
             Lr, d = oracle.logm(A[j])
-            assert rel(Lg[j], Lr) <= 1e-5, (n, int(idx[j]), rel(Lg[j], Lr))
+            assert rel(Lg[j], Lr) <= SPLIT_TOL_F32, (n, int(idx[j]), rel(Lg[j], Lr))

@@ -5,7 +5,7 @@ whole-GPU kernel, and the allocation-free entry point with k_max = 3 and the
 product form.
 
 Tolerances as in the single-option tests: 1e-12 relative for FP64 results
-(1e-11 with k_max = 3), 5e-6 for split precision, compared in the balanced
+(1e-11 with k_max = 3), SPLIT_TOL (tests/parity.py) for split precision, compared in the balanced
 frame where balancing is on.
 """
 import ctypes
@@ -15,6 +15,8 @@ import pytest
 
 import oracle
 from paper_2401_10089_gb300 import workloads
+from tests.parity import SPLIT_TOL
+from tests.parity import oracle_at_plan
 from tests.test_gpu_parity import check_logm, dev, lg, rel
 
 torch = pytest.importorskip("torch")
@@ -47,7 +49,7 @@ def test_ragged_mixed_kernels_split_precision(precision):
     for b, n in enumerate(sizes):
         assert int(info[b]) == 0
         Lr, d = oracle.logm(mats[b])
-        assert rel(out[offs[b]:offs[b] + n * n].reshape(n, n), Lr) <= 5e-6, (n, precision)
+        assert rel(out[offs[b]:offs[b] + n * n].reshape(n, n), Lr) <= SPLIT_TOL, (n, precision)
 
 
 def test_ragged_mixed_kernels_balanced():
@@ -56,8 +58,7 @@ def test_ragged_mixed_kernels_balanced():
     L, s, k, info = lg().logm_execute(R, balance=True)
     out = L.values.cpu().numpy()
     for b, n in enumerate(sizes):
-        Lr, d = oracle.logm(mats[b], balance=1)
-        assert int(info[b]) == d["info"] == 0
+        Lr = oracle_at_plan(mats[b], int(s[b]), int(k[b]), int(info[b]), balance=1)
         _, dv = oracle.balance(mats[b])
         Lg = out[offs[b]:offs[b] + n * n].reshape(n, n)
         assert rel(Lg / dv[:, None] * dv[None, :], Lr / dv[:, None] * dv[None, :]) <= 1e-12, n
@@ -113,10 +114,7 @@ def test_k3_balanced_whole_gpu():
     D = 2.0 ** np.random.default_rng(641).integers(-8, 9, n)
     A = A0 * D[:, None] / D[None, :]
     L, s, k, info = lg().logm_execute(dev(A[None]), balance=True)
-    Lr, d = oracle.logm(A, balance=1)
-    assert int(info[0]) == d["info"] == 0
-    if (int(s[0]), int(k[0])) != (d["s"], d["k"]):  # a decision at a threshold: compare at the GPU's plan
-        Lr, d = oracle.logm(A, balance=1, force_s=int(s[0]), force_k=int(k[0]))
+    Lr = oracle_at_plan(A, int(s[0]), int(k[0]), int(info[0]), balance=1)
     _, dv = oracle.balance(A)
     Lg = L[0].cpu().numpy()
     assert rel(Lg / dv[:, None] * dv[None, :], Lr / dv[:, None] * dv[None, :]) <= 1e-12

@@ -617,3 +617,30 @@ def test_sqrt_with_known_inverse():
     # and the previous root's Y is that inverse: sqrt(sqrt(A)) via the chain
     L0, d0 = oracle.logm(A)
     assert d0["s"] >= 2 and rel(L0, sla.logm(A).real) < 1e-12
+
+
+def test_as_written_and_root_of_root_agree_and_count_inversions():
+    # Algorithm 1 runs eq. (ScalDB) as written (X_0 = A, Y_0 = I at every
+    # level; Y_0 = I needs no inversion) unless reuse_root=1, where later
+    # levels take the previous level's Y as A^{-1}: the same plan, results
+    # within rounding, one inversion fewer per level after the first
+    for seed, n in ((57, 24), (58, 60)):
+        A = workloads.identity_plus(1, n, seed=seed, lo=3.0, hi=4.0)[0]
+        L0, d0 = oracle.logm(A)
+        L1, d1 = oracle.logm(A, reuse_root=1)
+        assert d0["s"] >= 2 and (d0["s"], d0["k"]) == (d1["s"], d1["k"])
+        assert rel(L1, L0) < 1e-13
+        assert d0["n_inv"] == 2 * d0["db_iters"] - d0["s"]
+        assert d1["n_inv"] == 2 * d1["db_iters"] - d1["s"] - (d1["s"] - 1)
+        assert rel(L0, sla.logm(A).real) < 1e-12
+
+
+def test_plan_margin_is_the_distance_to_the_deciding_threshold():
+    # diagonal A: ||A - I||_1 = max |lambda - 1| exactly. With it at Theta_5
+    # (1 - 1e-9) the first comparison finishes at s = 0 at relative distance
+    # 1e-9; at half of Theta_5 the closest comparison is far away
+    theta = oracle.THETA_TABLE[4]
+    L, d = oracle.logm(np.diag([1.0 + theta * (1.0 - 1e-9), 1.0, 1.0 - 0.1 * theta]))
+    assert d["s"] == 0 and d["margin_s"] == 0 and abs(d["margin"] - 1e-9) < 1e-12, d
+    L, d = oracle.logm(np.diag([1.0 + 0.5 * theta, 1.0]))
+    assert d["s"] == 0 and d["margin"] > 0.1, d

@@ -37,3 +37,21 @@ def test_fp32_device_tables_are_the_rounded_values():
     assert np.array_equal(f32(table("scheme_f32.cuh", "c_tc_g5")), f32(g))
     assert np.array_equal(f32(table("scheme_f32.cuh", "c_tc_y5")), f32(y))
     assert np.array_equal(f32(table("scheme_f32.cuh", "c_tc_k4")), f32(oracle.coeffs_k4()))
+
+
+def test_theta_table_of_the_library():
+    """The library's default Theta_{m_k} (one table, logm_internal.h, used by
+    every entry point) against the paper's backward-error table (golden) and
+    the oracle's copy."""
+    src = open(os.path.join(CSRC, "logm_internal.h")).read()
+    m = re.search(r"constexpr\s+double\s+kThetaPaper\[5\]\s*=\s*\{([^}]*)\}", src)
+    assert m
+    dev = np.array([float(t) for t in re.findall(r"[-+]?\d+\.\d*(?:e[-+]?\d+)?", m.group(1))])
+    gold = np.array([float(line.split()[3]) for line in open(os.path.join(GOLDEN, "theta_table.txt"))
+                     if line.strip() and not line.startswith("#")])
+    assert np.array_equal(dev, gold)
+    assert np.array_equal(np.array(oracle.THETA_TABLE), gold)
+    # no second copy of the table elsewhere in the library's sources
+    for f in os.listdir(CSRC):
+        if f != "logm_internal.h":
+            assert "2.46e-1}" not in open(os.path.join(CSRC, f)).read(), f
