@@ -90,6 +90,16 @@ typedef struct logm_batch {
                                  1-norms of the off-diagonal parts of rows and columns);
                                  A <- T^{-1} A T before, L <- T L T^{-1} after, both exact */
 
+/* How the whole-GPU kernel (n > 256) forms the FP64 products of its
+ * Gauss-Jordan inversions (logm_options.fp64_products). Not in the paper:
+ * an implementation choice for the left divisions of Sec. 6, eq. (ScalDB). */
+#define LOGM_FP64_PIPE 0      /* FP64 FMAs (DMMA tiles) */
+#define LOGM_FP64_TC_SLICED 1 /* each operand split into eight exact BF16 digits (per-row and
+                                 per-column powers of two), digit products accumulated exactly
+                                 in FP32 on the tensor cores (tcgen05), the exact integer dot
+                                 product rounded to FP64 once; the rank-32 updates of the
+                                 inversions run this way, everything else as with PIPE */
+
 typedef struct logm_options {
   int32_t k_max;          /* largest number of graph products, 1..5 (Table Table_theta;
                              k = 3 is T_8 by eq. eqP8pol, k = 4 the 14+ scheme of Sec. 3
@@ -100,6 +110,9 @@ typedef struct logm_options {
   int32_t max_db_iter;    /* cap on Denman-Beavers iterations per root (default 50) */
   int32_t db_form;        /* LOGM_DB_* (default LOGM_DB_TWO_INVERSE) */
   int32_t balance;        /* LOGM_BALANCE_*, logm_execute / logm_backward only (default NONE) */
+  int32_t fp64_products;  /* LOGM_FP64_*, the whole-GPU kernel's inversions (logm_execute,
+                             logm_sqrt; default LOGM_FP64_PIPE) */
+  int32_t reserved;       /* 0 */
   double theta[5];        /* Theta_{m_k} for k = 1..5; 0 selects
                              the paper's 1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1
                              (Table Table_theta) */

@@ -34,6 +34,7 @@ class LogmBatch(ctypes.Structure):
 class LogmOptions(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_sqrt", ctypes.c_int32),
                 ("max_db_iter", ctypes.c_int32), ("db_form", ctypes.c_int32), ("balance", ctypes.c_int32),
+                ("fp64_products", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("theta", ctypes.c_double * 5)]
 
 

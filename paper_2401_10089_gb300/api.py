@@ -78,18 +78,22 @@ def _values(A):
 
 
 _DB_FORM = {"two_inverse": 0, "product": 1}
+_FP64_PRODUCTS = {"pipe": 0, "tc_sliced": 1}
 
 
 def _options(k_max=5, precision="fp64", max_sqrt=40, max_db_iter=50, theta=None, db_form="two_inverse",
-             balance=False) -> _lib.LogmOptions:
+             balance=False, fp64_products="pipe") -> _lib.LogmOptions:
     """k_max in 1..5; db_form "two_inverse" (eq. ScalDB) or "product";
     balance: diagonal balancing of Algorithm 1, Step 1; theta: Theta_{m_k} for
-    k = 1..5 (0 = the paper's Table Table_theta)."""
+    k = 1..5 (0 = the paper's Table Table_theta); fp64_products: "pipe" (FP64
+    FMAs) or "tc_sliced" (the whole-GPU kernel's inversion updates from exact
+    BF16 digit products on the tensor cores)."""
     o = _lib.LogmOptions()
     o.k_max, o.max_sqrt, o.max_db_iter = k_max, max_sqrt, max_db_iter
     o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
     o.db_form = _DB_FORM[db_form] if isinstance(db_form, str) else int(db_form)
     o.balance = 1 if balance else 0
+    o.fp64_products = _FP64_PRODUCTS[fp64_products] if isinstance(fp64_products, str) else int(fp64_products)
     th = (0.0,) * 5 if theta is None else theta
     for t in range(5):
         o.theta[t] = th[t]

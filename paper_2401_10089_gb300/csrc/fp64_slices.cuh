@@ -1,0 +1,155 @@
+// fp64_slices.cuh -- FP64 products from exact BF16 digit products.
+//
+// A product C = U V of FP64 matrices (K <= kSliceK terms per entry) is formed
+// from small integers so that the BF16 tensor cores compute it exactly:
+//
+//  * every row u of U (every column v of V) is scaled by its own power of two
+//    2^-e, e the smallest integer with max_k |u_k| < 2^e, and rounded to a
+//    fixed-point integer X_k = round(u_k 2^(F - e)), F = 7 + 8 (kSlices - 1);
+//  * X_k is written in balanced base 256 with kSlices digits,
+//    X_k = sum_i d_i 256^(kSlices - i), d_1 in [-128, 128], the others in
+//    [-128, 127]: each digit is exact in BF16 (8 significant bits);
+//  * digit products d_i e_j are at most 2^14 in magnitude, so for a level
+//    L = i + j the sum over the pairs of that level and over K = 32 terms,
+//    C_L = sum_{i + j = L} sum_k d_i[k] e_j[k], is an integer of magnitude
+//    <= 8 * 32 * 2^14 = 2^22: FP32 accumulation on the tensor cores is exact;
+//  * u.v = 2^(e_u + e_v - 14 - 8 (kSlices - 1)) * T with the integer
+//    T = sum_{L = 2}^{kSlices + 1} C_L 256^(kSlices + 1 - L) (pairs with
+//    i + j > kSlices + 1 weigh less than 2^-76 of the row/column scale and are
+//    dropped). T is combined from the FP32 levels with integer arithmetic and
+//    converted to FP64 with two roundings.
+//
+// The split error is at most 2^-(F+1) of the row or column scale per operand
+// (2^-64 for kSlices = 8), below FP64's own rounding of the result. The
+// helpers are __host__ __device__ so that the CPU tests exercise the same code.
+#pragma once
+
+#include <cstdint>
+#include <cmath>
+#include <cstring>
+
+#ifdef __CUDACC__
+#define LG_HD __host__ __device__ __forceinline__
+#else
+#define LG_HD inline
+#endif
+
+namespace lg {
+
+constexpr int kSlices = 8;                     // digits per operand
+constexpr int kSliceK = 32;                    // K of one exact accumulation (the panel width)
+constexpr int kSliceLevels = kSlices;          // levels L = 2 .. kSlices + 1
+constexpr int kSliceFrac = 7 + 8 * (kSlices - 1);  // F: fractional bits of the fixed-point form
+constexpr int kSliceScale = 14 + 8 * (kSlices - 1);  // u.v = 2^(e_u + e_v - kSliceScale) T
+constexpr int32_t kSliceNonFinite = -0x40000000;   // exponent marker of a row/column with Inf or NaN
+
+LG_HD uint64_t lg_dbits(double x) {
+  uint64_t b;
+  memcpy(&b, &x, 8);
+  return b;
+}
+LG_HD double lg_bitsd(uint64_t b) {
+  double x;
+  memcpy(&x, &b, 8);
+  return x;
+}
+LG_HD uint32_t lg_fbits(float x) {
+  uint32_t b;
+  memcpy(&b, &x, 4);
+  return b;
+}
+
+// 2^e as a double for e in [-1022, 1023] (exact).
+LG_HD double lg_pow2(int e) { return lg_bitsd(static_cast<uint64_t>(e + 1023) << 52); }
+
+// Scale exponent of a row or column: the smallest e with max|u_k| < 2^e for
+// the finite maximum m > 0; 0 when m == 0; kSliceNonFinite for Inf or NaN.
+LG_HD int32_t slice_exponent(double m) {
+  if (!(m <= 1.79769313486231570815e308)) return kSliceNonFinite;  // Inf or NaN
+  if (m == 0.0) return 0;
+  const uint64_t b = lg_dbits(m);
+  const int be = static_cast<int>((b >> 52) & 0x7FF);
+  if (be != 0) return be - 1023 + 1;  // m in [2^(be-1023), 2^(be-1022))
+  // subnormal: m = frac * 2^-1074, frac < 2^52
+  const uint64_t frac = b & ((1ull << 52) - 1);
+  int top = 63;
+  while (!((frac >> top) & 1ull)) --top;
+  return -1074 + top + 1;
+}
+
+// Fixed-point integer round(u 2^(kSliceFrac - e)), |result| < 2^63 for |u| < 2^e.
+LG_HD int64_t slice_fixed(double u, int32_t e) {
+  // u 2^(F - e) computed as (u 2^-e) 2^F: exact scalings by powers of two, in
+  // two steps so that neither factor over- or underflows for e in the double range
+  const int sh = kSliceFrac - e;  // may be up to about 63 + 1074
+  double y = u;
+  int rest = sh;
+  while (rest > 1000) {
+    y *= lg_pow2(1000);
+    rest -= 1000;
+  }
+  while (rest < -1000) {
+    y *= lg_pow2(-1000);
+    rest += 1000;
+  }
+  y *= lg_pow2(rest);
+#ifdef __CUDA_ARCH__
+  return __double2ll_rn(y);
+#else
+  return static_cast<int64_t>(std::nearbyint(y));
+#endif
+}
+
+// Balanced base-256 digits of X, most significant first: d[0] in [-128, 128],
+// d[1..] in [-128, 127], X = sum d[i] 256^(kSlices - 1 - i).
+LG_HD void slice_digits(int64_t X, int32_t* d) {
+  for (int i = kSlices - 1; i >= 1; --i) {
+    const int32_t di = static_cast<int32_t>((X + 128) & 255) - 128;
+    d[i] = di;
+    X = (X - di) / 256;  // exact: X - di is a multiple of 256
+  }
+  d[0] = static_cast<int32_t>(X);
+}
+
+// Integer value of an FP32 level sum (an exact integer, |v| <= 2^22).
+LG_HD int32_t level_int(float v) {
+  return static_cast<int32_t>(lg_fbits(v + 12582912.0f)) - 0x4B400000;
+}
+
+// Exact integer T = sum_L C_L 256^(kSlices + 1 - L) as two halves,
+// T = hi 2^32 + lo, from the kSlices level sums c[0] (L = 2) .. c[kSlices-1].
+LG_HD void level_halves(const int32_t* c, int64_t* hi, int64_t* lo) {
+  static_assert(kSlices == 8, "two halves of four levels each");
+  *hi = ((static_cast<int64_t>(c[0]) * 256 + c[1]) * 256 + c[2]) * 256 + c[3];
+  *lo = ((static_cast<int64_t>(c[4]) * 256 + c[5]) * 256 + c[6]) * 256 + c[7];
+}
+
+// Exact FP64 value of an integer with |x| < 2^51.
+LG_HD double small_int_to_double(int64_t x) {
+  return lg_bitsd(static_cast<uint64_t>(x + 0x4338000000000000ll)) - 6755399441055744.0;
+}
+
+// u.v from the levels and the two scale exponents (both finite markers):
+// T rounded to FP64 once, then scaled exactly (unless it under- or overflows).
+LG_HD double combine_levels(const int32_t* c, int32_t eu, int32_t ev) {
+  if (eu == kSliceNonFinite || ev == kSliceNonFinite) return lg_bitsd(0x7FF8000000000000ull);  // NaN
+  int64_t hi, lo;
+  level_halves(c, &hi, &lo);
+  const double t = fma(small_int_to_double(hi), 4294967296.0, small_int_to_double(lo));
+  const int E = eu + ev - kSliceScale;
+  if (E >= -1022 && E <= 1023) return t * lg_pow2(E);
+  return ldexp(t, E);  // rare: the scale itself is outside the normal range
+}
+
+// w + u.v with the same two roundings (T to FP64, then the sum: one FMA).
+LG_HD double combine_levels_add(const int32_t* c, int32_t eu, int32_t ev, double w) {
+  if (eu == kSliceNonFinite || ev == kSliceNonFinite) return lg_bitsd(0x7FF8000000000000ull);  // NaN
+  int64_t hi, lo;
+  level_halves(c, &hi, &lo);
+  const double t = fma(small_int_to_double(hi), 4294967296.0, small_int_to_double(lo));
+  const int E = eu + ev - kSliceScale;
+  if (E >= -1022 && E <= 1023) return fma(t, lg_pow2(E), w);
+  return w + ldexp(t, E);
+}
+
+}  // namespace lg

@@ -29,6 +29,7 @@
 #include "../../include/logm.h"
 #include "logm_internal.h"
 #include "scheme_f32.cuh"
+#include "tc_ptx.cuh"
 
 namespace lg {
 
@@ -36,7 +37,6 @@ namespace {
 
 constexpr int kTmM = 128;  // tile rows = TMEM lanes
 constexpr int kTmThreads = 128;
-constexpr long long kTmWaitLimit = 1ll << 24;
 
 template <int PREC>
 struct TmCfg;
@@ -70,89 +70,12 @@ static __device__ __forceinline__ bool tm_skip(const GraphParams& p, int b) {
   return p.info_dev && (p.info_dev[b] == 1 || p.info_dev[b] == 4);
 }
 
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-static __device__ __forceinline__ uint32_t su32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory matrix descriptor for a K-major operand in the 128-byte
-// swizzle layout: start address, leading byte offset (unused for this
-// layout: 16 B), stride byte offset 1024 B (8 rows of 128 B), descriptor
-// version 1, layout type 2 (128-byte swizzle).
-static __device__ __forceinline__ uint64_t tm_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
-  d |= static_cast<uint64_t>(1) << 16;
-  d |= static_cast<uint64_t>(1024 >> 4) << 32;
-  d |= static_cast<uint64_t>(1) << 46;
-  d |= static_cast<uint64_t>(2) << 61;
-  return d;
-}
-
-// Instruction descriptor: FP32 accumulator, A and B of format fmt, both K-major.
-static __device__ __forceinline__ uint32_t tm_idesc(uint32_t fmt, int M, int N) {
-  uint32_t d = 0;
-  d |= 1u << 4;
-  d |= fmt << 7;
-  d |= fmt << 10;
-  d |= static_cast<uint32_t>(N >> 3) << 17;
-  d |= static_cast<uint32_t>(M >> 4) << 24;
-  return d;
-}
-
 template <int PREC>
 static __device__ __forceinline__ void tm_mma(uint32_t dt, uint64_t a, uint64_t b, uint32_t id, int acc) {
   if (PREC == LOGM_PREC_TF32X3)
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-        "l"(a), "l"(b), "r"(id), "r"(acc));
+    tm_mma_tf32(dt, a, b, id, acc);
   else
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-        "l"(a), "l"(b), "r"(id), "r"(acc));
-}
-
-static __device__ __forceinline__ void tm_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-static __device__ __forceinline__ bool tm_wait(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < kTmWaitLimit; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-static __device__ __forceinline__ void tm_expect(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-
-static __device__ __forceinline__ void tm_load3d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int x, int y,
-                                                 int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-      "[%2];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-
-static __device__ __forceinline__ void tm_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-static __device__ __forceinline__ void tm_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tm_mma_f16(dt, a, b, id, acc);
 }
 
 static __device__ __forceinline__ uint32_t tm_tf32(float x) {
@@ -286,7 +209,7 @@ __global__ void __launch_bounds__(kTmThreads, 1)
 
   const uint32_t full0 = su32(&bars[0]), empty0 = su32(&bars[2]), accum = su32(&bars[4]);
   if (tid == 0) {
-    for (int t = 0; t < 5; ++t) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&bars[t])), "r"(1));
+    for (int t = 0; t < 5; ++t) tm_bar_init(su32(&bars[t]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {

@@ -18,6 +18,7 @@
 #include <cstdint>
 
 #include "cta_linalg.cuh"
+#include "tc_update.cuh"
 
 namespace lg {
 
@@ -42,6 +43,8 @@ struct GjGroup {
   int* perm;         // [n_max] composite column permutation
   double* work;      // [n_max^2] working matrix
   double* result;    // [2] log|det|, status
+  SliceBufs sl;      // tensor-core updates: digits of the panel's factors
+  int gi;            // index of this group (its tensor maps)
 };
 
 struct GridWs {
@@ -66,6 +69,8 @@ struct GridSmem {
   int work[4];
   unsigned long long ep[3];  // barrier episodes seen: whole grid, group 0, group 1
   int winner;                // block holding the pivot candidate of the current column
+  SliceSmem slc;             // tensor-core updates: barriers, phases, TMEM base
+  int skip_upd;              // the grid's error word was set: no more tensor-core work
 };
 
 // Dynamic shared memory of the whole-GPU kernel: this block's rows of the
@@ -121,6 +126,7 @@ struct GridOps {
   GridWs& w;
   GridSmem& S;
   int rbuf;  // alternating partial buffer of the generic reductions
+  const SliceMaps* maps;  // non-null: the Gauss-Jordan updates run on the tensor cores (tc_update.cuh)
 
   __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
   __device__ int nthreads() const { return gridDim.x * blockDim.x; }
@@ -540,6 +546,16 @@ struct GridOps {
         W[(int64_t)r * n + kb + c] = v;
         Pf[(int64_t)c * n + r] = v;
       }
+      if (maps) {
+        // digits of the update's left factor U = P_f - I_J, one row per thread
+        for (int rr = threadIdx.x; rr < my_rows; rr += kThreads) {
+          const int r = r_lo + rr;
+          double u[kSliceK];
+          for (int c = 0; c < kSliceK; ++c)
+            u[c] = c < jb ? Sf[rr * kGridPanel + c] - (r == kb + c ? 1.0 : 0.0) : 0.0;
+          slice_store(u, jb, g.sl.adig + (int64_t)r * kDigK, g.sl.aexp + r);
+        }
+      }
       for (int j = gt; j < n; j += gnt) {
         if (j >= kb && j < kb + jb) continue;
         for (int c = 0; c < jb; ++c) {
@@ -550,12 +566,30 @@ struct GridOps {
             W[(int64_t)p * n + j] = t0;
           }
         }
-        for (int c = 0; c < jb; ++c) g.R[(int64_t)c * n + j] = W[(int64_t)(kb + c) * n + j];
+        if (maps) {  // the right factor V = R, column j: its digits
+          double v[kSliceK];
+          for (int c = 0; c < kSliceK; ++c) v[c] = c < jb ? W[(int64_t)(kb + c) * n + j] : 0.0;
+          slice_store(v, jb, g.sl.bdig + (int64_t)j * kDigK, g.sl.bexp + j);
+        } else {
+          for (int c = 0; c < jb; ++c) g.R[(int64_t)c * n + j] = W[(int64_t)(kb + c) * n + j];
+        }
       }
+      if (maps) fence_proxy_async_global();  // the digits are read by TMA after the barrier
       bounded_barrier(bar, gn, w.err, ep);
-      const int tiles = (n + kTileM - 1) / kTileM;
-      for (int t = lb; t < tiles * tiles; t += G)
-        rank_update_tile(W, n, kb, jb, Pf, g.R, (t / tiles) * kTileM, (t % tiles) * kTileN);
+      if (maps) {
+        if (threadIdx.x == 0) S.skip_upd = *(volatile int*)w.err;
+        __syncthreads();
+        if (!S.skip_upd) {
+          const int T = ((n + kUpdM - 1) / kUpdM) * ((n + kUpdN - 1) / kUpdN);
+          const int t_lo = (int)((int64_t)lb * T / G), t_hi = (int)((int64_t)(lb + 1) * T / G);
+          sliced_update(S.slc, reinterpret_cast<unsigned char*>(grid_panel_smem), &maps->a[g.gi], &maps->b[g.gi],
+                        g.sl, W, n, kb, jb, t_lo, t_hi, w.err);
+        }
+      } else {
+        const int tiles = (n + kTileM - 1) / kTileM;
+        for (int t = lb; t < tiles * tiles; t += G)
+          rank_update_tile(W, n, kb, jb, Pf, g.R, (t / tiles) * kTileM, (t % tiles) * kTileN);
+      }
       bounded_barrier(bar, gn, w.err, ep);
     }
     if (!status) {

@@ -63,6 +63,7 @@ int opts_ok(const logm_options* o) {
   if (o->max_db_iter < 1 || o->max_db_iter > 1000) return 0;
   if (o->db_form != LOGM_DB_TWO_INVERSE && o->db_form != LOGM_DB_PRODUCT) return 0;
   if (o->balance != LOGM_BALANCE_NONE && o->balance != LOGM_BALANCE_SCALE) return 0;
+  if (o->fp64_products != LOGM_FP64_PIPE && o->fp64_products != LOGM_FP64_TC_SLICED) return 0;
   for (int t = 0; t < 5; ++t)
     if (!(o->theta[t] >= 0.0) || !(o->theta[t] < 1.0)) return 0;
   return 1;
@@ -149,6 +150,7 @@ void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o)
     p.precision = o->precision;
     p.db_form = o->db_form;
     p.balance = o->balance;
+    p.fp64_tc = o->fp64_products == LOGM_FP64_TC_SLICED;
   } else {
     p.k_max = 5;
     p.max_sqrt = 40;

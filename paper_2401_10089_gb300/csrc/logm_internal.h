@@ -84,6 +84,7 @@ struct SmallParams {
   int32_t* order_aux;  // [2 * kOrderBuckets + count]: bucket counts, bucket cursors, bucket per matrix
   int n_slots;
   int precision;       // graph products (FP64 in this kernel family)
+  int fp64_tc;         // whole-GPU kernel: 1 = Gauss-Jordan updates on the tensor cores (exact BF16 digits)
   int large_pass;      // 1: matrices with n > kSmallMaxN are left to the whole-GPU kernel
   int bucket_mask;     // nonzero: only matrices whose size bucket bit is set (see size_bucket)
   float* gbuf;         // precision form: hand P_2, P_3 over in FP32 here and stop before the graph

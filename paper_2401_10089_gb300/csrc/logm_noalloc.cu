@@ -67,6 +67,7 @@ extern "C" int logm_execute_noalloc(const logm_batch* batch, const logm_options*
   if (opts->max_db_iter < 1 || opts->max_db_iter > 1000) return LOGM_ERR_INVALID_ARG;
   if (opts->db_form != LOGM_DB_TWO_INVERSE && opts->db_form != LOGM_DB_PRODUCT) return LOGM_ERR_INVALID_ARG;
   if (opts->balance != LOGM_BALANCE_NONE && opts->balance != LOGM_BALANCE_SCALE) return LOGM_ERR_INVALID_ARG;
+  if (opts->fp64_products != LOGM_FP64_PIPE && opts->fp64_products != LOGM_FP64_TC_SLICED) return LOGM_ERR_INVALID_ARG;
   for (int t = 0; t < 5; ++t)
     if (!(opts->theta[t] >= 0.0) || !(opts->theta[t] < 1.0)) return LOGM_ERR_INVALID_ARG;
   if (opts->precision != LOGM_PREC_FP64) return LOGM_ERR_UNSUPPORTED;

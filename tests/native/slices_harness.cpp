@@ -1,0 +1,51 @@
+// CPU harness for the digit split and level combination of the tensor-core
+// FP64 products (paper_2401_10089_gb300/csrc/fp64_slices.cuh): the same
+// __host__ __device__ code, compiled for the host by the CPU tests.
+#include "../../paper_2401_10089_gb300/csrc/fp64_slices.cuh"
+
+extern "C" {
+
+// Row split: e and kSlices digits for each of k values (digits[i * k + t]).
+int32_t h_split(const double* u, int k, int32_t* digits) {
+  double m = 0.0;
+  for (int t = 0; t < k; ++t) {
+    const double a = std::fabs(u[t]);
+    if (!(a <= m)) m = a;
+  }
+  const int32_t e = lg::slice_exponent(m);
+  for (int t = 0; t < k; ++t) {
+    int32_t d[lg::kSlices];
+    if (e == lg::kSliceNonFinite) {
+      for (int i = 0; i < lg::kSlices; ++i) d[i] = 0;
+    } else {
+      lg::slice_digits(lg::slice_fixed(u[t], e), d);
+    }
+    for (int i = 0; i < lg::kSlices; ++i) digits[i * k + t] = d[i];
+  }
+  return e;
+}
+
+// u.v as the tensor-core path forms it: digit products summed per level in
+// exact integers (what the FP32 accumulators hold), passed through the FP32
+// representation, combined.
+double h_sliced_dot(const double* u, const double* v, int k) {
+  int32_t du[lg::kSlices * lg::kSliceK], dv[lg::kSlices * lg::kSliceK];
+  const int32_t eu = h_split(u, k, du), ev = h_split(v, k, dv);
+  int32_t c[lg::kSliceLevels];
+  for (int L = 2; L <= lg::kSlices + 1; ++L) {
+    int64_t acc = 0;
+    for (int i = 1; i < L; ++i) {
+      const int j = L - i;
+      if (i > lg::kSlices || j > lg::kSlices) continue;
+      for (int t = 0; t < k; ++t) acc += (int64_t)du[(i - 1) * k + t] * dv[(j - 1) * k + t];
+    }
+    const float f = static_cast<float>(acc);  // exact while |acc| <= 2^24
+    c[L - 2] = lg::level_int(f);
+  }
+  return lg::combine_levels(c, eu, ev);
+}
+
+int32_t h_level_int(float v) { return lg::level_int(v); }
+double h_small_int_to_double(int64_t x) { return lg::small_int_to_double(x); }
+int32_t h_slice_exponent(double m) { return lg::slice_exponent(m); }
+}

@@ -1,0 +1,142 @@
+"""Digit split and level combination of the tensor-core FP64 products, on the
+CPU: the __host__ __device__ helpers of csrc/fp64_slices.cuh compiled for the
+host (g++), against exact rational arithmetic.
+
+What the GPU path relies on:
+  * the digits reconstruct the fixed-point integer exactly and stay within
+    [-128, 128] (exact in BF16; products of two digits <= 2^14);
+  * every level sum over 32 terms fits the FP32 accumulator exactly (<= 2^22);
+  * the combined product is the exact dot product to within one FP64
+    rounding of the result plus the split error, 2 K 2^(e_u + e_v - F)
+    (F = 63 fractional bits), i.e. below FP64's own dot-product error bound
+    K u sum |u_k v_k| whenever the row and column scales are within 2^9 of
+    the magnitudes that meet in the sum.
+"""
+import ctypes
+import os
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "native", "slices_harness.cpp")
+HDR = os.path.join(os.path.dirname(HERE), "paper_2401_10089_gb300", "csrc", "fp64_slices.cuh")
+BUILD = os.path.join(HERE, "native", "_build")
+LIB = os.path.join(BUILD, "libslices.so")
+K = 32
+F = 63
+
+
+@pytest.fixture(scope="module")
+def h():
+    os.makedirs(BUILD, exist_ok=True)
+    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, SRC],
+                       check=True)
+        os.replace(tmp, LIB)
+    L = ctypes.CDLL(LIB)
+    p = ctypes.c_void_p
+    L.h_split.restype = ctypes.c_int32
+    L.h_split.argtypes = [p, ctypes.c_int, p]
+    L.h_sliced_dot.restype = ctypes.c_double
+    L.h_sliced_dot.argtypes = [p, p, ctypes.c_int]
+    L.h_level_int.restype = ctypes.c_int32
+    L.h_level_int.argtypes = [ctypes.c_float]
+    L.h_small_int_to_double.restype = ctypes.c_double
+    L.h_small_int_to_double.argtypes = [ctypes.c_int64]
+    L.h_slice_exponent.restype = ctypes.c_int32
+    L.h_slice_exponent.argtypes = [ctypes.c_double]
+    return L
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def split(h, u):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    d = np.zeros(8 * len(u), dtype=np.int32)
+    e = h.h_split(_ptr(u), len(u), _ptr(d))
+    return e, d.reshape(8, len(u))
+
+
+def rows(rng):
+    yield rng.standard_normal(K)
+    yield rng.standard_normal(K) * np.exp(rng.uniform(-30, 30, K))  # wide dynamic range in one row
+    yield np.concatenate([np.zeros(K - 3), [1e-300, -5e-310, 3e-320]])  # subnormals
+    yield -np.full(K, 1.0 - 2.0 ** -53)  # digits at the edge (-128)
+    yield np.full(K, 2.0 ** 600 * (1 - 2.0 ** -52))
+    yield np.zeros(K)
+    u = rng.standard_normal(K)
+    u[5:] = 0.0  # a short panel (K < 32): zero tail
+    yield u
+
+
+def test_digits_reconstruct_the_fixed_point_integer(h):
+    rng = np.random.default_rng(1)
+    for u in rows(rng):
+        e, d = split(h, u)
+        m = np.max(np.abs(u))
+        if m == 0:
+            assert e == 0 and not d.any()
+            continue
+        assert Fraction(m) < Fraction(2) ** e <= 2 * Fraction(m)  # the smallest e with m < 2^e
+        assert d[0].min() >= -128 and d[0].max() <= 128 and d[1:].min() >= -128 and d[1:].max() <= 127
+        for t in range(K):
+            X = sum(int(d[i, t]) * 256 ** (7 - i) for i in range(8))
+            exact = Fraction(u[t]) * Fraction(2) ** (F - e)
+            assert abs(Fraction(X) - exact) <= Fraction(1, 2)  # X = round(u 2^(F - e))
+
+
+def test_level_sums_fit_fp32_exactly(h):
+    # worst case: every digit at its extreme; level 9 has 8 pairs of 32 terms
+    assert 8 * 32 * 128 * 128 == 2 ** 22
+    for v in list(range(-4096, 4097)) + [2 ** 22, -2 ** 22, 2 ** 22 - 1, -(2 ** 22 - 1), 3 * 2 ** 20 + 7]:
+        assert h.h_level_int(float(v)) == v
+    for x in (0, 1, -1, 2 ** 50 + 12345, -(2 ** 50) - 7, 2 ** 47 - 1):
+        assert h.h_small_int_to_double(x) == float(x)
+
+
+def test_sliced_dot_against_exact(h):
+    rng = np.random.default_rng(2)
+    us = list(rows(rng))
+    vs = list(rows(np.random.default_rng(3)))
+    for u in us:
+        for v in vs:
+            for k in (K, 7):
+                uu, vv = np.ascontiguousarray(u[:k]), np.ascontiguousarray(v[:k])
+                got = h.h_sliced_dot(_ptr(uu), _ptr(vv), k)
+                eu = h.h_slice_exponent(float(np.max(np.abs(uu))))
+                ev = h.h_slice_exponent(float(np.max(np.abs(vv))))
+                exact = sum(Fraction(a) * Fraction(b) for a, b in zip(uu, vv))
+                if abs(exact) > Fraction(np.finfo(np.float64).max):
+                    continue  # beyond the double range
+                # (+ k 2^-1074: products below the double range underflow, in any FP64 dot as well)
+                bound = abs(exact) * Fraction(2) ** -53 + 2 * k * Fraction(2) ** (eu + ev - F) + k * Fraction(2) ** -1074
+                assert abs(Fraction(got) - exact) <= bound, (got, float(exact))
+
+
+def test_sliced_dot_matches_fp64_on_gaussian_data(h):
+    # on data like a Gauss-Jordan update (Gaussian rows and columns) the
+    # sliced product is at least as close to the exact value as an FP64 dot
+    rng = np.random.default_rng(4)
+    worse = 0
+    for _ in range(300):
+        u = rng.standard_normal(K)
+        v = rng.standard_normal(K) * 10.0 ** rng.uniform(-3, 3)
+        got = h.h_sliced_dot(_ptr(u), _ptr(v), K)
+        exact = sum(Fraction(a) * Fraction(b) for a, b in zip(u, v))
+        fp64 = float(np.dot(u, v))
+        worse += abs(Fraction(got) - exact) > abs(Fraction(fp64) - exact)
+    assert worse <= 30  # one correctly rounded result against a sum of 32 rounded products
+
+
+def test_non_finite_rows_propagate(h):
+    u = np.ones(K)
+    u[3] = np.inf
+    v = np.ones(K)
+    assert h.h_slice_exponent(np.inf) == h.h_slice_exponent(np.nan)
+    assert np.isnan(h.h_sliced_dot(_ptr(u), _ptr(v), K))
