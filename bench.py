@@ -171,12 +171,13 @@ def cpu_baseline(A_np, sample: int):
             "seconds": dt}, Ls, ds
 
 
-def arm_config(count, big, big_n, world):
+def arm_config(count, big, big_n, world, fp64_products="pipe"):
     """The `config` of the JSON line: what the arm runs each step."""
     return {"workload": WORKLOAD if (count == COUNT and big and big_n == NBIG) else
             f"{count} x 256x256 A = I + E (||E||_1 ~ U[0.2, 5])" + (f" + one {big_n}^2 Q T Q^T" if big else "")
             + ", seeded, FP64 path",
             "count": count, "n": N, "n_big": big_n if big else None, "precision": "fp64",
+            "fp64_products": fp64_products,
             "l2": "inputs larger than the 129 MB L2; no flush", "parallelism": f"batch-sharded x{world}"}
 
 
@@ -227,6 +228,9 @@ def main():
     ap.add_argument("--count", type=int, default=COUNT, help="matrices per rank (smaller for profiling)")
     ap.add_argument("--no-big", action="store_true", help="leave out the 4096 x 4096 matrix")
     ap.add_argument("--big-n", type=int, default=NBIG, help="size of the large matrix (smaller for profiling)")
+    ap.add_argument("--fp64-products", default="tc_sliced", choices=["tc_sliced", "pipe"],
+                    help="FP64 products of the whole-GPU kernel: exact BF16 digit products on the tensor cores "
+                         "(default) or FP64 FMAs")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -265,9 +269,14 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    # the FP64 path: FP64 products of the whole-GPU kernel (the 4096^2 matrix)
+    # formed exactly from BF16 digit products on the tensor cores; the
+    # 256 x 256 matrices run on the FP64 pipe (one block per matrix)
+    main = {"fp64_products": args.fp64_products}
+
     def step():
-        out = lg.logm_execute(A_dev, stats=stats)
-        outb = lg.logm_execute(B_dev, stats=stats_b) if big else None
+        out = lg.logm_execute(A_dev, stats=stats, **main)
+        outb = lg.logm_execute(B_dev, stats=stats_b, **main) if big else None
         return out, outb
 
     for _ in range(args.warmup):
@@ -282,10 +291,10 @@ def main():
         e0.record(stream)
         for i in range(args.steps):
             ev[3 * i].record(stream)
-            L, s, k, info = lg.logm_execute(A_dev, stats=stats)
+            L, s, k, info = lg.logm_execute(A_dev, stats=stats, **main)
             ev[3 * i + 1].record(stream)
             if big:
-                Lb, sb, kb, infob = lg.logm_execute(B_dev, stats=stats_b)
+                Lb, sb, kb, infob = lg.logm_execute(B_dev, stats=stats_b, **main)
             ev[3 * i + 2].record(stream)
         e1.record(stream)
         barrier()
@@ -313,9 +322,9 @@ def main():
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        lg.logm_execute_host(A_host, out=L_host, device=dev, workspace=ws_e2e)
+        lg.logm_execute_host(A_host, out=L_host, device=dev, workspace=ws_e2e, **main)
         if big:
-            lg.logm_execute_host(B_host, out=LB_host, device=dev, workspace=ws_e2e)
+            lg.logm_execute_host(B_host, out=LB_host, device=dev, workspace=ws_e2e, **main)
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps if e2e_steps else float("nan")
     e2e_ms = shard.max_over_ranks(e2e_ms, device=dev)
     h2d = A_host.numel() * 8 + (B_host.numel() * 8 if big else 0)
@@ -328,7 +337,9 @@ def main():
     # product form of the Denman-Beavers iteration, and diagonal balancing;
     # each timed on the same inputs, error against the FP64 result.
     forms = {}
-    variants = [] if args.no_forms else [("tf32x3", {"precision": "tf32x3"}, 2), ("bf16x3", {"precision": "bf16x3"}, 2),
+    other = "pipe" if args.fp64_products == "tc_sliced" else "tc_sliced"
+    variants = [] if args.no_forms else [("fp64_" + other, {"fp64_products": other}, 1),
+                                         ("tf32x3", {"precision": "tf32x3"}, 2), ("bf16x3", {"precision": "bf16x3"}, 2),
                                          ("db_product", {"db_form": "product"}, 1), ("balanced", {"balance": True}, 1)]
     st_fa = torch.zeros(4 * count, dtype=torch.int32, device=dev)
     st_fb = torch.zeros(4, dtype=torch.int32, device=dev)
@@ -435,12 +446,24 @@ def main():
         peaks = {"fp64": measure_gemm_peak(torch, dev, torch.float64, local),
                  "tf32": measure_gemm_peak(torch, dev, torch.float32, local, tf32=True)}
         peak = peak_a = peaks["fp64"]["tflops"]
-        peak_note = ("of measured: cuBLAS DGEMM 8192^3 (torch.matmul float64) back to back for "
+        peak_note = ("FP64 dense of measured: cuBLAS DGEMM 8192^3 (torch.matmul float64) back to back for "
                      f"{peaks['fp64']['seconds']:.1f} s in this run")
+        bound = "tensor"
         # dominant kernel: the whole-GPU 4096 kernel
         if big:
             ach = flops_b / (ms_b * 1e-3) / 1e12
             kname, fpl = "k_logm_large<execute> (cooperative, whole GPU on the 4096 matrix)", flops_b
+            if args.fp64_products == "tc_sliced":
+                # its FP64 products run on the BF16 tensor cores as 36 exact digit-pair
+                # products each (8 digits per operand, pairs i + j <= 9): the ceiling of
+                # that form is the sustained BF16 peak / 36
+                pk = measured_peaks()
+                bf16 = pk.get("bf16_tflops_sustained", 1700.0)
+                peak = bf16 / 36.0
+                peak_note = (f"FP64-equivalent ceiling of the 8-digit BF16 form: {'measured' if pk else 'fallback'} "
+                             f"sustained BF16 {bf16:.1f} TFLOP/s / 36 digit-pair products per FP64 product "
+                             f"({'of measured' if pk else 'of fallback'}); against the measured FP64 DGEMM peak "
+                             f"{peak_a:.3f} TFLOP/s the kernel runs at {ach / peak_a:.2f}x")
         else:
             ach = flops_a / (ms_a * 1e-3) / 1e12
             kname, fpl = "k_logm_small<execute> (persistent, one block per matrix)", flops_a
@@ -450,7 +473,7 @@ def main():
         # 96.62 GB, mostly the working matrix written back by every rank-32
         # update, which scales with n^3: x 8 for one 4096^2 launch.
         traffic, traffic_note = None, "not captured for this configuration"
-        if big and args.big_n == NBIG:
+        if big and args.big_n == NBIG and args.fp64_products == "pipe":
             traffic = 8 * (7.813095e9 + 88.806196e9)
             traffic_note = ("bytes per launch: 8 x the DRAM bytes ncu measured on the 2048^2 case of the same "
                             "kernel and plan (traffic grows with n^3); far below HBM bandwidth, FP64-pipe bound")
@@ -458,7 +481,8 @@ def main():
             traffic = None
         parts = {"batch256": {"ms": ms_a, "matrices_per_s": count / (ms_a * 1e-3),
                               "tflops": flops_a / (ms_a * 1e-3) / 1e12,
-                              "frac": flops_a / (ms_a * 1e-3) / 1e12 / peak_a, "peak_note": "FP64 dense " + peak_note,
+                              "frac": flops_a / (ms_a * 1e-3) / 1e12 / peak_a,
+                              "peak_note": "of measured FP64 DGEMM peak (FP64 pipe, one block per matrix)",
                               "s_hist": np.bincount(s_np).tolist(), "k_hist": np.bincount(k_np, minlength=6).tolist(),
                               "info_nonzero": int((info_np != 0).sum()),
                               "work": dict(zip(("db_iterations", "inverses", "products"),
@@ -471,12 +495,12 @@ def main():
             "matrices_per_s": n_mats * world / (ms_max * 1e-3), "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": arm_config(count, big, args.big_n, world),
+            "config": arm_config(count, big, args.big_n, world, args.fp64_products),
             "parts": parts,
             "forms": forms,
-            "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "roofline": {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach / peak, "traffic": traffic, "traffic_note": traffic_note,
-                         "peak_note": "FP64 dense " + peak_note,
+                         "peak_note": peak_note,
                          "kernel": kname, "flops_per_launch": fpl},
             "peaks_measured": peaks,
             "e2e": {"value": (flops_a + flops_b) * world / (e2e_ms * 1e-3) / 1e12 if e2e_steps else None,

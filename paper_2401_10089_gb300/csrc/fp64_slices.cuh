@@ -36,7 +36,7 @@
 
 namespace lg {
 
-constexpr int kSlices = 8;                     // digits per operand
+constexpr int kSlices = 8;                     // digits per operand (slice_bias assumes 8)
 constexpr int kSliceK = 32;                    // K of one exact accumulation (the panel width)
 constexpr int kSliceLevels = kSlices;          // levels L = 2 .. kSlices + 1
 constexpr int kSliceFrac = 7 + 8 * (kSlices - 1);  // F: fractional bits of the fixed-point form
@@ -111,6 +111,52 @@ LG_HD void slice_digits(int64_t X, int32_t* d) {
   d[0] = static_cast<int32_t>(X);
 }
 
+// The same integer as slice_fixed (round(u 2^(kSliceFrac - e)), ties to
+// even) from the bits of u with integer operations only: u = M 2^(x - 52)
+// with the 53-bit integer M, so the result is M shifted by x - 52 + F - e
+// (at most 10 to the left, since |u| < 2^e), rounded when shifted right.
+LG_HD int64_t slice_fixed_int(double u, int32_t e) {
+  const uint64_t b = lg_dbits(u);
+  const int bx = static_cast<int>((b >> 52) & 0x7FF);
+  uint64_t M = b & ((1ull << 52) - 1);
+  int x;
+  if (bx == 0) {
+    x = -1022;  // subnormal (or zero): no implicit bit
+  } else {
+    M |= 1ull << 52;
+    x = bx - 1023;
+  }
+  const int sh = x - 52 + kSliceFrac - e;
+  uint64_t mag;
+  if (sh >= 0) {
+    mag = M << sh;  // sh <= 10: below 2^63
+  } else if (sh > -64) {
+    const int r = -sh;
+    const uint64_t q = M >> r, rem = M & ((1ull << r) - 1), half = 1ull << (r - 1);
+    mag = q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+  } else {
+    mag = 0;  // below half a unit of the last digit
+  }
+  return (b >> 63) ? -static_cast<int64_t>(mag) : static_cast<int64_t>(mag);
+}
+
+// Digit i (0 = most significant) of the balanced base-256 form of X (the
+// digits slice_digits gives), without the carry chain: with the bias
+// C = sum of 128 * 256^m (m = 0 .. kSlices - 2), digit m from the bottom is
+// byte m of X + C minus 128, and the top digit is (X + C) >> 8 (kSlices - 1).
+// Y = X + C is kept modulo 2^64 (|X| may reach 2^63 - 2^10); the top digit
+// is formed from X itself and the carry of its low bytes.
+constexpr uint64_t kSliceBias = 0x0080808080808080ull;
+LG_HD uint64_t slice_bias(int64_t X) { return static_cast<uint64_t>(X) + kSliceBias; }
+LG_HD int32_t slice_digit(int64_t X, uint64_t Y, int i) {
+  constexpr int top = 8 * (kSlices - 1);
+  if (i == 0) {
+    const uint64_t low = static_cast<uint64_t>(X) & ((1ull << top) - 1);
+    return static_cast<int32_t>(X >> top) + static_cast<int32_t>((low + kSliceBias) >> top);
+  }
+  return static_cast<int32_t>((Y >> (8 * (kSlices - 1 - i))) & 255) - 128;
+}
+
 // Integer value of an FP32 level sum (an exact integer, |v| <= 2^22).
 LG_HD int32_t level_int(float v) {
   return static_cast<int32_t>(lg_fbits(v + 12582912.0f)) - 0x4B400000;
@@ -141,6 +187,69 @@ LG_HD double combine_levels(const int32_t* c, int32_t eu, int32_t ev) {
   return ldexp(t, E);  // rare: the scale itself is outside the normal range
 }
 
+// Leading zeros of a 64-bit word (x != 0).
+LG_HD int lg_clz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __clzll(static_cast<long long>(x));
+#else
+  return __builtin_clzll(x);
+#endif
+}
+
+// (hi 2^32 + lo) 2^E rounded to the nearest FP64 (ties to even) with integer
+// operations only (no FP64 instruction): the signed 128-bit sum, its
+// magnitude normalised, 53 bits kept with round/sticky bits, the exponent
+// field set to the binary point plus E. hi, lo as from level_halves
+// (|hi|, |lo| < 2^48). Returns false (leaving *out alone) when the result
+// would be subnormal or overflow; the caller then takes the FP64 route.
+LG_HD bool levels_to_double(int64_t hi, int64_t lo, int E, double* out) {
+  // 128-bit two's complement value v = hi 2^32 + lo as (vh, vl)
+  const uint64_t a_lo = static_cast<uint64_t>(hi) << 32;
+  const uint64_t a_hi = static_cast<uint64_t>(hi >> 32);  // arithmetic shift: sign extension
+  const uint64_t b_lo = static_cast<uint64_t>(lo);
+  const uint64_t b_hi = static_cast<uint64_t>(lo >> 63);
+  uint64_t vl = a_lo + b_lo;
+  uint64_t vh = a_hi + b_hi + (vl < a_lo ? 1u : 0u);
+  const uint64_t sign = vh >> 63;
+  if (sign) {  // magnitude
+    vl = ~vl + 1;
+    vh = ~vh + (vl == 0 ? 1u : 0u);
+  }
+  if ((vh | vl) == 0) {
+    *out = 0.0;
+    return true;
+  }
+  // normalise: the leading one to bit 127
+  int lz;
+  if (vh != 0) {
+    lz = lg_clz64(vh);
+    if (lz) {
+      vh = (vh << lz) | (vl >> (64 - lz));
+      vl <<= lz;
+    }
+  } else {
+    lz = 64 + lg_clz64(vl);
+    vh = vl << (lz - 64);
+    vl = 0;
+  }
+  // 53 bits of mantissa, then the guard bit and the sticky bits
+  uint64_t m = vh >> 11;
+  const uint64_t guard = (vh >> 10) & 1u;
+  const bool sticky = ((vh & 0x3FFu) | vl) != 0;
+  int p = 127 - lz;  // position of the leading one in the integer
+  if (guard && (sticky || (m & 1u))) {
+    m += 1;
+    if (m >> 53) {
+      m >>= 1;
+      ++p;
+    }
+  }
+  const int be = p + E + 1023;  // biased exponent of m 2^(p - 52) 2^E
+  if (be < 1 || be > 2046) return false;
+  *out = lg_bitsd((sign << 63) | (static_cast<uint64_t>(be) << 52) | (m & ((1ull << 52) - 1)));
+  return true;
+}
+
 // w + u.v with the same two roundings (T to FP64, then the sum: one FMA).
 LG_HD double combine_levels_add(const int32_t* c, int32_t eu, int32_t ev, double w) {
   if (eu == kSliceNonFinite || ev == kSliceNonFinite) return lg_bitsd(0x7FF8000000000000ull);  // NaN
@@ -150,6 +259,28 @@ LG_HD double combine_levels_add(const int32_t* c, int32_t eu, int32_t ev, double
   const int E = eu + ev - kSliceScale;
   if (E >= -1022 && E <= 1023) return fma(t, lg_pow2(E), w);
   return w + ldexp(t, E);
+}
+
+// u.v with T rounded to FP64 by integer operations (no FP64 instruction
+// unless the product is subnormal or overflows).
+LG_HD double combine_levels_int(const int32_t* c, int32_t eu, int32_t ev) {
+  if (eu == kSliceNonFinite || ev == kSliceNonFinite) return lg_bitsd(0x7FF8000000000000ull);  // NaN
+  int64_t hi, lo;
+  level_halves(c, &hi, &lo);
+  double t;
+  if (levels_to_double(hi, lo, eu + ev - kSliceScale, &t)) return t;
+  return combine_levels(c, eu, ev);
+}
+
+// w + u.v with T rounded to FP64 by integer operations (one FP64 instruction
+// per element: the addition), the same two roundings as combine_levels_add.
+LG_HD double combine_levels_add_int(const int32_t* c, int32_t eu, int32_t ev, double w) {
+  if (eu == kSliceNonFinite || ev == kSliceNonFinite) return lg_bitsd(0x7FF8000000000000ull);  // NaN
+  int64_t hi, lo;
+  level_halves(c, &hi, &lo);
+  double t;
+  if (levels_to_double(hi, lo, eu + ev - kSliceScale, &t)) return w + t;
+  return combine_levels_add(c, eu, ev, w);  // subnormal or overflowing product: the FP64 route
 }
 
 }  // namespace lg

@@ -337,9 +337,63 @@ struct GridOps {
 
   __device__ void gemm(int n, const double* A, double as, const double* B, double bs, double alpha,
                        const EpiTerms& e, OutView out, bool ta = false, bool tb = false) {
+    if (maps && !ta && !tb) {
+      gemm_sliced(n, A, as, B, bs, alpha, e, out);
+      return;
+    }
     const int tiles = (n + kTileM - 1) / kTileM;
     for (int t = blockIdx.x; t < tiles * tiles; t += gridDim.x)
       gemm_tile(n, (t / tiles) * kTileM, (t % tiles) * kTileN, A, as, B, bs, alpha, e, out, S.gemm, ta, tb);
+    sync();
+  }
+
+  // out = alpha (A - as I)(B - bs I) + sum_t e.c[t] e.M[t] on the tensor cores:
+  // K in chunks of 32, each chunk's rank-32 product formed exactly from BF16
+  // digits (tc_update.cuh, per-row scales of the chunk of A, per-column scales
+  // of the chunk of B) and added to an FP64 accumulator, then the epilogue
+  // terms. Uses group 0's digit buffers and working matrix (free outside the
+  // inversions) with every block of the grid.
+  __device__ __noinline__ void gemm_sliced(int n, const double* A, double as, const double* B, double bs, double alpha,
+                              const EpiTerms& e, OutView out) {
+    GjGroup& g = w.gj[0];
+    double* C = g.work;
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t t = tid(); t < nn; t += nthreads()) C[t] = 0.0;
+    const int T = ((n + kUpdM - 1) / kUpdM) * ((n + kUpdN - 1) / kUpdN);
+    const int G = gridDim.x, lb = blockIdx.x;
+    const int t_lo = (int)((int64_t)lb * T / G), t_hi = (int)((int64_t)(lb + 1) * T / G);
+    for (int kb = 0; kb < n; kb += kSliceK) {
+      const int jb = min(kSliceK, n - kb);
+      // digits of A[:, kb..kb+jb) by rows and of B[kb..kb+jb, :] by columns,
+      // eight threads (one per digit slice) per row or column
+      for (int q = tid(); q < 2 * n * kSlices; q += nthreads()) {
+        const int rc = q / kSlices, i = q % kSlices;
+        double u[kSliceK];
+        if (rc < n) {
+          for (int c = 0; c < kSliceK; ++c)
+            u[c] = c < jb ? A[(int64_t)rc * n + kb + c] - (rc == kb + c ? as : 0.0) : 0.0;
+          slice_store_part(u, jb, i, g.sl.adig + (int64_t)rc * kDigK, g.sl.aexp + rc);
+        } else {
+          const int j = rc - n;
+          for (int c = 0; c < kSliceK; ++c)
+            u[c] = c < jb ? B[(int64_t)(kb + c) * n + j] - (kb + c == j ? bs : 0.0) : 0.0;
+          slice_store_part(u, jb, i, g.sl.bdig + (int64_t)j * kDigK, g.sl.bexp + j);
+        }
+      }
+      fence_proxy_async_global();
+      sync();
+      if (threadIdx.x == 0) S.skip_upd = *(volatile int*)w.err;
+      __syncthreads();
+      if (!S.skip_upd)
+        sliced_update(S.slc, reinterpret_cast<unsigned char*>(grid_panel_smem), &maps->a[0], &maps->b[0], g.sl, C, n,
+                      0, 0, t_lo, t_hi, w.err);
+      sync();
+    }
+    for (int64_t t = tid(); t < nn; t += nthreads()) {
+      double v = alpha * C[t];
+      for (int s = 0; s < e.count; ++s) v = fma(e.c[s], e.M[s][t], v);
+      store_out(out, (size_t)t, v);
+    }
     sync();
   }
 
@@ -547,34 +601,58 @@ struct GridOps {
         Pf[(int64_t)c * n + r] = v;
       }
       if (maps) {
-        // digits of the update's left factor U = P_f - I_J, one row per thread
-        for (int rr = threadIdx.x; rr < my_rows; rr += kThreads) {
-          const int r = r_lo + rr;
+        // digits of the update's left factor U = P_f - I_J: this block's rows,
+        // eight threads (one per digit slice) per row
+        for (int q = threadIdx.x; q < my_rows * kSlices; q += kThreads) {
+          const int rr = q / kSlices, r = r_lo + rr;
           double u[kSliceK];
           for (int c = 0; c < kSliceK; ++c)
             u[c] = c < jb ? Sf[rr * kGridPanel + c] - (r == kb + c ? 1.0 : 0.0) : 0.0;
-          slice_store(u, jb, g.sl.adig + (int64_t)r * kDigK, g.sl.aexp + r);
+          slice_store_part(u, jb, q % kSlices, g.sl.adig + (int64_t)r * kDigK, g.sl.aexp + r);
         }
       }
-      for (int j = gt; j < n; j += gnt) {
-        if (j >= kb && j < kb + jb) continue;
-        for (int c = 0; c < jb; ++c) {
-          const int k = kb + c, p = g.piv[k];
-          if (p != k) {
-            const double t0 = W[(int64_t)k * n + j];
-            W[(int64_t)k * n + j] = W[(int64_t)p * n + j];
-            W[(int64_t)p * n + j] = t0;
+      if (!maps) {
+        for (int j = gt; j < n; j += gnt) {
+          if (j >= kb && j < kb + jb) continue;
+          for (int c = 0; c < jb; ++c) {
+            const int k = kb + c, p = g.piv[k];
+            if (p != k) {
+              const double t0 = W[(int64_t)k * n + j];
+              W[(int64_t)k * n + j] = W[(int64_t)p * n + j];
+              W[(int64_t)p * n + j] = t0;
+            }
           }
-        }
-        if (maps) {  // the right factor V = R, column j: its digits
-          double v[kSliceK];
-          for (int c = 0; c < kSliceK; ++c) v[c] = c < jb ? W[(int64_t)(kb + c) * n + j] : 0.0;
-          slice_store(v, jb, g.sl.bdig + (int64_t)j * kDigK, g.sl.bexp + j);
-        } else {
           for (int c = 0; c < jb; ++c) g.R[(int64_t)c * n + j] = W[(int64_t)(kb + c) * n + j];
         }
+      } else {
+        // eight lanes of a warp per column: the first swaps the panel's pivot
+        // rows in that column, then each lane forms one digit slice of the
+        // column of V = R (the swapped pivot rows); warps walk the columns
+        // four at a time, so every block of the group takes part
+        const int lane = threadIdx.x & 31, i = lane & 7;
+        const int gw = gt >> 5, nw = gnt >> 5;
+        for (int j4 = gw * 4; j4 < n; j4 += nw * 4) {
+          const int j = j4 + (lane >> 3);
+          const bool valid = j < n && (j < kb || j >= kb + jb);
+          if (valid && i == 0)
+            for (int c = 0; c < jb; ++c) {
+              const int k = kb + c, p = g.piv[k];
+              if (p != k) {
+                const double t0 = W[(int64_t)k * n + j];
+                W[(int64_t)k * n + j] = W[(int64_t)p * n + j];
+                W[(int64_t)p * n + j] = t0;
+              }
+            }
+          __syncwarp();
+          if (valid) {
+            double v[kSliceK];
+            for (int c = 0; c < kSliceK; ++c) v[c] = c < jb ? W[(int64_t)(kb + c) * n + j] : 0.0;
+            slice_store_part(v, jb, i, g.sl.bdig + (int64_t)j * kDigK, g.sl.bexp + j);
+          }
+          __syncwarp();
+        }
+        fence_proxy_async_global();  // the digits are read by TMA after the barrier
       }
-      if (maps) fence_proxy_async_global();  // the digits are read by TMA after the barrier
       bounded_barrier(bar, gn, w.err, ep);
       if (maps) {
         if (threadIdx.x == 0) S.skip_upd = *(volatile int*)w.err;

@@ -14,8 +14,11 @@
 //     region of 64 columns (8 levels = all 512 columns). Every level sum is an
 //     integer below 2^22, so the FP32 accumulation is exact;
 //   * all eight warps read the levels back (tcgen05.ld), combine them into the
-//     exact integer dot product, round it to FP64 once and add it to W.
-// Per element and panel that is 4 FP64 instructions instead of 32 FP64 FMAs.
+//     exact integer dot product and round it to FP64 with integer operations
+//     into a shared-memory tile; the next tile's MMAs start as soon as TMEM is
+//     read, while the warps add the staged tile to W row by row (coalesced).
+// Per element and panel that is one FP64 instruction (the addition) instead
+// of 32 FP64 FMAs.
 //
 // Every mbarrier wait is bounded (kTmWaitLimit polls); a wait that runs out
 // sets the grid's error word, and the kernel reports LOGM_INFO_TIMEOUT for the
@@ -34,7 +37,9 @@ constexpr int kDigK = kSlices * kSliceK;                    // digits per row of
 constexpr uint32_t kUpdABytes = kUpdM * kDigK * 2;          // 64 KB
 constexpr uint32_t kUpdBBytes = kUpdN * kDigK * 2;          // 32 KB
 constexpr uint32_t kUpdAtomA = kUpdM * 128, kUpdAtomB = kUpdN * 128;  // one 128-byte swizzle box
-constexpr size_t kUpdSmemBytes = kUpdABytes + 2 * kUpdBBytes + 1024;  // + alignment slack
+constexpr int kUpdTsStride = kUpdN + 1;                     // staged tile: doubles per row (padded)
+constexpr uint32_t kUpdTsBytes = kUpdM * kUpdTsStride * 8;   // 65 KB
+constexpr size_t kUpdSmemBytes = kUpdABytes + 2 * kUpdBBytes + kUpdTsBytes + 1024;  // + alignment slack
 constexpr int kUpdTmemCols = kSliceLevels * kUpdN;           // 512
 static_assert(kUpdTmemCols == 512, "eight levels of 64 columns fill TMEM");
 
@@ -57,41 +62,36 @@ struct SliceSmem {
   uint32_t phase[4];          // completed phases of each barrier
   uint32_t tmem;              // TMEM base address of the level accumulators
   int failed;                 // a bounded wait ran out
+  int32_t ecol[kUpdN];        // scale exponents of the current tile's columns of V
 };
 
-// The digits of 32 values (the first `count` given, the rest zero), stored
-// as one row of kDigK BF16 at out; the scale exponent goes to *eo.
-static __device__ void slice_store(const double* v, int count, __nv_bfloat16* out, int32_t* eo) {
+// Digit slice i of 32 values (the first `count` given, the rest zero): the
+// 32 BF16 at out[32 i .. 32 i + 31] of a row of kDigK; slice 0 also stores
+// the scale exponent at *eo. Eight threads, one per slice, split a row
+// between them (each forms the row's scale itself). Integer operations only.
+static __device__ __noinline__ void slice_store_part(const double* v, int count, int i, __nv_bfloat16* out,
+                                                     int32_t* eo) {
   double m = 0.0;
   for (int k = 0; k < count; ++k) {
     const double a = fabs(v[k]);
     if (!(a <= m)) m = a;  // NaN wins
   }
   const int32_t e = slice_exponent(m);
-  *eo = e;
-  int64_t X[kSliceK];
-  for (int k = 0; k < kSliceK; ++k) X[k] = (k < count && e != kSliceNonFinite) ? slice_fixed(v[k], e) : 0;
-  uint4* o = reinterpret_cast<uint4*>(out);
-  // least significant digit first; digit i of every term fills 32 BF16 (4 x 16 B)
-  for (int i = kSlices - 1; i >= 0; --i) {
-    uint32_t pk[kSliceK / 2];
-    for (int k = 0; k < kSliceK; k += 2) {
-      int32_t d0, d1;
-      if (i > 0) {
-        d0 = static_cast<int32_t>((X[k] + 128) & 255) - 128;
-        d1 = static_cast<int32_t>((X[k + 1] + 128) & 255) - 128;
-        X[k] = (X[k] - d0) / 256;
-        X[k + 1] = (X[k + 1] - d1) / 256;
-      } else {
-        d0 = static_cast<int32_t>(X[k]);
-        d1 = static_cast<int32_t>(X[k + 1]);
-      }
-      // |d| <= 128 has at most 8 significant bits: the BF16 is the FP32's top half
-      pk[k / 2] = (__float_as_uint(static_cast<float>(d0)) >> 16) |
-                  (__float_as_uint(static_cast<float>(d1)) & 0xFFFF0000u);
+  if (i == 0) *eo = e;
+  uint32_t pk[kSliceK / 2];
+  for (int k = 0; k < kSliceK; k += 2) {
+    int32_t d[2];
+    for (int h = 0; h < 2; ++h) {
+      const int kk = k + h;
+      const int64_t X = (kk < count && e != kSliceNonFinite) ? slice_fixed_int(v[kk], e) : 0;
+      d[h] = slice_digit(X, slice_bias(X), i);
     }
-    for (int q = 0; q < 4; ++q) o[i * 4 + q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    // |d| <= 128 has at most 8 significant bits: the BF16 is the FP32's top half
+    pk[k / 2] = (__float_as_uint(static_cast<float>(d[0])) >> 16) |
+                (__float_as_uint(static_cast<float>(d[1])) & 0xFFFF0000u);
   }
+  uint4* o = reinterpret_cast<uint4*>(out) + i * 4;
+  for (int q = 0; q < 4; ++q) o[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
 }
 
 // Generic-proxy writes (the digits) made visible to later TMA reads.
@@ -99,19 +99,51 @@ static __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// The 72 MMAs of one tile (called by one thread): waits for its U tile (when
+// it is a new one) and its V stage, then for each level L = i + j the digit
+// pairs (i, j), both K halves of the 32 terms, into the level's 64 TMEM
+// columns; the commit arrives on bar_acc once they are done (also when a wait
+// ran out: then nothing was issued and the result is false).
+static __device__ __forceinline__ bool tile_mmas(uint32_t tmem, uint32_t sA, uint32_t sB, uint32_t bar_a, bool wait_a,
+                                                 uint32_t ph_a, uint32_t bar_b, uint32_t ph_b, uint32_t bar_acc) {
+  bool ok = true;
+  if (wait_a) ok = tm_wait(bar_a, ph_a & 1);
+  ok = ok && tm_wait(bar_b, ph_b & 1);
+  if (ok) {
+    tm_fence_after();
+    const uint32_t id = tm_idesc(1, kUpdM, kUpdN);  // BF16 x BF16 -> FP32
+    for (int L = 2; L <= kSlices + 1; ++L) {
+      int first = 1;
+      for (int i = 1; i < L; ++i) {
+        const int j = L - i;
+        for (int h = 0; h < 2; ++h) {
+          const int ka = 32 * (i - 1) + 16 * h, kbb = 32 * (j - 1) + 16 * h;
+          const uint64_t da = tm_desc(sA + (ka / 64) * kUpdAtomA + (ka % 64) * 2);
+          const uint64_t db = tm_desc(sB + (kbb / 64) * kUpdAtomB + (kbb % 64) * 2);
+          tm_mma_f16(tmem + static_cast<uint32_t>((L - 2) * kUpdN), da, db, id, first ? 0 : 1);
+          first = 0;
+        }
+      }
+    }
+  }
+  tm_commit(bar_acc);
+  return ok;
+}
+
 // W[r, c] += (U V)[r, c] for every r < n and every column c < n outside
 // [kb, kb + jb), over the tiles [t_lo, t_hi) of this block (row-major order
 // of the ceil(n / 128) x ceil(n / 64) tiles). dyn: this block's dynamic shared
 // memory; err: the grid's error word.
-static __device__ void sliced_update(SliceSmem& sm, unsigned char* dyn, const CUtensorMap* map_a,
-                                     const CUtensorMap* map_b, const SliceBufs& sb, double* W, int n, int kb, int jb,
-                                     int t_lo, int t_hi, int* err) {
+static __device__ __noinline__ void sliced_update(SliceSmem& sm, unsigned char* dyn, const CUtensorMap* map_a,
+                                                  const CUtensorMap* map_b, const SliceBufs& sb, double* W, int n,
+                                                  int kb, int jb, int t_lo, int t_hi, int* err) {
   if (t_lo >= t_hi) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ncb = (n + kUpdN - 1) / kUpdN;
   const uint32_t raw = su32(dyn);
   const uint32_t sA = (raw + 1023u) & ~1023u;
   const uint32_t sB[2] = {sA + kUpdABytes, sA + kUpdABytes + kUpdBBytes};
+  double* Ts = reinterpret_cast<double*>(dyn + (sA - raw) + kUpdABytes + 2 * kUpdBBytes);  // [kUpdM][kUpdTsStride]
   const uint32_t barA = su32(&sm.bar[0]), barB[2] = {su32(&sm.bar[1]), su32(&sm.bar[2])}, barAcc = su32(&sm.bar[3]);
   uint32_t phA = sm.phase[0], phB[2] = {sm.phase[1], sm.phase[2]}, phAcc = sm.phase[3];
   const uint32_t tmem = sm.tmem;
@@ -130,49 +162,27 @@ static __device__ void sliced_update(SliceSmem& sm, unsigned char* dyn, const CU
   // thread 0: phases issued on each barrier (lifetime counts, like phA ...)
   uint32_t isA = phA, isB[2] = {phB[0], phB[1]}, isAcc = phAcc;
   if (tid == 0) {
+    fence_proxy_async_global();  // the digits other blocks wrote before the barrier, for the copies below
     issue(t_lo, true, 0);
     ++isA;
     ++isB[0];
   }
+  if (tid == 32 && !tile_mmas(tmem, sA, sB[0], barA, true, phA, barB[0], phB[0], barAcc)) atomicExch(&sm.failed, 1);
+  ++phA;
+  ++phB[0];
+  ++isAcc;
   bool failed = false;
   for (int t = t_lo; t < t_hi; ++t) {
     const int k = t - t_lo, st = k & 1;
     const int rb = t / ncb, cb = t % ncb;
-    const bool new_a = (t == t_lo) || (rb != (t - 1) / ncb);
+    const int r0 = rb * kUpdM, c0 = cb * kUpdN;
     const bool has_next = t + 1 < t_hi;
     const bool next_new_a = has_next && ((t + 1) / ncb != rb);
-    if (tid == 32) {  // the MMA issuer
-      bool ok = true;
-      if (new_a) ok = tm_wait(barA, phA & 1);
-      ok = ok && tm_wait(barB[st], phB[st] & 1);
-      if (ok) {
-        tm_fence_after();
-        const uint32_t id = tm_idesc(1, kUpdM, kUpdN);  // BF16 x BF16 -> FP32
-        for (int L = 2; L <= kSlices + 1; ++L) {
-          int first = 1;
-          for (int i = 1; i < L; ++i) {
-            const int j = L - i;
-            for (int h = 0; h < 2; ++h) {
-              const int ka = 32 * (i - 1) + 16 * h, kbb = 32 * (j - 1) + 16 * h;
-              const uint64_t da = tm_desc(sA + (ka / 64) * kUpdAtomA + (ka % 64) * 2);
-              const uint64_t db = tm_desc(sB[st] + (kbb / 64) * kUpdAtomB + (kbb % 64) * 2);
-              tm_mma_f16(tmem + static_cast<uint32_t>((L - 2) * kUpdN), da, db, id, first ? 0 : 1);
-              first = 0;
-            }
-          }
-        }
-      } else {
-        atomicExch(&sm.failed, 1);
-      }
-      tm_commit(barAcc);  // arrives once the MMAs issued so far are complete
-    }
-    if (new_a) ++phA;
-    ++phB[st];
-    ++isAcc;  // one commit per tile
     if (tid == 0 && has_next && !next_new_a) {  // the other V stage is free: its last reader was tile t - 1
       issue(t + 1, false, st ^ 1);
       ++isB[st ^ 1];
     }
+    if (tid < kUpdN) sm.ecol[tid] = c0 + tid < n ? sb.bexp[c0 + tid] : 0;
     // tcgen05.ld is warp-collective: a warp reads the accumulators only if all its lanes saw them ready
     const bool acc_ok = __all_sync(0xffffffffu, tm_wait(barAcc, phAcc & 1));
     ++phAcc;
@@ -183,32 +193,60 @@ static __device__ void sliced_update(SliceSmem& sm, unsigned char* dyn, const CU
       ++isA;
       ++isB[st ^ 1];
     }
-    // epilogue: warp w reads lanes 32 (w % 4) .. + 31 (rows), columns half (w / 4)
-    const int lbase = (warp & 3) * 32, half = warp >> 2;
-    const int row = rb * kUpdM + lbase + lane;
-    const int c0 = cb * kUpdN;
-    const int32_t er = row < n ? sb.aexp[row] : 0;
-    double* Wrow = W + (int64_t)row * n;
+    __syncthreads();  // the column exponents are in shared memory
+    // levels -> exact dot products -> FP64, staged in Ts (warp w: TMEM lanes
+    // 32 (w % 4) .. + 31 = tile rows, columns half (w / 4))
     if (acc_ok) {
+      const int lrow = (warp & 3) * 32 + lane, half = warp >> 2;
+      const int row = r0 + lrow;
+      const int32_t er = row < n ? sb.aexp[row] : 0;
       for (int q = 0; q < 4; ++q) {
         const int cc = half * 32 + q * 8;
         uint32_t v[kSliceLevels][8];
         for (int L = 0; L < kSliceLevels; ++L)
-          tm_ld8(tmem + (static_cast<uint32_t>(lbase) << 16) + static_cast<uint32_t>(L * kUpdN + cc), v[L]);
+          tm_ld8(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + static_cast<uint32_t>(L * kUpdN + cc), v[L]);
         tm_ld_wait();
-        if (row < n) {
-          for (int e = 0; e < 8; ++e) {
-            const int gc = c0 + cc + e;
-            if (gc >= n || (gc >= kb && gc < kb + jb)) continue;
-            int32_t c[kSliceLevels];
-            for (int L = 0; L < kSliceLevels; ++L) c[L] = level_int(__uint_as_float(v[L][e]));
-            Wrow[gc] = combine_levels_add(c, er, sb.bexp[gc], Wrow[gc]);
-          }
+        for (int e = 0; e < 8; ++e) {
+          int32_t c[kSliceLevels];
+          for (int L = 0; L < kSliceLevels; ++L) c[L] = level_int(__uint_as_float(v[L][e]));
+          Ts[lrow * kUpdTsStride + cc + e] = combine_levels_int(c, er, sm.ecol[cc + e]);
         }
       }
     }
     tm_fence_before();
-    __syncthreads();
+    __syncthreads();  // TMEM read, Ts complete
+    // the next tile's MMAs overlap the additions below
+    if (has_next) {
+      if (tid == 32 && sm.failed == 0 &&
+          !tile_mmas(tmem, sA, sB[st ^ 1], barA, next_new_a, phA, barB[st ^ 1], phB[st ^ 1], barAcc))
+        atomicExch(&sm.failed, 1);
+      if (next_new_a) ++phA;
+      ++phB[st ^ 1];
+      ++isAcc;
+    }
+    // W += Ts: warp w takes rows w, w + 8, ..., lanes along the row
+    // (coalesced). All 32 loads of a thread are issued before any store, so
+    // their latencies overlap (the compiler may not move a load above a store
+    // to memory it cannot prove distinct).
+    if (acc_ok) {
+      constexpr int kPer = (kUpdM / 8) * 2;  // 16 rows x 2 column halves per thread
+      double wv[kPer];
+#pragma unroll
+      for (int it = 0; it < kPer; ++it) {
+        const int rr = warp + 8 * (it >> 1), c = lane + 32 * (it & 1);
+        const int gr = r0 + rr, gc = c0 + c;
+        const bool ok = gr < n && gc < n && (gc < kb || gc >= kb + jb);
+        wv[it] = ok ? __ldcg(W + (int64_t)gr * n + gc) : 0.0;
+      }
+#pragma unroll
+      for (int it = 0; it < kPer; ++it) {
+        const int rr = warp + 8 * (it >> 1), c = lane + 32 * (it & 1);
+        const int gr = r0 + rr, gc = c0 + c;
+        if (gr < n && gc < n && (gc < kb || gc >= kb + jb))
+          W[(int64_t)gr * n + gc] = wv[it] + Ts[rr * kUpdTsStride + c];
+      }
+    }
+    __syncthreads();  // Ts free for the next tile
     failed = sm.failed != 0;
     if (failed) break;
   }
@@ -217,8 +255,8 @@ static __device__ void sliced_update(SliceSmem& sm, unsigned char* dyn, const CU
     // last phase issued on each barrier (a completed phase returns at once)
     if (tid == 0) {
       if (isA > sm.phase[0]) tm_wait(barA, (isA - 1) & 1);
-      for (int s = 0; s < 2; ++s)
-        if (isB[s] > sm.phase[1 + s]) tm_wait(barB[s], (isB[s] - 1) & 1);
+      for (int s2 = 0; s2 < 2; ++s2)
+        if (isB[s2] > sm.phase[1 + s2]) tm_wait(barB[s2], (isB[s2] - 1) & 1);
       if (isAcc > sm.phase[3]) tm_wait(barAcc, (isAcc - 1) & 1);
       atomicExch(err, 1);
     }

@@ -46,6 +46,29 @@ double h_sliced_dot(const double* u, const double* v, int k) {
 }
 
 int32_t h_level_int(float v) { return lg::level_int(v); }
+
+// the integer-only split against the FP64-scaled one: fixed-point integers
+// and digits, 1 when identical
+int h_split_routes_agree(double u, int32_t e) {
+  const int64_t a = lg::slice_fixed(u, e), b = lg::slice_fixed_int(u, e);
+  if (a != b) return 0;
+  int32_t d[lg::kSlices];
+  lg::slice_digits(a, d);
+  const uint64_t Y = lg::slice_bias(b);
+  for (int i = 0; i < lg::kSlices; ++i)
+    if (lg::slice_digit(b, Y, i) != d[i]) return 0;
+  return 1;
+}
+
+// levels_to_double on (hi, lo, E): returns 1 and the double, or 0 when the
+// integer route declines (subnormal / overflow)
+int h_levels_to_double(int64_t hi, int64_t lo, int E, double* out) { return lg::levels_to_double(hi, lo, E, out) ? 1 : 0; }
+
+// the two epilogue routes on the same levels: FP64 (combine_levels_add) and integer
+void h_combine_both(const int32_t* c, int32_t eu, int32_t ev, double w, double* out2) {
+  out2[0] = lg::combine_levels_add(c, eu, ev, w);
+  out2[1] = lg::combine_levels_add_int(c, eu, ev, w);
+}
 double h_small_int_to_double(int64_t x) { return lg::small_int_to_double(x); }
 int32_t h_slice_exponent(double m) { return lg::slice_exponent(m); }
 }

@@ -3,7 +3,8 @@
 known bit pattern, and the bands must be intact after the call. The L payload
 is pre-filled with the same pattern and must be fully overwritten. Covers the
 one-block and whole-GPU kernels, uniform and ragged batches, split precision
-(packed and in-place product kernels) and the adjoint."""
+(packed and in-place product kernels), the whole-GPU kernel with its
+tensor-core updates and the adjoint."""
 import ctypes
 
 import numpy as np
@@ -41,9 +42,9 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def run_execute(A, precision="fp64", with_ctx=False):
+def run_execute(A, precision="fp64", with_ctx=False, fp64_products="pipe"):
     L = _lib.load()
-    b, o = api._batch(A), api._options(precision=precision)
+    b, o = api._batch(A), api._options(precision=precision, fp64_products=fp64_products)
     v = api._values(A)
     esz = v.element_size()
     out = Banded(v.numel() * esz)
@@ -73,9 +74,12 @@ def ragged(sizes, seed):
     return api.Ragged(vals, torch.tensor(ns, device="cuda"), torch.tensor(offs, device="cuda"), max(sizes))
 
 
-@pytest.mark.parametrize("case", ["uniform48", "uniform300", "ragged_mixed", "uniform64_tf32", "ragged_tf32"])
+@pytest.mark.parametrize("case", ["uniform48", "uniform300", "ragged_mixed", "uniform64_tf32", "ragged_tf32",
+                                  "uniform300_tc", "ragged_mixed_tc"])
 def test_guard_bands_intact(case):
     precision = "tf32x3" if case.endswith("tf32") else "fp64"
+    fp64_products = "tc_sliced" if case.endswith("_tc") else "pipe"
+    case = case[:-3] if case.endswith("_tc") else case
     if case == "uniform48":
         A = torch.tensor(workloads.identity_plus(5, 48, seed=970, lo=0.1, hi=0.9), device="cuda")
     elif case == "uniform300":
@@ -84,7 +88,7 @@ def test_guard_bands_intact(case):
         A = torch.tensor(workloads.identity_plus(6, 64, seed=972, lo=0.1, hi=0.9), device="cuda")
     else:
         A = ragged([33, 300, 7] if case == "ragged_mixed" else [33, 64, 17], seed=973)
-    out, s, k, info, ws, ctx = run_execute(A, precision=precision)
+    out, s, k, info, ws, ctx = run_execute(A, precision=precision, fp64_products=fp64_products)
     check({"L": out, "s": s, "k": k, "info": info, "workspace": ws})
     assert not bool((out.payload() == CANARY).all())
     assert (info.payload().view(torch.int32) == 0).all()

@@ -49,6 +49,11 @@ def h():
     L.h_small_int_to_double.argtypes = [ctypes.c_int64]
     L.h_slice_exponent.restype = ctypes.c_int32
     L.h_slice_exponent.argtypes = [ctypes.c_double]
+    L.h_levels_to_double.restype = ctypes.c_int
+    L.h_levels_to_double.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, p]
+    L.h_combine_both.argtypes = [p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, p]
+    L.h_split_routes_agree.restype = ctypes.c_int
+    L.h_split_routes_agree.argtypes = [ctypes.c_double, ctypes.c_int32]
     return L
 
 
@@ -140,3 +145,62 @@ def test_non_finite_rows_propagate(h):
     v = np.ones(K)
     assert h.h_slice_exponent(np.inf) == h.h_slice_exponent(np.nan)
     assert np.isnan(h.h_sliced_dot(_ptr(u), _ptr(v), K))
+
+
+def _round_exact(x: Fraction) -> float:
+    """The nearest double to a rational (ties to even), for normal results."""
+    return float(x)  # Python rounds Fraction -> float correctly (round-half-even)
+
+
+def test_integer_conversion_rounds_correctly(h):
+    # the epilogue's integer route: (hi 2^32 + lo) 2^E to the nearest double, no FP64 instruction
+    rng = np.random.default_rng(5)
+    out = ctypes.c_double()
+    cases = [(0, 0, 0), (1, 0, -32), (0, 1, 0), (-1, 0, 0), (0, -1, 5), (2 ** 47 - 1, 2 ** 47 - 1, -70),
+             (-(2 ** 47) + 1, 2 ** 47 - 1, -70), (1, -(2 ** 32), 0), (3, 2 ** 31, -3), (2 ** 40, 1, -70)]
+    for _ in range(3000):
+        hi = int(rng.integers(-(2 ** 47), 2 ** 47))
+        lo = int(rng.integers(-(2 ** 47), 2 ** 47))
+        if rng.random() < 0.3:  # near-ties: low bits with a single one
+            lo = (lo & ~((1 << 24) - 1)) | (1 << int(rng.integers(0, 24)))
+        cases.append((hi, lo, int(rng.integers(-200, 200))))
+    for hi, lo, E in cases:
+        ok = h.h_levels_to_double(hi, lo, E, ctypes.byref(out))
+        exact = (Fraction(hi) * 2 ** 32 + lo) * Fraction(2) ** E
+        assert ok == 1
+        assert out.value == _round_exact(exact), (hi, lo, E, out.value, float(exact))
+
+
+def test_integer_conversion_declines_out_of_range(h):
+    out = ctypes.c_double(7.0)
+    assert h.h_levels_to_double(1, 0, -1100, ctypes.byref(out)) == 0 and out.value == 7.0
+    assert h.h_levels_to_double(2 ** 46, 0, 960, ctypes.byref(out)) == 0
+
+
+def test_epilogue_routes_agree(h):
+    # combine_levels_add (FP64 ops) and combine_levels_add_int (integer route + one add)
+    # round T the same way: identical results on level sums within the FP32-exact range
+    rng = np.random.default_rng(6)
+    res = np.zeros(2)
+    for _ in range(2000):
+        c = rng.integers(-(2 ** 22), 2 ** 22 + 1, 8).astype(np.int32)
+        eu, ev = (int(x) for x in rng.integers(-40, 40, 2))
+        w = float(rng.standard_normal() * 2.0 ** rng.integers(-20, 20))
+        h.h_combine_both(_ptr(c), eu, ev, w, _ptr(res))
+        assert res[0] == res[1], (c, eu, ev, w, res)
+
+
+def test_integer_split_matches_scaled_split(h):
+    # the device split runs on integer operations only (fixed point from the
+    # mantissa and exponent bits, digits from one biased integer): the same
+    # integers and digits as the FP64-scaled split with its carry chain
+    rng = np.random.default_rng(7)
+    vals = [0.0, -0.0, 1.0, -1.0, 0.5, 1.5 * 2 ** -60, 5e-324, -3e-310, 1.0 - 2 ** -53, -(1.0 - 2 ** -53)]
+    vals += list(rng.standard_normal(2000) * np.exp(rng.uniform(-80, 80, 2000)))
+    # exact ties of the rounding: a mantissa whose dropped bits are 10...0
+    vals += [float(Fraction(2 ** 52 + 2 * t + 1, 2 ** 52)) * 2.0 ** -70 for t in range(50)]
+    for u in vals:
+        m = abs(u)
+        e0 = h.h_slice_exponent(m) if m > 0 else 0
+        for e in (e0, e0 + 1, e0 + 9, e0 + 70):
+            assert h.h_split_routes_agree(u, e) == 1, (u, e)
