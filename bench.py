@@ -344,6 +344,7 @@ def main():
     st_fa = torch.zeros(4 * count, dtype=torch.int32, device=dev)
     st_fb = torch.zeros(4, dtype=torch.int32, device=dev)
     for name, vopts, vreps in variants:
+        vopts = {**main, **vopts}  # each form changes one option of the FP64 step
         lg.logm_execute(A_dev, **vopts)
         if big:
             lg.logm_execute(B_dev, **vopts)

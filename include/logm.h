@@ -254,7 +254,10 @@ int logm_execute_host(const logm_batch* batch, const logm_options* opts, const v
  * Variants: 0 = 256-thread blocks, 64 x 64 DMMA tiles, any n <= 256;
  *           1 = 128-thread blocks, 32 x 32 tiles, n <= 64 (buckets 0-3);
  *           2 = 64-thread blocks, 32 x 32 tiles, n <= 32 (buckets 0-2);
- *           3 = 256-thread blocks as 0, three per SM (registers capped), any n <= 256.
+ *           3 = 256-thread blocks as 0, three per SM (registers capped), any n <= 256;
+ *           4 = 64-thread blocks as 2 (buckets 0-2) with the working matrices in the
+ *               block's shared memory instead of an L2-resident workspace slot
+ *               (execute only; as many blocks per SM as fit).
  * Smaller configurations keep more small matrices in flight per SM; a
  * uniform batch that variant 1 would run in two rounds of five blocks per SM
  * but that fits one round of seven runs on its 7-per-SM build instead. The

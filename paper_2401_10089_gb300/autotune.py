@@ -22,7 +22,10 @@ import torch
 from . import api
 
 BUCKET_MAX_N = (8, 16, 32, 64, 128, 256)
-CANDIDATES = {0: (0, 1, 2), 1: (0, 1, 2), 2: (0, 1, 2), 3: (0, 1, 3), 4: (0, 3), 5: (0, 3)}
+# configurations: 0 = 256 threads, n <= 256; 1 = 128 threads, n <= 64; 2 = 64 threads,
+# n <= 32; 3 = 256 threads, three blocks per SM; 4 = configuration 2 with the working
+# matrices in shared memory
+CANDIDATES = {0: (0, 1, 2, 4), 1: (0, 1, 2, 4), 2: (0, 1, 2, 4), 3: (0, 1, 3), 4: (0, 3), 5: (0, 3)}
 
 
 def _bucket(n: int) -> int:
@@ -100,7 +103,9 @@ def autotune(A, precision: str = "fp64", sample: int = 4096, reps: int = 3, path
                        "variants": {"0": "256 threads, 64x64 DMMA tiles, n <= 256",
                                     "1": "128 threads, 32x32 tiles, n <= 64",
                                     "2": "64 threads, 32x32 tiles, n <= 32",
-                                    "3": "256 threads, 64x64 tiles, n <= 256, 3 blocks per SM"}}, f, indent=1)
+                                    "3": "256 threads, 64x64 tiles, n <= 256, 3 blocks per SM",
+                                    "4": "64 threads, 32x32 tiles, n <= 32, working matrices in shared memory"}},
+                      f, indent=1)
     return table, times
 
 

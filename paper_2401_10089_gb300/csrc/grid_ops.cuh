@@ -117,8 +117,9 @@ static __device__ void bounded_barrier(unsigned long long* bar, unsigned nblocks
         }
       }
     }
-    __threadfence();
   }
+  // the acquire load that saw every arrival orders thread 0 after the other
+  // blocks' releases; the block barrier orders the other threads after it
   __syncthreads();
 }
 
@@ -364,20 +365,30 @@ struct GridOps {
     const int t_lo = (int)((int64_t)lb * T / G), t_hi = (int)((int64_t)(lb + 1) * T / G);
     for (int kb = 0; kb < n; kb += kSliceK) {
       const int jb = min(kSliceK, n - kb);
-      // digits of A[:, kb..kb+jb) by rows and of B[kb..kb+jb, :] by columns,
-      // eight threads (one per digit slice) per row or column
-      for (int q = tid(); q < 2 * n * kSlices; q += nthreads()) {
-        const int rc = q / kSlices, i = q % kSlices;
-        double u[kSliceK];
-        if (rc < n) {
-          for (int c = 0; c < kSliceK; ++c)
-            u[c] = c < jb ? A[(int64_t)rc * n + kb + c] - (rc == kb + c ? as : 0.0) : 0.0;
-          slice_store_part(u, jb, i, g.sl.adig + (int64_t)rc * kDigK, g.sl.aexp + rc);
-        } else {
-          const int j = rc - n;
-          for (int c = 0; c < kSliceK; ++c)
-            u[c] = c < jb ? B[(int64_t)(kb + c) * n + j] - (kb + c == j ? bs : 0.0) : 0.0;
-          slice_store_part(u, jb, i, g.sl.bdig + (int64_t)j * kDigK, g.sl.bexp + j);
+      // digits of A[:, kb..kb+jb) by rows (rc < n) and of B[kb..kb+jb, :] by
+      // columns (rc - n), eight lanes per row or column, four per warp at a time
+      {
+        const int lane = threadIdx.x & 31, i = lane & 7;
+        const int gw = tid() >> 5, nw = nthreads() >> 5;
+        for (int q4 = gw * 4; q4 < 2 * n; q4 += nw * 4) {
+          const int rc = q4 + (lane >> 3);
+          const bool valid = rc < 2 * n;
+          double u[4];
+          for (int t = 0; t < 4; ++t) {
+            const int c = 4 * i + t;
+            double x = 0.0;
+            if (valid && c < jb) {
+              if (rc < n)
+                x = A[(int64_t)rc * n + kb + c] - (rc == kb + c ? as : 0.0);
+              else
+                x = B[(int64_t)(kb + c) * n + (rc - n)] - (kb + c == rc - n ? bs : 0.0);
+            }
+            u[t] = x;
+          }
+          const bool isa = rc < n;
+          const int64_t row = isa ? rc : rc - n;
+          slice_row8(u[0], u[1], u[2], u[3], i, valid, (isa ? g.sl.adig : g.sl.bdig) + row * kDigK,
+                     (isa ? g.sl.aexp : g.sl.bexp) + row);
         }
       }
       fence_proxy_async_global();
@@ -540,19 +551,24 @@ struct GridOps {
           block_argmax_key(cv, ci, S.red, &pv, &p);
         }
         if (pv == 0 || pv >= 0x7FF0000000000000ull || p < k || p >= n) { status = 1; break; }  // zero, Inf or NaN
-        if (threadIdx.x < jb)
-          S.rowp[threadIdx.x] = g.cand_row[((int64_t)buf * kMaxGrid + p / rows_per) * kGridPanel + threadIdx.x];
-        __syncthreads();
-        // one division per step (thread 0), then the scaled pivot row (one warp)
-        if (threadIdx.x == 0) S.bc[0] = 1.0 / S.rowp[c];
-        __syncthreads();
-        const double inv = S.bc[0];
-        if (threadIdx.x < jb) S.prow[threadIdx.x] = (threadIdx.x == c) ? inv : S.rowp[threadIdx.x] * inv;
-        if (glead) {
-          g.pivval[k] = S.rowp[c];
-          g.piv[k] = p;
+        // warp 0: the winner's row, the reciprocal of the pivot (the same
+        // division in every lane: one warp instruction sequence) and the
+        // scaled pivot row; one block barrier publishes them
+        if (threadIdx.x < 32) {
+          const int t = threadIdx.x;
+          const double rp =
+              t < jb ? g.cand_row[((int64_t)buf * kMaxGrid + p / rows_per) * kGridPanel + t] : 0.0;
+          const double pivot = __shfl_sync(0xffffffffu, rp, c);
+          const double rinv = 1.0 / pivot;
+          if (t < jb) S.prow[t] = (t == c) ? rinv : rp * rinv;
+          if (t == 0) S.bc[0] = rinv;
+          if (glead) {
+            g.pivval[k] = pivot;
+            g.piv[k] = p;
+          }
         }
         __syncthreads();
+        const double inv = S.bc[0];
         unsigned long long cv = 0;
         int ci = 0x7fffffff;
         for (int e = threadIdx.x; e < my_rows * jb; e += kThreads) {
@@ -602,13 +618,17 @@ struct GridOps {
       }
       if (maps) {
         // digits of the update's left factor U = P_f - I_J: this block's rows,
-        // eight threads (one per digit slice) per row
-        for (int q = threadIdx.x; q < my_rows * kSlices; q += kThreads) {
-          const int rr = q / kSlices, r = r_lo + rr;
-          double u[kSliceK];
-          for (int c = 0; c < kSliceK; ++c)
-            u[c] = c < jb ? Sf[rr * kGridPanel + c] - (r == kb + c ? 1.0 : 0.0) : 0.0;
-          slice_store_part(u, jb, q % kSlices, g.sl.adig + (int64_t)r * kDigK, g.sl.aexp + r);
+        // eight lanes per row (four rows per warp at a time)
+        const int lane = threadIdx.x & 31, i = lane & 7, wq = threadIdx.x >> 5;
+        for (int r4 = wq * 4; r4 < my_rows; r4 += kThreads / 8) {
+          const int rr = r4 + (lane >> 3), r = r_lo + rr;
+          const bool valid = rr < my_rows;
+          double u[4];
+          for (int t = 0; t < 4; ++t) {
+            const int c = 4 * i + t;
+            u[t] = (valid && c < jb) ? Sf[rr * kGridPanel + c] - (r == kb + c ? 1.0 : 0.0) : 0.0;
+          }
+          slice_row8(u[0], u[1], u[2], u[3], i, valid, g.sl.adig + (int64_t)r * kDigK, g.sl.aexp + r);
         }
       }
       if (!maps) {
@@ -644,11 +664,12 @@ struct GridOps {
               }
             }
           __syncwarp();
-          if (valid) {
-            double v[kSliceK];
-            for (int c = 0; c < kSliceK; ++c) v[c] = c < jb ? W[(int64_t)(kb + c) * n + j] : 0.0;
-            slice_store_part(v, jb, i, g.sl.bdig + (int64_t)j * kDigK, g.sl.bexp + j);
+          double v[4];
+          for (int t = 0; t < 4; ++t) {
+            const int c = 4 * i + t;
+            v[t] = (valid && c < jb) ? W[(int64_t)(kb + c) * n + j] : 0.0;
           }
+          slice_row8(v[0], v[1], v[2], v[3], i, valid, g.sl.bdig + (int64_t)j * kDigK, g.sl.bexp + j);
           __syncwarp();
         }
         fence_proxy_async_global();  // the digits are read by TMA after the barrier

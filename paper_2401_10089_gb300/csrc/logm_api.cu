@@ -30,8 +30,8 @@ namespace {
 
 // Kernel configuration per size bucket (logm_set_tuning).
 int g_variant[lg::kBuckets] = {0, 0, 0, 0, 0, 0};
-constexpr int kVariants = 4;  // tunable configurations; configuration 1's 7-per-SM twin is picked by batch size
-constexpr int kVariantMaxBucket[kVariants] = {5, 3, 2, 5};  // largest bucket each configuration serves
+constexpr int kVariants = 5;  // tunable configurations; configuration 1's 7-per-SM twin is picked by batch size
+constexpr int kVariantMaxBucket[kVariants] = {5, 3, 2, 5, 2};  // largest bucket each configuration serves
 
 size_t small_slots_bytes_all_variants(int count, int small_nmax) {
   size_t m = lg::small_workspace_bytes(count, small_nmax);
@@ -39,6 +39,8 @@ size_t small_slots_bytes_all_variants(int count, int small_nmax) {
   const size_t m2 = lg_v2::small_workspace_bytes(count, small_nmax < 32 ? small_nmax : 32);
   const size_t m3 = lg_v3::small_workspace_bytes(count, small_nmax);
   const size_t m4 = lg_v4::small_workspace_bytes(count, small_nmax < 64 ? small_nmax : 64);
+  const size_t m5 = lg_v5::small_workspace_bytes(count, small_nmax < 32 ? small_nmax : 32);
+  if (m5 > m) m = m5;
   if (m4 > m) m = m4;
   if (m1 > m) m = m1;
   if (m2 > m) m = m2;
@@ -167,7 +169,7 @@ void fill_common(lg::SmallParams& p, const logm_batch* b, const logm_options* o)
 cudaError_t launch_small_variants(lg::Mode mode, const lg::SmallParams& q, int small_nmax, int count,
                                   cudaStream_t st) {
   const bool tuned = mode == lg::kModeExecute || mode == lg::kModeBackward;
-  int mask[kVariants] = {0, 0, 0, 0};
+  int mask[kVariants] = {0, 0, 0, 0, 0};
   const int top = lg::size_bucket(small_nmax);
   // a uniform batch fills one bucket: only its configuration is launched
   const int lo = q.n_uniform > 0 ? top : 0;
@@ -176,7 +178,7 @@ cudaError_t launch_small_variants(lg::Mode mode, const lg::SmallParams& q, int s
   if (lo > 0 && mask[0]) mask[0] = 0;  // configuration 0 holds the only bucket: no filter
   for (int v = kVariants - 1; v >= 0; --v) {
     if (v > 0 && !mask[v]) continue;
-    if (v == 0 && !mask[0] && (mask[1] || mask[2] || mask[3])) continue;
+    if (v == 0 && !mask[0] && (mask[1] || mask[2] || mask[3] || mask[4])) continue;
     lg::SmallParams r = q;
     r.bucket_mask = mask[v];
     cudaError_t e;
@@ -197,6 +199,10 @@ cudaError_t launch_small_variants(lg::Mode mode, const lg::SmallParams& q, int s
       r.n_max = q.n_max < 32 ? q.n_max : 32;
       r.n_slots = lg_v2::small_kernel_slots(count);
       e = lg_v2::launch_small(mode, r, st);
+    } else if (v == 4) {
+      r.n_max = q.n_max < 32 ? q.n_max : 32;
+      r.n_slots = lg_v5::small_kernel_slots(count);  // execute sizes its grid by occupancy
+      e = lg_v5::launch_small(mode, r, st);
     } else {
       r.n_slots = lg_v3::small_kernel_slots(count);
       e = lg_v3::launch_small(mode, r, st);
@@ -357,8 +363,10 @@ size_t logm_backward_workspace_size(const logm_batch* batch, const logm_options*
   const size_t m2 = lg_v2::small_bwd_workspace_bytes(batch->count, n_max < 32 ? n_max : 32);
   const size_t m3 = lg_v3::small_bwd_workspace_bytes(batch->count, n_max);
   const size_t m4 = lg_v4::small_bwd_workspace_bytes(batch->count, n_max < 64 ? n_max : 64);
+  const size_t m5 = lg_v5::small_bwd_workspace_bytes(batch->count, n_max < 32 ? n_max : 32);
   size_t r = m > m1 ? m : m1;
   r = r > m4 ? r : m4;
+  r = r > m5 ? r : m5;
   r = r > m2 ? r : m2;
   return r > m3 ? r : m3;
 }

@@ -167,6 +167,14 @@ size_t small_bwd_workspace_bytes(int count, int n_max);
 size_t small_workspace_bytes(int count, int n_max);
 cudaError_t launch_small(lg::Mode mode, const lg::SmallParams& p, cudaStream_t stream);
 }  // namespace lg_v3
+// lg_v5 = lg_v2 with the execute mode's working matrices in shared memory.
+namespace lg_v5 {
+constexpr int kVariantMaxN = 32;
+int small_kernel_slots(int count);
+size_t small_bwd_workspace_bytes(int count, int n_max);
+size_t small_workspace_bytes(int count, int n_max);
+cudaError_t launch_small(lg::Mode mode, const lg::SmallParams& p, cudaStream_t stream);
+}  // namespace lg_v5
 // lg_v4 = lg_v1 with seven blocks per SM (one round for uniform batches of
 // 5..7 matrices per SM).
 namespace lg_v4 {

@@ -5,7 +5,8 @@
 // iterations, estimator sweeps) runs on the device with no host round trip.
 //
 // Per block, the working matrices live in a workspace slot of kSlotMats
-// n_max x n_max FP64 buffers (L2-resident):
+// n_max x n_max FP64 buffers (L2-resident; with LG_SMEM_SLOTS the execute
+// mode keeps them in the block's shared memory instead):
 //   Acur  current A (the Denman-Beavers X in place), later P_2 = X = I - A
 //   A2    saved A_2, then A_I2 = A_2 - 2A + I (eq. AI2) = P_3
 //   Y     Denman-Beavers Y, later P_4
@@ -18,7 +19,19 @@
 #include "block_ops.cuh"
 #include "logm_algo.cuh"
 
+#ifndef LG_SMEM_SLOTS
+#define LG_SMEM_SLOTS 0
+#endif
+
 namespace LG_NS {
+
+// Byte offset of the shared-memory slot after the block's BlockSmem.
+constexpr size_t kSmemSlotOffset = (sizeof(BlockSmem) + 255) / 256 * 256;
+// Shared-memory slot mode: execute keeps its slot in shared memory.
+template <int MODE>
+__host__ __device__ constexpr bool smem_slot() {
+  return LG_SMEM_SLOTS && MODE == kModeExecute;
+}
 
 // ---------------------------------------------------------------------------
 // Queue order for execute: longest work first. The cost of a matrix grows
@@ -94,7 +107,8 @@ __global__ void __launch_bounds__(kThreads, LG_MINBLOCKS) k_logm_small(SmallPara
   BlockOps ops{S};
   const int64_t nn_max = (int64_t)p.n_max * p.n_max;
   const int mats = (MODE == kModeBackward) ? kBwdSlotMats : kSlotMats;
-  double* base = p.slots + (int64_t)blockIdx.x * mats * nn_max;
+  double* base = smem_slot<MODE>() ? reinterpret_cast<double*>(smem_raw + kSmemSlotOffset)
+                                   : p.slots + (int64_t)blockIdx.x * mats * nn_max;
   Slot M{base, base + nn_max, base + 2 * nn_max, base + 3 * nn_max,
          base + 4 * nn_max, base + 5 * nn_max, base + 6 * nn_max};
   BwdSlot W;
@@ -186,11 +200,27 @@ size_t small_workspace_bytes(int count, int n_max) {
 template <int MODE>
 static cudaError_t launch_mode(const SmallParams& p, cudaStream_t st) {
   static lg::DeviceOnce attr;
-  const size_t smem = sizeof(BlockSmem);
+  // shared memory: BlockSmem, plus the slot's kSlotMats matrices in the
+  // shared-memory slot mode (the attribute allows the configuration's largest n)
+  const size_t smem_cap = smem_slot<MODE>() ? kSmemSlotOffset + sizeof(double) * kSlotMats * kMaxN * kMaxN
+                                            : sizeof(BlockSmem);
+  const size_t smem = smem_slot<MODE>()
+                          ? kSmemSlotOffset + sizeof(double) * kSlotMats * (size_t)p.n_max * p.n_max
+                          : sizeof(BlockSmem);
   cudaError_t e = attr.run([&] {
-    return cudaFuncSetAttribute(k_logm_small<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_logm_small<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap);
   });
   if (e != cudaSuccess) return e;
+  SmallParams q = p;
+  if (smem_slot<MODE>()) {
+    // as many persistent blocks as fit with this n_max's slot (no workspace slots)
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_logm_small<MODE>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    const int cap = per_sm * lg::device_sm_count();
+    q.n_slots = p.count < cap ? p.count : cap;
+  }
   e = cudaMemsetAsync(p.queue, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   if (MODE == kModeExecute && p.order && p.order_aux && p.count > 1) {
@@ -201,7 +231,6 @@ static cudaError_t launch_mode(const SmallParams& p, cudaStream_t st) {
     k_order_scan<<<1, 32, 0, st>>>(p);
     k_order_scatter<<<(p.count + kThreads - 1) / kThreads, kThreads, 0, st>>>(p);
   }
-  SmallParams q = p;
   if (!(MODE == kModeExecute && p.count > 1)) q.order = nullptr;
   k_logm_small<MODE><<<q.n_slots, kThreads, smem, st>>>(q);
   return cudaGetLastError();

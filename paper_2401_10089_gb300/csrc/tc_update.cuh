@@ -14,11 +14,11 @@
 //     region of 64 columns (8 levels = all 512 columns). Every level sum is an
 //     integer below 2^22, so the FP32 accumulation is exact;
 //   * all eight warps read the levels back (tcgen05.ld), combine them into the
-//     exact integer dot product and round it to FP64 with integer operations
-//     into a shared-memory tile; the next tile's MMAs start as soon as TMEM is
+//     exact integer dot product and round it to FP64 (integer operations and
+//     three FP64 instructions) into a shared-memory tile; the next tile's MMAs start as soon as TMEM is
 //     read, while the warps add the staged tile to W row by row (coalesced).
-// Per element and panel that is one FP64 instruction (the addition) instead
-// of 32 FP64 FMAs.
+// Per element and panel that is four FP64 instructions (the conversion and
+// the addition) instead of 32 FP64 FMAs.
 //
 // Every mbarrier wait is bounded (kTmWaitLimit polls); a wait that runs out
 // sets the grid's error word, and the kernel reports LOGM_INFO_TIMEOUT for the
@@ -65,33 +65,42 @@ struct SliceSmem {
   int32_t ecol[kUpdN];        // scale exponents of the current tile's columns of V
 };
 
-// Digit slice i of 32 values (the first `count` given, the rest zero): the
-// 32 BF16 at out[32 i .. 32 i + 31] of a row of kDigK; slice 0 also stores
-// the scale exponent at *eo. Eight threads, one per slice, split a row
-// between them (each forms the row's scale itself). Integer operations only.
-static __device__ __noinline__ void slice_store_part(const double* v, int count, int i, __nv_bfloat16* out,
-                                                     int32_t* eo) {
-  double m = 0.0;
-  for (int k = 0; k < count; ++k) {
-    const double a = fabs(v[k]);
-    if (!(a <= m)) m = a;  // NaN wins
+// The digits of one row of 32 values split among the 8 lanes of an aligned
+// lane group (lanes 8q .. 8q + 7 of a warp): lane i holds the values
+// k = 4 i .. 4 i + 3 (zero past the row's length) in v0..v3. The group forms the
+// row's scale exponent (the largest magnitude by integer comparison of the
+// bit patterns: NaN above Inf above every finite value), each lane the
+// fixed-point integers and all eight digits of its four values, and writes
+// them as eight 8-byte pieces of the row of kDigK BF16 at out (digit s of
+// value k at out[32 s + k]); lane 0 stores the exponent at *eo. Every lane
+// of the warp must call this (the shuffles); `valid` lanes store.
+static __device__ __noinline__ void slice_row8(double v0, double v1, double v2, double v3, int i, bool valid,
+                                               __nv_bfloat16* out, int32_t* eo) {
+  const double v[4] = {v0, v1, v2, v3};
+  unsigned long long mb = 0;
+  for (int t = 0; t < 4; ++t) {
+    const unsigned long long a = lg_dbits(v[t]) & 0x7FFFFFFFFFFFFFFFull;
+    mb = a > mb ? a : mb;
   }
-  const int32_t e = slice_exponent(m);
-  if (i == 0) *eo = e;
-  uint32_t pk[kSliceK / 2];
-  for (int k = 0; k < kSliceK; k += 2) {
-    int32_t d[2];
-    for (int h = 0; h < 2; ++h) {
-      const int kk = k + h;
-      const int64_t X = (kk < count && e != kSliceNonFinite) ? slice_fixed_int(v[kk], e) : 0;
-      d[h] = slice_digit(X, slice_bias(X), i);
-    }
+  for (int x = 1; x < 8; x <<= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, mb, x);
+    mb = o > mb ? o : mb;
+  }
+  const int32_t e = slice_exponent(lg_bitsd(mb));
+  if (valid && i == 0) *eo = e;
+  int64_t X[4];
+  uint64_t Y[4];
+  for (int t = 0; t < 4; ++t) {
+    X[t] = e != kSliceNonFinite ? slice_fixed_int(v[t], e) : 0;
+    Y[t] = slice_bias(X[t]);
+  }
+  if (!valid) return;
+  for (int sl = 0; sl < kSlices; ++sl) {
+    uint32_t b[4];
     // |d| <= 128 has at most 8 significant bits: the BF16 is the FP32's top half
-    pk[k / 2] = (__float_as_uint(static_cast<float>(d[0])) >> 16) |
-                (__float_as_uint(static_cast<float>(d[1])) & 0xFFFF0000u);
+    for (int t = 0; t < 4; ++t) b[t] = __float_as_uint(static_cast<float>(slice_digit(X[t], Y[t], sl))) >> 16;
+    *reinterpret_cast<uint2*>(out + kSliceK * sl + 4 * i) = make_uint2(b[0] | (b[1] << 16), b[2] | (b[3] << 16));
   }
-  uint4* o = reinterpret_cast<uint4*>(out) + i * 4;
-  for (int q = 0; q < 4; ++q) o[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
 }
 
 // Generic-proxy writes (the digits) made visible to later TMA reads.
@@ -209,13 +218,28 @@ static __device__ __noinline__ void sliced_update(SliceSmem& sm, unsigned char* 
         for (int e = 0; e < 8; ++e) {
           int32_t c[kSliceLevels];
           for (int L = 0; L < kSliceLevels; ++L) c[L] = level_int(__uint_as_float(v[L][e]));
-          Ts[lrow * kUpdTsStride + cc + e] = combine_levels_int(c, er, sm.ecol[cc + e]);
+          Ts[lrow * kUpdTsStride + cc + e] = combine_levels_fp(c, er, sm.ecol[cc + e]);
         }
       }
     }
     tm_fence_before();
     __syncthreads();  // TMEM read, Ts complete
-    // the next tile's MMAs overlap the additions below
+    // W += Ts: warp w takes rows w, w + 8, ..., lanes along the row
+    // (coalesced). All 32 loads of a thread are issued before any store, so
+    // their latencies overlap (the compiler may not move a load above a store
+    // to memory it cannot prove distinct); the next tile's MMAs are issued
+    // while these loads are in flight.
+    constexpr int kPer = (kUpdM / 8) * 2;  // 16 rows x 2 column halves per thread
+    double wv[kPer];
+    if (acc_ok) {
+#pragma unroll
+      for (int it = 0; it < kPer; ++it) {
+        const int rr = warp + 8 * (it >> 1), c = lane + 32 * (it & 1);
+        const int gr = r0 + rr, gc = c0 + c;
+        const bool ok = gr < n && gc < n && (gc < kb || gc >= kb + jb);
+        wv[it] = ok ? __ldcg(W + (int64_t)gr * n + gc) : 0.0;
+      }
+    }
     if (has_next) {
       if (tid == 32 && sm.failed == 0 &&
           !tile_mmas(tmem, sA, sB[st ^ 1], barA, next_new_a, phA, barB[st ^ 1], phB[st ^ 1], barAcc))
@@ -224,20 +248,7 @@ static __device__ __noinline__ void sliced_update(SliceSmem& sm, unsigned char* 
       ++phB[st ^ 1];
       ++isAcc;
     }
-    // W += Ts: warp w takes rows w, w + 8, ..., lanes along the row
-    // (coalesced). All 32 loads of a thread are issued before any store, so
-    // their latencies overlap (the compiler may not move a load above a store
-    // to memory it cannot prove distinct).
     if (acc_ok) {
-      constexpr int kPer = (kUpdM / 8) * 2;  // 16 rows x 2 column halves per thread
-      double wv[kPer];
-#pragma unroll
-      for (int it = 0; it < kPer; ++it) {
-        const int rr = warp + 8 * (it >> 1), c = lane + 32 * (it & 1);
-        const int gr = r0 + rr, gc = c0 + c;
-        const bool ok = gr < n && gc < n && (gc < kb || gc >= kb + jb);
-        wv[it] = ok ? __ldcg(W + (int64_t)gr * n + gc) : 0.0;
-      }
 #pragma unroll
       for (int it = 0; it < kPer; ++it) {
         const int rr = warp + 8 * (it >> 1), c = lane + 32 * (it & 1);

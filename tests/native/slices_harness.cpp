@@ -46,6 +46,7 @@ double h_sliced_dot(const double* u, const double* v, int k) {
 }
 
 int32_t h_level_int(float v) { return lg::level_int(v); }
+double h_exact_int_to_double(int64_t x) { return lg::exact_int_to_double(x); }
 
 // the integer-only split against the FP64-scaled one: fixed-point integers
 // and digits, 1 when identical
@@ -64,10 +65,23 @@ int h_split_routes_agree(double u, int32_t e) {
 // integer route declines (subnormal / overflow)
 int h_levels_to_double(int64_t hi, int64_t lo, int E, double* out) { return lg::levels_to_double(hi, lo, E, out) ? 1 : 0; }
 
+// the 32-bit conversion against the 128-bit one on the same levels: 1 if both
+// give the same result (or both refuse)
+int h_levels32_agree(const int32_t* c, int E) {
+  int64_t hi, lo;
+  lg::level_halves(c, &hi, &lo);
+  double a = 0.0, b = 0.0;
+  const bool ra = lg::levels_to_double(hi, lo, E, &a), rb = lg::levels_to_double32(c, E, &b);
+  if (ra != rb) return 0;
+  return (!ra || a == b) ? 1 : 0;
+}
+
 // the two epilogue routes on the same levels: FP64 (combine_levels_add) and integer
 void h_combine_both(const int32_t* c, int32_t eu, int32_t ev, double w, double* out2) {
   out2[0] = lg::combine_levels_add(c, eu, ev, w);
   out2[1] = lg::combine_levels_add_int(c, eu, ev, w);
+  if (lg::combine_levels_int32(c, eu, ev) != lg::combine_levels_int(c, eu, ev)) out2[1] = -out2[1] - 1.0;
+  if (lg::combine_levels_fp(c, eu, ev) != lg::combine_levels_int(c, eu, ev)) out2[1] = -out2[1] - 2.0;
 }
 double h_small_int_to_double(int64_t x) { return lg::small_int_to_double(x); }
 int32_t h_slice_exponent(double m) { return lg::slice_exponent(m); }

@@ -24,10 +24,10 @@ def test_size_buckets_match_the_library():
     assert [_bucket(n) for n in (1, 8, 9, 16, 17, 32, 33, 64, 65, 128, 129, 256)] == \
         [0, 0, 1, 1, 2, 2, 3, 3, 4, 4, 5, 5]
     assert BUCKET_MAX_N == (8, 16, 32, 64, 128, 256)
-    # every candidate configuration can serve its bucket (1: n <= 64, 2: n <= 32)
+    # every candidate configuration can serve its bucket (1: n <= 64, 2 and 4: n <= 32)
     for b, cands in CANDIDATES.items():
         for v in cands:
-            assert v in (0, 3) or (v == 1 and b <= 3) or (v == 2 and b <= 2)
+            assert v in (0, 3) or (v == 1 and b <= 3) or (v in (2, 4) and b <= 2)
 
 
 def test_shipped_tuning_table_installs_and_bad_tables_are_refused():

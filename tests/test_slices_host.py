@@ -52,6 +52,10 @@ def h():
     L.h_levels_to_double.restype = ctypes.c_int
     L.h_levels_to_double.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, p]
     L.h_combine_both.argtypes = [p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, p]
+    L.h_exact_int_to_double.restype = ctypes.c_double
+    L.h_exact_int_to_double.argtypes = [ctypes.c_int64]
+    L.h_levels32_agree.restype = ctypes.c_int
+    L.h_levels32_agree.argtypes = [p, ctypes.c_int]
     L.h_split_routes_agree.restype = ctypes.c_int
     L.h_split_routes_agree.argtypes = [ctypes.c_double, ctypes.c_int32]
     return L
@@ -204,3 +208,36 @@ def test_integer_split_matches_scaled_split(h):
         e0 = h.h_slice_exponent(m) if m > 0 else 0
         for e in (e0, e0 + 1, e0 + 9, e0 + 70):
             assert h.h_split_routes_agree(u, e) == 1, (u, e)
+
+
+def test_32bit_conversion_matches_the_exact_one(h):
+    # the epilogue's branch-free 32-bit conversion of the eight level sums
+    # against the 128-bit one (itself pinned to exact rationals above)
+    rng = np.random.default_rng(8)
+    lim = 2 ** 22
+    cases = [np.zeros(8), np.full(8, lim), np.full(8, -lim), np.array([0] * 7 + [1]), np.array([0] * 7 + [-1]),
+             np.array([1] + [0] * 7), np.array([-1] + [0] * 7), np.array([lim, -lim, lim, -lim, lim, -lim, lim, -lim]),
+             np.array([0, 0, 0, 0, 0, 0, 1, -256]), np.array([0, 0, 1, 0, 0, 0, 0, 0])]
+    for _ in range(20000):
+        c = rng.integers(-lim, lim + 1, 8)
+        z = rng.random(8) < rng.random()  # leading levels zero: small T, every normalisation case
+        c[np.cumsum(~z) == 0] = 0
+        if rng.random() < 0.2:  # near ties of the rounding
+            c[-3:] = rng.integers(-2, 3, 3)
+        cases.append(c)
+    for c in cases:
+        c = np.ascontiguousarray(c, dtype=np.int32)
+        for E in (-70, -200, 0, 37):
+            assert h.h_levels32_agree(_ptr(c), E) == 1, (c.tolist(), E)
+    for E in (-1100, -1030, 990, 1000):  # results out of the normal range: both refuse alike
+        c = np.full(8, 3, dtype=np.int32)
+        assert h.h_levels32_agree(_ptr(c), E) == 1
+
+
+def test_exact_int_to_double(h):
+    rng = np.random.default_rng(9)
+    xs = [0, 1, -1, 2 ** 52, -(2 ** 52), 2 ** 53 - 1, -(2 ** 53 - 1), 3, 2 ** 47 + 5]
+    xs += [int(v) for v in rng.integers(-(2 ** 53) + 1, 2 ** 53, 5000)]
+    xs += [int(v) >> int(s) for v, s in zip(rng.integers(-(2 ** 53) + 1, 2 ** 53, 2000), rng.integers(0, 53, 2000))]
+    for x in xs:
+        assert h.h_exact_int_to_double(x) == float(x), x
