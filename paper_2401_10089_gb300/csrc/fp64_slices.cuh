@@ -162,6 +162,15 @@ LG_HD int32_t level_int(float v) {
   return static_cast<int32_t>(lg_fbits(v + 12582912.0f)) - 0x4B400000;
 }
 
+// Integer value of an FP32 level sum accumulated over up to four chunks of
+// 32 terms (an exact integer, |v| <= 2^24): split as v = h 2^12 + l with
+// |h| <= 2^12 and |l| <= 2^11, each converted by the magic-number addition.
+LG_HD int32_t level_int_wide(float v) {
+  const float hf = (v * 2.44140625e-4f + 12582912.0f) - 12582912.0f;  // rint(v 2^-12), exact
+  const float lf = fmaf(-hf, 4096.0f, v);                              // exact remainder
+  return level_int(hf) * 4096 + level_int(lf);
+}
+
 // Exact integer T = sum_L C_L 256^(kSlices + 1 - L) as two halves,
 // T = hi 2^32 + lo, from the kSlices level sums c[0] (L = 2) .. c[kSlices-1].
 LG_HD void level_halves(const int32_t* c, int64_t* hi, int64_t* lo) {

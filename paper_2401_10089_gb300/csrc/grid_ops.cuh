@@ -23,6 +23,8 @@
 namespace lg {
 
 constexpr int kGridPanel = 32;          // Gauss-Jordan panel width for large n
+constexpr int kSuperCols = kMaxChunks * kGridPanel;  // tensor-core form: columns of a super-panel
+static_assert(kGridPanel == kSliceK, "a panel is one chunk of the tensor-core updates");
 constexpr int kColGroups = 16;          // row groups of the column passes (norms, transposed mat-vecs, updates)
 constexpr int kMaxGrid = 1024;          // upper bound on co-resident blocks
 constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s
@@ -43,7 +45,9 @@ struct GjGroup {
   int* perm;         // [n_max] composite column permutation
   double* work;      // [n_max^2] working matrix
   double* result;    // [2] log|det|, status
-  SliceBufs sl;      // tensor-core updates: digits of the panel's factors
+  SliceBufs sl;      // tensor-core updates: digits of the factors
+  double* ucat;      // [n_max][kSuperCols] tensor-core form: the factors U_q of a super-panel's sub-panels
+  double* vcat;      // [n_max][kSuperCols] tensor-core form: their pivot rows v_q, by column
   int gi;            // index of this group (its tensor maps)
 };
 
@@ -60,7 +64,6 @@ struct GridWs {
 };
 
 struct GridSmem {
-  GemmSmem gemm;
   Reduce red;
   double rowk[kGridPanel];
   double rowp[kGridPanel];
@@ -71,10 +74,27 @@ struct GridSmem {
   int winner;                // block holding the pivot candidate of the current column
   SliceSmem slc;             // tensor-core updates: barriers, phases, TMEM base
   int skip_upd;              // the grid's error word was set: no more tensor-core work
+  int psrc[2 * kGridPanel];  // rows traced back through a panel's swaps
+  int ppos[2 * kGridPanel];  // the positions they move to
 };
 
-// Dynamic shared memory of the whole-GPU kernel: this block's rows of the
-// current Gauss-Jordan panel, row-major, two buffers of rows_cap x kGridPanel.
+// Geometry of one Gauss-Jordan inversion on a group of G blocks: this block's
+// index in the group (lb), its thread index in the group (gt of gnt), its rows
+// [r_lo, r_hi) of rows_per, its two panel buffers in shared memory, and the
+// group's barrier counter and this block's episode count of it.
+struct GjCtx {
+  int lb, gt, gnt, G, rows_per, r_lo, r_hi, my_rows;
+  double* Sp0;
+  double* Sp1;
+  unsigned long long* bar;
+  unsigned long long* ep;
+};
+
+// Dynamic shared memory of the whole-GPU kernel, used by one phase at a time:
+// this block's rows of the current Gauss-Jordan panel (row-major, two buffers
+// of rows_per x kGridPanel) and, in the tensor-core form, the transposed rows
+// of the earlier sub-panels' factors after them; the stage ring and staged
+// tile of the tensor-core updates; the DMMA tiles of the FP64-pipe products.
 extern __shared__ double grid_panel_smem[];
 
 static __device__ __forceinline__ unsigned long long global_ns() {
@@ -133,6 +153,7 @@ struct GridOps {
   __device__ int nthreads() const { return gridDim.x * blockDim.x; }
   __device__ void sync() { bounded_barrier(w.bar, gridDim.x, w.err, &S.ep[0]); }
   __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
+  __device__ GemmSmem& gsm() const { return *reinterpret_cast<GemmSmem*>(grid_panel_smem); }
 
   __device__ double sum(double v) {
     const double bs = block_sum(v, S.red);
@@ -344,12 +365,12 @@ struct GridOps {
     }
     const int tiles = (n + kTileM - 1) / kTileM;
     for (int t = blockIdx.x; t < tiles * tiles; t += gridDim.x)
-      gemm_tile(n, (t / tiles) * kTileM, (t % tiles) * kTileN, A, as, B, bs, alpha, e, out, S.gemm, ta, tb);
+      gemm_tile(n, (t / tiles) * kTileM, (t % tiles) * kTileN, A, as, B, bs, alpha, e, out, gsm(), ta, tb);
     sync();
   }
 
   // out = alpha (A - as I)(B - bs I) + sum_t e.c[t] e.M[t] on the tensor cores:
-  // K in chunks of 32, each chunk's rank-32 product formed exactly from BF16
+  // K in chunks of kSuperCols, each chunk's product formed exactly from BF16
   // digits (tc_update.cuh, per-row scales of the chunk of A, per-column scales
   // of the chunk of B) and added to an FP64 accumulator, then the epilogue
   // terms. Uses group 0's digit buffers and working matrix (free outside the
@@ -360,11 +381,12 @@ struct GridOps {
     double* C = g.work;
     const int64_t nn = (int64_t)n * n;
     for (int64_t t = tid(); t < nn; t += nthreads()) C[t] = 0.0;
-    const int T = ((n + kUpdM - 1) / kUpdM) * ((n + kUpdN - 1) / kUpdN);
+    const int ncb = (n + kUpdN - 1) / kUpdN;
+    const int T = ((n + kUpdM - 1) / kUpdM) * ncb;
     const int G = gridDim.x, lb = blockIdx.x;
     const int t_lo = (int)((int64_t)lb * T / G), t_hi = (int)((int64_t)(lb + 1) * T / G);
-    for (int kb = 0; kb < n; kb += kSliceK) {
-      const int jb = min(kSliceK, n - kb);
+    for (int kb = 0; kb < n; kb += kSuperCols) {
+      const int jb = min(kSuperCols, n - kb), nc = (jb + kSliceK - 1) / kSliceK;
       // digits of A[:, kb..kb+jb) by rows (rc < n) and of B[kb..kb+jb, :] by
       // columns (rc - n), eight lanes per row or column, four per warp at a time
       {
@@ -372,32 +394,36 @@ struct GridOps {
         const int gw = tid() >> 5, nw = nthreads() >> 5;
         for (int q4 = gw * 4; q4 < 2 * n; q4 += nw * 4) {
           const int rc = q4 + (lane >> 3);
-          const bool valid = rc < 2 * n;
-          double u[4];
-          for (int t = 0; t < 4; ++t) {
-            const int c = 4 * i + t;
-            double x = 0.0;
-            if (valid && c < jb) {
-              if (rc < n)
-                x = A[(int64_t)rc * n + kb + c] - (rc == kb + c ? as : 0.0);
-              else
-                x = B[(int64_t)(kb + c) * n + (rc - n)] - (kb + c == rc - n ? bs : 0.0);
+          const bool valid = rc < 2 * n, isa = rc < n;
+          double u[4 * kMaxChunks];
+#pragma unroll
+          for (int c = 0; c < kMaxChunks; ++c)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const int kk = kSliceK * c + 4 * i + t;
+              double x = 0.0;
+              if (valid && kk < jb) {
+                if (isa)
+                  x = A[(int64_t)rc * n + kb + kk] - (rc == kb + kk ? as : 0.0);
+                else
+                  x = B[(int64_t)(kb + kk) * n + (rc - n)] - (kb + kk == rc - n ? bs : 0.0);
+              }
+              u[4 * c + t] = x;
             }
-            u[t] = x;
-          }
-          const bool isa = rc < n;
-          const int64_t row = isa ? rc : rc - n;
-          slice_row8(u[0], u[1], u[2], u[3], i, valid, (isa ? g.sl.adig : g.sl.bdig) + row * kDigK,
-                     (isa ? g.sl.aexp : g.sl.bexp) + row);
+          const int64_t row = !valid ? 0 : isa ? rc : rc - n;
+          slice_row8<kMaxChunks>(u, i, valid, nc, (isa ? g.sl.adig : g.sl.bdig) + row * kDigRow,
+                                 (isa ? g.sl.aexp : g.sl.bexp) + row);
         }
       }
       fence_proxy_async_global();
       sync();
       if (threadIdx.x == 0) S.skip_upd = *(volatile int*)w.err;
       __syncthreads();
-      if (!S.skip_upd)
+      if (!S.skip_upd) {
+        const UpdTiles ut{nc, 0, ncb, 1 << 30, 0, 0, 0};
         sliced_update(S.slc, reinterpret_cast<unsigned char*>(grid_panel_smem), &maps->a[0], &maps->b[0], g.sl, C, n,
-                      0, 0, t_lo, t_hi, w.err);
+                      ut, t_lo, t_hi, w.err);
+      }
       sync();
     }
     for (int64_t t = tid(); t < nn; t += nthreads()) {
@@ -421,7 +447,7 @@ struct GridOps {
   // W[r0.., c0..] (64 x 64 tile) += (Pf - I_J)[r0.., 0..jb) R[0..jb), c0..], columns of J skipped.
   __device__ void rank_update_tile(double* W, int n, int kb, int jb, const double* Pf, const double* R, int r0,
                                    int c0) {
-    GemmSmem& sm = S.gemm;
+    GemmSmem& sm = gsm();
     const int tid_ = threadIdx.x, lane = tid_ & 31, warp = tid_ >> 5;
     const int wm = warp >> 1, wn = warp & 1;
     const int g = lane >> 2, q = lane & 3;
@@ -484,177 +510,279 @@ struct GridOps {
   // for the next column together with that candidate's panel row. Writes
   // log|det| and the status (0, or 1 for a zero / non-finite pivot) to
   // g.result.
-  __device__ void inverse_group(GjGroup& g, int g0, int gn, unsigned long long* bar, unsigned long long* ep,
-                                const double* src, double* dst, int n) {
-    const int lb = blockIdx.x - g0;
-    const int gt = lb * kThreads + threadIdx.x, gnt = gn * kThreads;
+  // One Gauss-Jordan panel (columns [kb, kb + jb)) on the group: the block's
+  // rows of W[:, J] into shared memory, then jb column steps (pivot search
+  // over the group's candidates, scaled pivot row, elimination of the panel's
+  // rows, the next column's candidates), one group barrier each. The finished
+  // panel (this block's rows) is left in x.Sp1 if jb is odd, else x.Sp0; the
+  // pivots in g.piv and g.pivval. Returns 1 for a zero or non-finite pivot.
+  __device__ __noinline__ int panel_steps(GjGroup& g, const GjCtx& x, double* W, int n, int kb, int jb) {
+    const int lb = x.lb, G = x.G, gn = x.G, rows_per = x.rows_per, r_lo = x.r_lo, r_hi = x.r_hi;
+    const int my_rows = x.my_rows;
+    double* Sp0 = x.Sp0;
+    double* Sp1 = x.Sp1;
+    unsigned long long* bar = x.bar;
+    unsigned long long* ep = x.ep;
     const bool glead = lb == 0 && threadIdx.x == 0;
-    double* W = g.work;
-    const int64_t nn = (int64_t)n * n;
-    for (int64_t t = gt; t < nn; t += gnt) W[t] = src[t];
-    const int G = gn;
-    const int rows_per = (n + G - 1) / G;
-    const int r_lo = lb * rows_per;
-    const int r_hi = min(n, r_lo + rows_per);
-    const int my_rows = r_hi > r_lo ? r_hi - r_lo : 0;
-    double* Sp0 = grid_panel_smem;                             // [rows_per][kGridPanel]
-    double* Sp1 = grid_panel_smem + rows_per * kGridPanel;
-    double* Pf = g.panel;                                      // finished panel, column-major
-    double ld = 0.0;  // group leader
-    int status = 0;
-    bounded_barrier(bar, gn, w.err, ep);
-    for (int kb = 0; kb < n && !status; kb += kGridPanel) {
-      const int jb = min(kGridPanel, n - kb);
-      // own rows of W[:, J] -> shared memory; candidates of column kb; the
-      // candidate's row and the row of pivot position kb are published
-      {
-        unsigned long long cv = 0;
-        int ci = 0x7fffffff;
-        for (int e = threadIdx.x; e < my_rows * jb; e += kThreads) {
-          const int rr = e / jb, c = e % jb;
-          const int r = r_lo + rr;
-          const double v = W[(int64_t)r * n + kb + c];
-          Sp0[rr * kGridPanel + c] = v;
-          if (c == 0 && r >= kb) {
-            const unsigned long long a = abs_key(v);
-            if (key_better(a, r, cv, ci)) { cv = a; ci = r; }
-          }
-        }
-        unsigned long long bv;
-        int bi;
-        block_argmax_key(cv, ci, S.red, &bv, &bi);  // ends with a block barrier: Sp0 is complete
-        if (threadIdx.x == 0) {
-          g.cand_v[lb] = bv;
-          g.cand_i[lb] = bi;
-        }
-        if (bi >= r_lo && bi < r_hi && threadIdx.x < jb)
-          g.cand_row[(int64_t)lb * kGridPanel + threadIdx.x] = Sp0[(bi - r_lo) * kGridPanel + threadIdx.x];
-        if (kb >= r_lo && kb < r_hi && threadIdx.x < jb) g.row_k[threadIdx.x] = Sp0[(kb - r_lo) * kGridPanel + threadIdx.x];
-      }
-      bounded_barrier(bar, gn, w.err, ep);
-      for (int c = 0; c < jb; ++c) {
-        const int k = kb + c;
-        const int buf = c & 1;
-        const double* Sin = buf ? Sp1 : Sp0;
-        double* Sout = buf ? Sp0 : Sp1;
-        const unsigned long long* cvv = g.cand_v + buf * kMaxGrid;
-        const int* cii = g.cand_i + buf * kMaxGrid;
-        // pivot: the largest candidate (smallest row on ties), and the row of position k
-        unsigned long long pv;
-        int p;
-        {
-          unsigned long long cv = 0;
-          int ci = 0x7fffffff;
-          for (int q = threadIdx.x; q < G; q += kThreads)
-            if (key_better(cvv[q], cii[q], cv, ci)) { cv = cvv[q]; ci = cii[q]; }
-          if (threadIdx.x < jb) S.rowk[threadIdx.x] = g.row_k[buf * kGridPanel + threadIdx.x];
-          block_argmax_key(cv, ci, S.red, &pv, &p);
-        }
-        if (pv == 0 || pv >= 0x7FF0000000000000ull || p < k || p >= n) { status = 1; break; }  // zero, Inf or NaN
-        // warp 0: the winner's row, the reciprocal of the pivot (the same
-        // division in every lane: one warp instruction sequence) and the
-        // scaled pivot row; one block barrier publishes them
-        if (threadIdx.x < 32) {
-          const int t = threadIdx.x;
-          const double rp =
-              t < jb ? g.cand_row[((int64_t)buf * kMaxGrid + p / rows_per) * kGridPanel + t] : 0.0;
-          const double pivot = __shfl_sync(0xffffffffu, rp, c);
-          const double rinv = 1.0 / pivot;
-          if (t < jb) S.prow[t] = (t == c) ? rinv : rp * rinv;
-          if (t == 0) S.bc[0] = rinv;
-          if (glead) {
-            g.pivval[k] = pivot;
-            g.piv[k] = p;
-          }
-        }
-        __syncthreads();
-        const double inv = S.bc[0];
-        unsigned long long cv = 0;
-        int ci = 0x7fffffff;
-        for (int e = threadIdx.x; e < my_rows * jb; e += kThreads) {
-          const int rr = e / jb, cc = e % jb;
-          const int r = r_lo + rr;
-          double val;
-          if (r == k) {
-            val = S.prow[cc];
-          } else {
-            const double srcv = (r == p) ? S.rowk[cc] : Sin[rr * kGridPanel + cc];
-            const double f = (r == p) ? S.rowk[c] : Sin[rr * kGridPanel + c];
-            val = (cc == c) ? -f * inv : fma(-f, S.prow[cc], srcv);
-          }
-          Sout[rr * kGridPanel + cc] = val;
-          if (cc == c + 1 && r > k) {
-            const unsigned long long a = abs_key(val);
-            if (key_better(a, r, cv, ci)) { cv = a; ci = r; }
-          }
-        }
-        if (c + 1 < jb) {
-          unsigned long long bv;
-          int bi;
-          block_argmax_key(cv, ci, S.red, &bv, &bi);  // ends with a block barrier: Sout is complete
-          const int nb = (c + 1) & 1;
-          if (threadIdx.x == 0) {
-            g.cand_v[nb * kMaxGrid + lb] = bv;
-            g.cand_i[nb * kMaxGrid + lb] = bi;
-          }
-          if (bi >= r_lo && bi < r_hi && threadIdx.x < jb)
-            g.cand_row[((int64_t)nb * kMaxGrid + lb) * kGridPanel + threadIdx.x] =
-                Sout[(bi - r_lo) * kGridPanel + threadIdx.x];
-          if (k + 1 >= r_lo && k + 1 < r_hi && threadIdx.x < jb)
-            g.row_k[nb * kGridPanel + threadIdx.x] = Sout[(k + 1 - r_lo) * kGridPanel + threadIdx.x];
-        }
-        bounded_barrier(bar, gn, w.err, ep);
-      }
-      if (status) break;
-      const double* Sf = (jb & 1) ? Sp1 : Sp0;
-      // panel -> W and the column-major copy Pf, the panel's row swaps on the
-      // other columns, pivot rows -> R
+    // own rows of W[:, J] -> shared memory; candidates of column kb; the
+    // candidate's row and the row of pivot position kb are published
+    {
+      unsigned long long cv = 0;
+      int ci = 0x7fffffff;
       for (int e = threadIdx.x; e < my_rows * jb; e += kThreads) {
         const int rr = e / jb, c = e % jb;
         const int r = r_lo + rr;
-        const double v = Sf[rr * kGridPanel + c];
-        W[(int64_t)r * n + kb + c] = v;
-        Pf[(int64_t)c * n + r] = v;
+        const double v = W[(int64_t)r * n + kb + c];
+        Sp0[rr * kGridPanel + c] = v;
+        if (c == 0 && r >= kb) {
+          const unsigned long long a = abs_key(v);
+          if (key_better(a, r, cv, ci)) { cv = a; ci = r; }
+        }
       }
-      if (maps) {
-        // digits of the update's left factor U = P_f - I_J: this block's rows,
-        // eight lanes per row (four rows per warp at a time)
-        const int lane = threadIdx.x & 31, i = lane & 7, wq = threadIdx.x >> 5;
-        for (int r4 = wq * 4; r4 < my_rows; r4 += kThreads / 8) {
-          const int rr = r4 + (lane >> 3), r = r_lo + rr;
-          const bool valid = rr < my_rows;
+      unsigned long long bv;
+      int bi;
+      block_argmax_key(cv, ci, S.red, &bv, &bi);  // ends with a block barrier: Sp0 is complete
+      if (threadIdx.x == 0) {
+        g.cand_v[lb] = bv;
+        g.cand_i[lb] = bi;
+      }
+      if (bi >= r_lo && bi < r_hi && threadIdx.x < jb)
+        g.cand_row[(int64_t)lb * kGridPanel + threadIdx.x] = Sp0[(bi - r_lo) * kGridPanel + threadIdx.x];
+      if (kb >= r_lo && kb < r_hi && threadIdx.x < jb) g.row_k[threadIdx.x] = Sp0[(kb - r_lo) * kGridPanel + threadIdx.x];
+    }
+    bounded_barrier(bar, gn, w.err, ep);
+    for (int c = 0; c < jb; ++c) {
+      const int k = kb + c;
+      const int buf = c & 1;
+      const double* Sin = buf ? Sp1 : Sp0;
+      double* Sout = buf ? Sp0 : Sp1;
+      const unsigned long long* cvv = g.cand_v + buf * kMaxGrid;
+      const int* cii = g.cand_i + buf * kMaxGrid;
+      // pivot: the largest candidate (smallest row on ties), and the row of position k
+      unsigned long long pv;
+      int p;
+      {
+        unsigned long long cv = 0;
+        int ci = 0x7fffffff;
+        for (int q = threadIdx.x; q < G; q += kThreads)
+          if (key_better(cvv[q], cii[q], cv, ci)) { cv = cvv[q]; ci = cii[q]; }
+        if (threadIdx.x < jb) S.rowk[threadIdx.x] = g.row_k[buf * kGridPanel + threadIdx.x];
+        block_argmax_key(cv, ci, S.red, &pv, &p);
+      }
+      if (pv == 0 || pv >= 0x7FF0000000000000ull || p < k || p >= n) return 1;  // zero, Inf or NaN
+      // warp 0: the winner's row, the reciprocal of the pivot (the same
+      // division in every lane: one warp instruction sequence) and the
+      // scaled pivot row; one block barrier publishes them
+      if (threadIdx.x < 32) {
+        const int t = threadIdx.x;
+        const double rp =
+            t < jb ? g.cand_row[((int64_t)buf * kMaxGrid + p / rows_per) * kGridPanel + t] : 0.0;
+        const double pivot = __shfl_sync(0xffffffffu, rp, c);
+        const double rinv = 1.0 / pivot;
+        if (t < jb) S.prow[t] = (t == c) ? rinv : rp * rinv;
+        if (t == 0) S.bc[0] = rinv;
+        if (glead) {
+          g.pivval[k] = pivot;
+          g.piv[k] = p;
+        }
+      }
+      __syncthreads();
+      const double inv = S.bc[0];
+      unsigned long long cv = 0;
+      int ci = 0x7fffffff;
+      for (int e = threadIdx.x; e < my_rows * jb; e += kThreads) {
+        const int rr = e / jb, cc = e % jb;
+        const int r = r_lo + rr;
+        double val;
+        if (r == k) {
+          val = S.prow[cc];
+        } else {
+          const double srcv = (r == p) ? S.rowk[cc] : Sin[rr * kGridPanel + cc];
+          const double f = (r == p) ? S.rowk[c] : Sin[rr * kGridPanel + c];
+          val = (cc == c) ? -f * inv : fma(-f, S.prow[cc], srcv);
+        }
+        Sout[rr * kGridPanel + cc] = val;
+        if (cc == c + 1 && r > k) {
+          const unsigned long long a = abs_key(val);
+          if (key_better(a, r, cv, ci)) { cv = a; ci = r; }
+        }
+      }
+      if (c + 1 < jb) {
+        unsigned long long bv;
+        int bi;
+        block_argmax_key(cv, ci, S.red, &bv, &bi);  // ends with a block barrier: Sout is complete
+        const int nb = (c + 1) & 1;
+        if (threadIdx.x == 0) {
+          g.cand_v[nb * kMaxGrid + lb] = bv;
+          g.cand_i[nb * kMaxGrid + lb] = bi;
+        }
+        if (bi >= r_lo && bi < r_hi && threadIdx.x < jb)
+          g.cand_row[((int64_t)nb * kMaxGrid + lb) * kGridPanel + threadIdx.x] =
+              Sout[(bi - r_lo) * kGridPanel + threadIdx.x];
+        if (k + 1 >= r_lo && k + 1 < r_hi && threadIdx.x < jb)
+          g.row_k[nb * kGridPanel + threadIdx.x] = Sout[(k + 1 - r_lo) * kGridPanel + threadIdx.x];
+      }
+      bounded_barrier(bar, gn, w.err, ep);
+    }
+    return 0;
+  }
+
+  // The panel's update on the FP64 pipe: panel -> W and its column-major copy
+  // Pf, the panel's row swaps on the other columns, pivot rows -> R, then
+  // W[:, not J] += (Pf - I_J) R in DMMA tiles.
+  __device__ __noinline__ void update_rank32(GjGroup& g, const GjCtx& x, double* W, int n, int kb, int jb) {
+    const double* Sf = (jb & 1) ? x.Sp1 : x.Sp0;
+    double* Pf = g.panel;
+    for (int e = threadIdx.x; e < x.my_rows * jb; e += kThreads) {
+      const int rr = e / jb, c = e % jb;
+      const int r = x.r_lo + rr;
+      const double v = Sf[rr * kGridPanel + c];
+      W[(int64_t)r * n + kb + c] = v;
+      Pf[(int64_t)c * n + r] = v;
+    }
+    for (int j = x.gt; j < n; j += x.gnt) {
+      if (j >= kb && j < kb + jb) continue;
+      for (int c = 0; c < jb; ++c) {
+        const int k = kb + c, p = g.piv[k];
+        if (p != k) {
+          const double t0 = W[(int64_t)k * n + j];
+          W[(int64_t)k * n + j] = W[(int64_t)p * n + j];
+          W[(int64_t)p * n + j] = t0;
+        }
+      }
+      for (int c = 0; c < jb; ++c) g.R[(int64_t)c * n + j] = W[(int64_t)(kb + c) * n + j];
+    }
+    bounded_barrier(x.bar, x.G, w.err, x.ep);
+    const int tiles = (n + kTileM - 1) / kTileM;
+    for (int t = x.lb; t < tiles * tiles; t += x.G)
+      rank_update_tile(W, n, kb, jb, Pf, g.R, (t / tiles) * kTileM, (t % tiles) * kTileN);
+    bounded_barrier(x.bar, x.G, w.err, x.ep);
+  }
+
+  // One tensor-core update of W on this block's share of the tiles ut names
+  // (skipped once the grid's error word is set).
+  __device__ void group_update(GjGroup& g, const GjCtx& x, double* W, int n, const UpdTiles& ut) {
+    if (threadIdx.x == 0) S.skip_upd = *(volatile int*)w.err;
+    __syncthreads();
+    if (S.skip_upd) return;
+    const int T = ((n + kUpdM - 1) / kUpdM) * ut.ncbt;
+    const int t_lo = (int)((int64_t)x.lb * T / x.G), t_hi = (int)((int64_t)(x.lb + 1) * T / x.G);
+    sliced_update(S.slc, reinterpret_cast<unsigned char*>(grid_panel_smem), &maps->a[g.gi], &maps->b[g.gi], g.sl,
+                  W, n, ut, t_lo, t_hi, w.err);
+  }
+
+  // Rows of U_0 .. U_{q-1} (columns [0, 32 q) of g.ucat) permuted by the row
+  // swaps of the sub-panel at kb: each position the swaps touch (J and the
+  // pivot rows) gets the row the swaps moved there, traced back through them.
+  // One block; all reads before any write.
+  __device__ __noinline__ void permute_ucat(GjGroup& g, int kb, int jb, int q) {
+    const int np = 2 * jb, cols = q * kGridPanel;
+    if ((int)threadIdx.x < np) {
+      const int idx = threadIdx.x;
+      const int pos = idx < jb ? kb + idx : g.piv[kb + idx - jb];
+      int s = pos;
+      for (int t = jb - 1; t >= 0; --t) {
+        const int k = kb + t, p = g.piv[k];
+        s = s == k ? p : (s == p ? k : s);
+      }
+      S.ppos[idx] = pos;
+      S.psrc[idx] = s;
+    }
+    __syncthreads();
+    constexpr int kPer = (2 * kGridPanel * (kSuperCols - kGridPanel) + kThreads - 1) / kThreads;
+    const int E = np * cols;
+    double buf[kPer];
+#pragma unroll
+    for (int it = 0; it < kPer; ++it) {
+      const int e = threadIdx.x + it * kThreads;
+      if (e < E) buf[it] = g.ucat[(int64_t)S.psrc[e / cols] * kSuperCols + e % cols];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kPer; ++it) {
+      const int e = threadIdx.x + it * kThreads;
+      if (e < E) g.ucat[(int64_t)S.ppos[e / cols] * kSuperCols + e % cols] = buf[it];
+    }
+    __syncthreads();
+  }
+
+  // Gauss-Jordan inversion with the updates on the tensor cores, blocked in
+  // super-panels of up to kMaxChunks sub-panels (kSuperCols columns).
+  // Within a super-panel each sub-panel q (columns J_q) is factored on the
+  // current W[:, J_q] as in the unblocked form, and its rank-32 update reaches
+  // at once only the super-panel's other columns (a narrow update). For the
+  // columns outside the super-panel the update is deferred: the sub-panel's
+  // row swaps are applied to them at once, and its factor U_q = P_q - I_{J_q}
+  // (rows permuted by the later sub-panels' swaps) and its pivot rows
+  //   v_q = W[J_q, :] + sum_{p < q} U_p[J_q, :] v_p
+  // (W swapped but not yet updated there: v_q is the block of pivot rows the
+  // unblocked form would meet) are kept in g.ucat and g.vcat. The super-panel
+  // ends with one update W[:, outside] += [U_0 .. U_{m-1}] [v_0; ..; v_{m-1}],
+  // K = 32 m exact digit products per element, so W is read and written once
+  // per super-panel instead of once per panel. Returns 1 for a bad pivot.
+  __device__ __noinline__ int gj_blocked(GjGroup& g, const GjCtx& x, double* W, int n) {
+    const int lane = threadIdx.x & 31, i8 = lane & 7;
+    const int gw = x.gt >> 5, nw = x.gnt >> 5;
+    const int ncb = (n + kUpdN - 1) / kUpdN;
+    double* UsT = grid_panel_smem + 2 * x.rows_per * kGridPanel;  // [32 q][32]: rows J_q of U_0 .. U_{q-1}, transposed
+    for (int K0 = 0; K0 < n; K0 += kSuperCols) {
+      const int B = min(kSuperCols, n - K0);
+      const int m = (B + kGridPanel - 1) / kGridPanel;
+      for (int q = 0; q < m; ++q) {
+        const int kb = K0 + q * kGridPanel, jb = min(kGridPanel, n - kb);
+        if (panel_steps(g, x, W, n, kb, jb)) return 1;
+        const double* Sf = (jb & 1) ? x.Sp1 : x.Sp0;
+        for (int e = threadIdx.x; e < x.my_rows * jb; e += kThreads) {
+          const int rr = e / jb, c = e % jb;
+          W[(int64_t)(x.r_lo + rr) * n + kb + c] = Sf[rr * kGridPanel + c];
+        }
+        // U_q = P_q - I_{J_q}, this block's rows, eight lanes per row: FP64
+        // into block q of g.ucat, and its digits (one chunk) for the narrow update
+        for (int r4 = (threadIdx.x >> 5) * 4; r4 < x.my_rows; r4 += kThreads / 8) {
+          const int rr = r4 + (lane >> 3), r = x.r_lo + rr;
+          const bool valid = rr < x.my_rows;
           double u[4];
           for (int t = 0; t < 4; ++t) {
-            const int c = 4 * i + t;
+            const int c = 4 * i8 + t;
             u[t] = (valid && c < jb) ? Sf[rr * kGridPanel + c] - (r == kb + c ? 1.0 : 0.0) : 0.0;
           }
-          slice_row8(u[0], u[1], u[2], u[3], i, valid, g.sl.adig + (int64_t)r * kDigK, g.sl.aexp + r);
-        }
-      }
-      if (!maps) {
-        for (int j = gt; j < n; j += gnt) {
-          if (j >= kb && j < kb + jb) continue;
-          for (int c = 0; c < jb; ++c) {
-            const int k = kb + c, p = g.piv[k];
-            if (p != k) {
-              const double t0 = W[(int64_t)k * n + j];
-              W[(int64_t)k * n + j] = W[(int64_t)p * n + j];
-              W[(int64_t)p * n + j] = t0;
-            }
+          if (valid) {
+            double* up = g.ucat + (int64_t)r * kSuperCols + q * kGridPanel + 4 * i8;
+            *reinterpret_cast<double2*>(up) = make_double2(u[0], u[1]);
+            *reinterpret_cast<double2*>(up + 2) = make_double2(u[2], u[3]);
           }
-          for (int c = 0; c < jb; ++c) g.R[(int64_t)c * n + j] = W[(int64_t)(kb + c) * n + j];
+          if (m > 1)
+            slice_row8_1(u[0], u[1], u[2], u[3], i8, valid, g.sl.adig + (int64_t)r * kDigRow, g.sl.aexp + r);
         }
-      } else {
-        // eight lanes of a warp per column: the first swaps the panel's pivot
-        // rows in that column, then each lane forms one digit slice of the
-        // column of V = R (the swapped pivot rows); warps walk the columns
-        // four at a time, so every block of the group takes part
-        const int lane = threadIdx.x & 31, i = lane & 7;
-        const int gw = gt >> 5, nw = gnt >> 5;
+        // rows J_q of U_0 .. U_{q-1} as this sub-panel's swaps leave them,
+        // transposed into shared memory (UsT[32 p + c2][c] = U_p[kb + c, c2])
+        if (q > 0) {
+          if ((int)threadIdx.x < jb) {
+            int s = kb + threadIdx.x;
+            for (int t = jb - 1; t >= 0; --t) {
+              const int k = kb + t, p = g.piv[k];
+              s = s == k ? p : (s == p ? k : s);
+            }
+            S.psrc[threadIdx.x] = s;
+          }
+          __syncthreads();
+          for (int e = threadIdx.x; e < q * kGridPanel * kGridPanel; e += kThreads) {
+            const int c = e % kGridPanel, kq = e / kGridPanel;
+            UsT[e] = c < jb ? g.ucat[(int64_t)S.psrc[c] * kSuperCols + kq] : 0.0;
+          }
+          __syncthreads();
+        }
+        // every column outside J_q, eight lanes per column (warps walk the
+        // columns four at a time, every block of the group taking part): the
+        // first lane applies the sub-panel's row swaps; then, inside the
+        // super-panel, the lanes split the pivot rows W[J_q, j] into digits
+        // for the narrow update; outside it they form v_q[:, j] (lane i8:
+        // rows 4 i8 .. 4 i8 + 3) into g.vcat
         for (int j4 = gw * 4; j4 < n; j4 += nw * 4) {
           const int j = j4 + (lane >> 3);
           const bool valid = j < n && (j < kb || j >= kb + jb);
-          if (valid && i == 0)
+          const bool inside = j >= K0 && j < K0 + B;
+          if (valid && i8 == 0)
             for (int c = 0; c < jb; ++c) {
               const int k = kb + c, p = g.piv[k];
               if (p != k) {
@@ -666,30 +794,123 @@ struct GridOps {
           __syncwarp();
           double v[4];
           for (int t = 0; t < 4; ++t) {
-            const int c = 4 * i + t;
+            const int c = 4 * i8 + t;
             v[t] = (valid && c < jb) ? W[(int64_t)(kb + c) * n + j] : 0.0;
           }
-          slice_row8(v[0], v[1], v[2], v[3], i, valid, g.sl.bdig + (int64_t)j * kDigK, g.sl.bexp + j);
+          if (m > 1)
+            slice_row8_1(v[0], v[1], v[2], v[3], i8, valid && inside, g.sl.bdig + (int64_t)j * kDigRow,
+                         g.sl.bexp + j);
+          const bool outside = valid && !inside;
+          double* vc = g.vcat + (int64_t)(outside ? j : 0) * kSuperCols;
+          for (int p = 0; p < q; ++p) {
+            double a[4] = {0.0, 0.0, 0.0, 0.0};
+            if (outside) {
+              const double2 a01 = *reinterpret_cast<const double2*>(vc + p * kGridPanel + 4 * i8);
+              const double2 a23 = *reinterpret_cast<const double2*>(vc + p * kGridPanel + 4 * i8 + 2);
+              a[0] = a01.x;
+              a[1] = a01.y;
+              a[2] = a23.x;
+              a[3] = a23.y;
+            }
+#pragma unroll
+            for (int c2 = 0; c2 < kGridPanel; ++c2) {
+              const double b = __shfl_sync(0xffffffffu, a[c2 & 3], (lane & ~7) | (c2 >> 2));
+              const double* us = UsT + (p * kGridPanel + c2) * kGridPanel + 4 * i8;
+              const double2 u01 = *reinterpret_cast<const double2*>(us);
+              const double2 u23 = *reinterpret_cast<const double2*>(us + 2);
+              v[0] = fma(u01.x, b, v[0]);
+              v[1] = fma(u01.y, b, v[1]);
+              v[2] = fma(u23.x, b, v[2]);
+              v[3] = fma(u23.y, b, v[3]);
+            }
+          }
+          if (outside) {
+            *reinterpret_cast<double2*>(vc + q * kGridPanel + 4 * i8) = make_double2(v[0], v[1]);
+            *reinterpret_cast<double2*>(vc + q * kGridPanel + 4 * i8 + 2) = make_double2(v[2], v[3]);
+          }
           __syncwarp();
         }
         fence_proxy_async_global();  // the digits are read by TMA after the barrier
-      }
-      bounded_barrier(bar, gn, w.err, ep);
-      if (maps) {
-        if (threadIdx.x == 0) S.skip_upd = *(volatile int*)w.err;
-        __syncthreads();
-        if (!S.skip_upd) {
-          const int T = ((n + kUpdM - 1) / kUpdM) * ((n + kUpdN - 1) / kUpdN);
-          const int t_lo = (int)((int64_t)lb * T / G), t_hi = (int)((int64_t)(lb + 1) * T / G);
-          sliced_update(S.slc, reinterpret_cast<unsigned char*>(grid_panel_smem), &maps->a[g.gi], &maps->b[g.gi],
-                        g.sl, W, n, kb, jb, t_lo, t_hi, w.err);
+        bounded_barrier(x.bar, x.G, w.err, x.ep);
+        // the narrow update (block 0 first applies the swaps to U_0 .. U_{q-1})
+        if (q > 0 && x.lb == 0) permute_ucat(g, kb, jb, q);
+        if (m > 1) {
+          const int cb0 = K0 / kUpdN;
+          const UpdTiles ut{1, cb0, min(ncb - cb0, (B + kUpdN - 1) / kUpdN), 1 << 30, 0, kb, jb};
+          group_update(g, x, W, n, ut);
         }
-      } else {
-        const int tiles = (n + kTileM - 1) / kTileM;
-        for (int t = lb; t < tiles * tiles; t += G)
-          rank_update_tile(W, n, kb, jb, Pf, g.R, (t / tiles) * kTileM, (t % tiles) * kTileN);
+        bounded_barrier(x.bar, x.G, w.err, x.ep);
       }
-      bounded_barrier(bar, gn, w.err, ep);
+      // digits of the deferred update, K = 32 m: every row of
+      // [U_0 .. U_{m-1}] and every column of [v_0; ..; v_{m-1}] outside the
+      // super-panel, eight lanes per row or column
+      const int items = 2 * n - B;
+      for (int q4 = gw * 4; q4 < items; q4 += nw * 4) {
+        const int it = q4 + (lane >> 3);
+        const bool valid = it < items, isa = it < n;
+        int row = isa ? it : it - n;
+        if (!isa && row >= K0) row += B;
+        if (!valid) row = 0;
+        const double* sp = (isa ? g.ucat : g.vcat) + (int64_t)row * kSuperCols + 4 * i8;
+        double v[4 * kMaxChunks];
+#pragma unroll
+        for (int c = 0; c < kMaxChunks; ++c) {
+          double2 a01 = make_double2(0.0, 0.0), a23 = make_double2(0.0, 0.0);
+          if (valid && c < m) {
+            a01 = *reinterpret_cast<const double2*>(sp + c * kGridPanel);
+            a23 = *reinterpret_cast<const double2*>(sp + c * kGridPanel + 2);
+          }
+          v[4 * c] = a01.x;
+          v[4 * c + 1] = a01.y;
+          v[4 * c + 2] = a23.x;
+          v[4 * c + 3] = a23.y;
+        }
+        slice_row8<kMaxChunks>(v, i8, valid, m, (isa ? g.sl.adig : g.sl.bdig) + (int64_t)row * kDigRow,
+                               (isa ? g.sl.aexp : g.sl.bexp) + row);
+      }
+      fence_proxy_async_global();
+      bounded_barrier(x.bar, x.G, w.err, x.ep);
+      {
+        const int cin0 = K0 / kUpdN, cin1 = min(ncb, (K0 + B + kUpdN - 1) / kUpdN);
+        const UpdTiles ut{m, 0, ncb - (cin1 - cin0), cin0, cin1 - cin0, K0, B};
+        if (ut.ncbt > 0) group_update(g, x, W, n, ut);
+      }
+      bounded_barrier(x.bar, x.G, w.err, x.ep);
+    }
+    return 0;
+  }
+
+  __device__ void inverse_group(GjGroup& g, int g0, int gn, unsigned long long* bar, unsigned long long* ep,
+                                const double* src, double* dst, int n) {
+    GjCtx x;
+    x.lb = blockIdx.x - g0;
+    x.gt = x.lb * kThreads + threadIdx.x;
+    x.gnt = gn * kThreads;
+    x.G = gn;
+    x.rows_per = (n + gn - 1) / gn;
+    x.r_lo = x.lb * x.rows_per;
+    x.r_hi = min(n, x.r_lo + x.rows_per);
+    x.my_rows = x.r_hi > x.r_lo ? x.r_hi - x.r_lo : 0;
+    x.Sp0 = grid_panel_smem;                             // [rows_per][kGridPanel]
+    x.Sp1 = grid_panel_smem + x.rows_per * kGridPanel;
+    x.bar = bar;
+    x.ep = ep;
+    const int lb = x.lb, gt = x.gt, gnt = x.gnt, G = x.G;
+    const bool glead = lb == 0 && threadIdx.x == 0;
+    double* W = g.work;
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t t = gt; t < nn; t += gnt) W[t] = src[t];
+    double ld = 0.0;  // group leader
+    int status = 0;
+    bounded_barrier(bar, gn, w.err, ep);
+    if (maps) {
+      status = gj_blocked(g, x, W, n);
+    } else {
+      for (int kb = 0; kb < n && !status; kb += kGridPanel) {
+        const int jb = min(kGridPanel, n - kb);
+        status = panel_steps(g, x, W, n, kb, jb);
+        if (!status) update_rank32(g, x, W, n, kb, jb);
+      }
     }
     if (!status) {
       // log|det| = sum of log|pivot|, one log per thread, per-block partial sums

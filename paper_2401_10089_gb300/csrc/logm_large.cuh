@@ -32,11 +32,13 @@ __global__ void __launch_bounds__(kThreads, SLICED ? 1 : 2)
   if (threadIdx.x == 0) {
     S.ep[0] = S.ep[1] = S.ep[2] = 0;
     if (SLICED) {
-      for (int t = 0; t < 4; ++t) {
-        tm_bar_init(su32(&S.slc.bar[t]), 1);
-        S.slc.phase[t] = 0;
+      for (int t = 0; t < kUpdStages; ++t) {
+        tm_bar_init(su32(&S.slc.full[t]), 1);
+        tm_bar_init(su32(&S.slc.empty[t]), 1);
       }
-      S.slc.failed = 0;
+      tm_bar_init(su32(&S.slc.acc), 1);
+      S.slc.stages = 0;
+      S.slc.tiles = 0;
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
   }
@@ -89,7 +91,8 @@ namespace large_detail {
 inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct GroupLayout {
-  size_t cand_v, cand_i, cand_row, row_k, pivval, ldpart, panel, R, piv, perm, work, adig, bdig, aexp, bexp;
+  size_t cand_v, cand_i, cand_row, row_k, pivval, ldpart, panel, R, piv, perm, work, adig, bdig, aexp, bexp, ucat,
+      vcat;
 };
 
 struct LargeLayout {
@@ -120,10 +123,12 @@ inline LargeLayout large_layout(int n_max) {
     g.piv = o;    o = align256(o + sizeof(int) * nm);
     g.perm = o;   o = align256(o + sizeof(int) * nm);
     g.work = o;   o = align256(o + sizeof(double) * nm * nm);
-    g.adig = o;   o = align256(o + 2 * (size_t)kDigK * nm);  // BF16 digits of the tensor-core updates
-    g.bdig = o;   o = align256(o + 2 * (size_t)kDigK * nm);
+    g.adig = o;   o = align256(o + 2 * (size_t)kDigRow * nm);  // BF16 digits of the tensor-core updates
+    g.bdig = o;   o = align256(o + 2 * (size_t)kDigRow * nm);
     g.aexp = o;   o = align256(o + sizeof(int32_t) * nm);
     g.bexp = o;   o = align256(o + sizeof(int32_t) * nm);
+    g.ucat = o;   o = align256(o + sizeof(double) * kSuperCols * nm);  // deferred factors of a super-panel
+    g.vcat = o;   o = align256(o + sizeof(double) * kSuperCols * nm);
   }
   L.slot = o;     o = align256(o + sizeof(double) * kSlotMats * nm * nm);
   L.total = o;
@@ -147,13 +152,13 @@ inline EncodeTiledFn tensor_map_encoder() {
   return fn;
 }
 
-// 2-D map over a digit buffer: n_max rows of kDigK BF16, box of 64 BF16
+// 2-D map over a digit buffer: n_max rows of kDigRow BF16, box of 64 BF16
 // (128 bytes) x box_rows, 128-byte swizzle, zero fill outside.
 inline bool digit_map(CUtensorMap* m, void* base, int n_max, int box_rows) {
   EncodeTiledFn f = tensor_map_encoder();
   if (!f) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)kDigK, (cuuint64_t)n_max};
-  const cuuint64_t strides[1] = {(cuuint64_t)kDigK * 2};
+  const cuuint64_t dims[2] = {(cuuint64_t)kDigRow, (cuuint64_t)n_max};
+  const cuuint64_t strides[1] = {(cuuint64_t)kDigRow * 2};
   const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -192,6 +197,8 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
     g.sl.bdig = reinterpret_cast<__nv_bfloat16*>(ws + gl.bdig);
     g.sl.aexp = reinterpret_cast<int32_t*>(ws + gl.aexp);
     g.sl.bexp = reinterpret_cast<int32_t*>(ws + gl.bexp);
+    g.ucat = reinterpret_cast<double*>(ws + gl.ucat);
+    g.vcat = reinterpret_cast<double*>(ws + gl.vcat);
     g.gi = t;
   }
   SliceMaps maps;
@@ -212,9 +219,11 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
   // Dynamic shared memory: two buffers of a block's panel rows, sized for the
-  // smallest group (half the grid); with SLICED at least the digit tiles of
-  // the tensor-core updates (which also keeps one block per SM, the owner of
-  // its SM's TMEM). Two blocks per SM if they fit, else one.
+  // smallest group (half the grid), and at least the DMMA tiles of the FP64
+  // products; with SLICED also the transposed factor rows of a super-panel,
+  // and at least the stage ring and staged tile of the tensor-core updates
+  // (which also keeps one block per SM, the owner of its SM's TMEM). Two
+  // blocks per SM if they fit, else one.
   int grid = 0;
   size_t dyn = 0;
   for (int want = SLICED ? 1 : 2; want >= 1 && grid == 0; --want) {
@@ -222,6 +231,8 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
     if (gsz > kMaxGrid) gsz = kMaxGrid;
     const int min_group = gsz / 2 >= 8 ? gsz / 2 : gsz;
     size_t d = 2 * (size_t)((p.n_max + min_group - 1) / min_group) * kGridPanel * sizeof(double);
+    if (SLICED) d += sizeof(double) * (kSuperCols - kGridPanel) * kGridPanel;
+    if (d < sizeof(GemmSmem)) d = sizeof(GemmSmem);
     if (SLICED && d < kUpdSmemBytes) d = kUpdSmemBytes;
     e = cudaFuncSetAttribute(k_logm_large<MODE, SLICED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d);
     if (e != cudaSuccess) continue;
@@ -238,7 +249,7 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   if (SLICED)  // digit rows past a matrix's n are never written: they stay zero
     for (int t = 0; t < 2; ++t) {
-      e = cudaMemsetAsync(ws + L.g[t].adig, 0, L.g[t].bexp + sizeof(int32_t) * p.n_max - L.g[t].adig, st);
+      e = cudaMemsetAsync(ws + L.g[t].adig, 0, L.g[t].ucat - L.g[t].adig, st);
       if (e != cudaSuccess) return e;
     }
   SmallParams pp = p;

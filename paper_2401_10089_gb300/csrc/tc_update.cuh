@@ -1,24 +1,27 @@
-// tc_update.cuh -- the rank-32 Gauss-Jordan update of the whole-GPU kernel,
-// W[:, not J] += (P_f - I_J) R, on the tensor cores with FP64 accuracy.
+// tc_update.cuh -- the rank-K updates of the whole-GPU kernel,
+// W[:, cols] += U V, on the tensor cores with FP64 accuracy.
 //
-// The panel's two factors are split into exact BF16 digits (fp64_slices.cuh):
-// U = P_f - I_J row by row, V = R column by column, eight digits each, stored
-// K-major in global memory (kDigK = 8 x 32 BF16 per row or column). Each
-// block then runs its share of the 128 x 64 output tiles of W:
-//   * TMA copies the tile's U digits (128 x 256 BF16, four 128-byte swizzle
-//     boxes) and V digits (64 x 256) into shared memory; the V copy of the next
-//     tile overlaps the current tile's epilogue (two stages);
-//   * one thread issues 72 tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
-//     M = 128, N = 64, K = 16): for every level L = i + j of the digit pairs
-//     (i, j), both K halves of the 32 terms, accumulated into its own TMEM
-//     region of 64 columns (8 levels = all 512 columns). Every level sum is an
-//     integer below 2^22, so the FP32 accumulation is exact;
+// U (n x K) and V (K x n), K = 32 nc for nc <= kMaxChunks chunks, are split
+// into exact BF16 digits (fp64_slices.cuh): every row of U and every column
+// of V gets one power-of-two scale over its K values and eight digits per
+// value, stored K-major in global memory (kDigRow BF16 per row or column:
+// chunk c at kChunkDig c; inside a chunk the half h of its 32 terms at 128 h,
+// digit s of that half at 16 s). Each block then runs its share of the
+// 128 x 64 output tiles of W:
+//   * thread 0 streams the digits through a ring of kUpdStages shared-memory
+//     stages with TMA, one stage per (chunk, half): 128 x 128 BF16 of U and
+//     64 x 128 of V, two 128-byte swizzle boxes each;
+//   * thread 32 issues, per stage, 36 tcgen05.mma (kind::f16, BF16 x BF16 ->
+//     FP32, M = 128, N = 64, K = 16): for every level L = i + j of the digit
+//     pairs (i, j) one MMA into that level's 64 TMEM columns (8 levels = all
+//     512 columns), accumulated over all stages of the tile. A level sum is an
+//     integer of magnitude <= nc 2^22 <= 2^24, so FP32 accumulation is exact;
 //   * all eight warps read the levels back (tcgen05.ld), combine them into the
-//     exact integer dot product and round it to FP64 (integer operations and
-//     three FP64 instructions) into a shared-memory tile; the next tile's MMAs start as soon as TMEM is
-//     read, while the warps add the staged tile to W row by row (coalesced).
-// Per element and panel that is four FP64 instructions (the conversion and
-// the addition) instead of 32 FP64 FMAs.
+//     exact integer dot product and round it to FP64 into a shared-memory
+//     tile; then the next tile's MMAs run while the warps add the staged tile
+//     to W row by row (coalesced).
+// Per element that is four FP64 instructions (conversion and addition) for K
+// terms instead of K FP64 FMAs.
 //
 // Every mbarrier wait is bounded (kTmWaitLimit polls); a wait that runs out
 // sets the grid's error word, and the kernel reports LOGM_INFO_TIMEOUT for the
@@ -32,18 +35,22 @@
 
 namespace lg {
 
-constexpr int kUpdM = 128, kUpdN = 64;                      // output tile of W: rows x columns
-constexpr int kDigK = kSlices * kSliceK;                    // digits per row of U / column of V
-constexpr uint32_t kUpdABytes = kUpdM * kDigK * 2;          // 64 KB
-constexpr uint32_t kUpdBBytes = kUpdN * kDigK * 2;          // 32 KB
-constexpr uint32_t kUpdAtomA = kUpdM * 128, kUpdAtomB = kUpdN * 128;  // one 128-byte swizzle box
-constexpr int kUpdTsStride = kUpdN + 1;                     // staged tile: doubles per row (padded)
+constexpr int kUpdM = 128, kUpdN = 64;                       // output tile of W: rows x columns
+constexpr int kMaxChunks = 4;                                // K of one update: up to 4 x 32 terms
+constexpr int kChunkDig = kSlices * kSliceK;                 // digits of one chunk of a row: 256 BF16
+constexpr int kDigRow = kMaxChunks * kChunkDig;              // digit buffer row: 1024 BF16
+constexpr int kUpdStages = 3;                                // TMA ring depth
+constexpr uint32_t kAtomA = kUpdM * 128, kAtomB = kUpdN * 128;  // one 128-byte swizzle box (4 digits x 16 terms)
+constexpr uint32_t kStageA = 2 * kAtomA, kStageB = 2 * kAtomB;  // half a chunk: 32 KB + 16 KB
+constexpr uint32_t kStageBytes = kStageA + kStageB;
+constexpr int kUpdTsStride = kUpdN + 1;                      // staged tile: doubles per row (padded)
 constexpr uint32_t kUpdTsBytes = kUpdM * kUpdTsStride * 8;   // 65 KB
-constexpr size_t kUpdSmemBytes = kUpdABytes + 2 * kUpdBBytes + kUpdTsBytes + 1024;  // + alignment slack
+constexpr size_t kUpdSmemBytes = kUpdStages * kStageBytes + kUpdTsBytes + 1024;  // + alignment slack
 constexpr int kUpdTmemCols = kSliceLevels * kUpdN;           // 512
 static_assert(kUpdTmemCols == 512, "eight levels of 64 columns fill TMEM");
+static_assert(kSlices == 8, "a stage holds two swizzle boxes of four digits");
 
-// Tensor maps of the digit buffers, per inversion group (2-D: kDigK x n_max
+// Tensor maps of the digit buffers, per inversion group (2-D: kDigRow x n_max
 // BF16, boxes of 64 x 128 rows for U and 64 x 64 for V, 128-byte swizzle).
 struct SliceMaps {
   CUtensorMap a[2];
@@ -51,56 +58,89 @@ struct SliceMaps {
 };
 
 struct SliceBufs {
-  __nv_bfloat16* adig;  // [n_max][kDigK]: row r of U, digit i of term k at [r][32 i + k]
-  __nv_bfloat16* bdig;  // [n_max][kDigK]: column j of V likewise
+  __nv_bfloat16* adig;  // [n_max][kDigRow]: digits of the rows of U
+  __nv_bfloat16* bdig;  // [n_max][kDigRow]: digits of the columns of V
   int32_t* aexp;        // [n_max] scale exponent of each row of U
   int32_t* bexp;        // [n_max] scale exponent of each column of V
 };
 
+// Barriers and lifetime counters of the engine (they persist across calls:
+// a stage with lifetime index u uses ring slot u % kUpdStages for the
+// (u / kUpdStages)-th time, which fixes the phase parity of its barriers).
 struct SliceSmem {
-  unsigned long long bar[4];  // U tile full, V stage 0 full, V stage 1 full, accumulators ready
-  uint32_t phase[4];          // completed phases of each barrier
-  uint32_t tmem;              // TMEM base address of the level accumulators
-  int failed;                 // a bounded wait ran out
-  int32_t ecol[kUpdN];        // scale exponents of the current tile's columns of V
+  unsigned long long full[kUpdStages];   // stage loaded (TMA transaction bytes)
+  unsigned long long empty[kUpdStages];  // stage's MMAs done (tcgen05.commit)
+  unsigned long long acc;                // tile's MMAs done
+  uint32_t stages;                       // stages loaded and consumed so far
+  uint32_t tiles;                        // tiles accumulated so far
+  uint32_t tmem;                         // TMEM base address of the level accumulators
+  int32_t ecol[kUpdN];                   // scale exponents of the current tile's columns of V
 };
 
-// The digits of one row of 32 values split among the 8 lanes of an aligned
-// lane group (lanes 8q .. 8q + 7 of a warp): lane i holds the values
-// k = 4 i .. 4 i + 3 (zero past the row's length) in v0..v3. The group forms the
-// row's scale exponent (the largest magnitude by integer comparison of the
-// bit patterns: NaN above Inf above every finite value), each lane the
-// fixed-point integers and all eight digits of its four values, and writes
-// them as eight 8-byte pieces of the row of kDigK BF16 at out (digit s of
-// value k at out[32 s + k]); lane 0 stores the exponent at *eo. Every lane
-// of the warp must call this (the shuffles); `valid` lanes store.
-static __device__ __noinline__ void slice_row8(double v0, double v1, double v2, double v3, int i, bool valid,
-                                               __nv_bfloat16* out, int32_t* eo) {
-  const double v[4] = {v0, v1, v2, v3};
+// Which tiles and columns of W an update touches: output column tiles
+// cb0 .. cb0 + ncbt - 1 of every row tile, those from gap_at on shifted by
+// gap (so that [gap_at, gap_at + gap) is skipped), and within them every
+// column outside [mk, mk + mj).
+struct UpdTiles {
+  int nc;
+  int cb0, ncbt, gap_at, gap;
+  int mk, mj;
+};
+
+// The digits of one row of up to 32 NC values split among the 8 lanes of an
+// aligned lane group (lanes 8q .. 8q + 7 of a warp): lane i holds, for every
+// chunk c < NC, the values k = 4 i .. 4 i + 3 of that chunk in v[4 c .. 4 c + 3]
+// (zero past the row's length). The group forms the row's scale exponent (the
+// largest magnitude by integer comparison of the bit patterns: NaN above Inf
+// above every finite value), each lane the fixed-point integers and all eight
+// digits of its values, and writes them as 8-byte pieces of the row at out
+// (chunks c < nc); lane 0 stores the exponent at *eo. Every lane of the warp
+// must call this (the shuffles); `valid` lanes store.
+template <int NC>
+static __device__ __forceinline__ void slice_row8(const double* v, int i, bool valid, int nc, __nv_bfloat16* out,
+                                                  int32_t* eo) {
   unsigned long long mb = 0;
-  for (int t = 0; t < 4; ++t) {
+#pragma unroll
+  for (int t = 0; t < 4 * NC; ++t) {
     const unsigned long long a = lg_dbits(v[t]) & 0x7FFFFFFFFFFFFFFFull;
     mb = a > mb ? a : mb;
   }
+#pragma unroll
   for (int x = 1; x < 8; x <<= 1) {
     const unsigned long long o = __shfl_xor_sync(0xffffffffu, mb, x);
     mb = o > mb ? o : mb;
   }
   const int32_t e = slice_exponent(lg_bitsd(mb));
   if (valid && i == 0) *eo = e;
-  int64_t X[4];
-  uint64_t Y[4];
-  for (int t = 0; t < 4; ++t) {
-    X[t] = e != kSliceNonFinite ? slice_fixed_int(v[t], e) : 0;
-    Y[t] = slice_bias(X[t]);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    int64_t X[4];
+    uint64_t Y[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      X[t] = e != kSliceNonFinite ? slice_fixed_int(v[4 * c + t], e) : 0;
+      Y[t] = slice_bias(X[t]);
+    }
+    if (valid && c < nc) {
+      __nv_bfloat16* o = out + kChunkDig * c + 128 * (i >> 2) + 4 * (i & 3);
+#pragma unroll
+      for (int sl = 0; sl < kSlices; ++sl) {
+        uint32_t b[4];
+        // |d| <= 128 has at most 8 significant bits: the BF16 is the FP32's top half
+#pragma unroll
+        for (int t = 0; t < 4; ++t) b[t] = __float_as_uint(static_cast<float>(slice_digit(X[t], Y[t], sl))) >> 16;
+        *reinterpret_cast<uint2*>(o + 16 * sl) = make_uint2(b[0] | (b[1] << 16), b[2] | (b[3] << 16));
+      }
+    }
   }
-  if (!valid) return;
-  for (int sl = 0; sl < kSlices; ++sl) {
-    uint32_t b[4];
-    // |d| <= 128 has at most 8 significant bits: the BF16 is the FP32's top half
-    for (int t = 0; t < 4; ++t) b[t] = __float_as_uint(static_cast<float>(slice_digit(X[t], Y[t], sl))) >> 16;
-    *reinterpret_cast<uint2*>(out + kSliceK * sl + 4 * i) = make_uint2(b[0] | (b[1] << 16), b[2] | (b[3] << 16));
-  }
+}
+
+// One row of 32 values (one chunk), out of line: the split of the Gauss-Jordan
+// panels and pivot rows.
+static __device__ __noinline__ void slice_row8_1(double v0, double v1, double v2, double v3, int i, bool valid,
+                                                 __nv_bfloat16* out, int32_t* eo) {
+  const double v[4] = {v0, v1, v2, v3};
+  slice_row8<1>(v, i, valid, 1, out, eo);
 }
 
 // Generic-proxy writes (the digits) made visible to later TMA reads.
@@ -108,100 +148,119 @@ static __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// The 72 MMAs of one tile (called by one thread): waits for its U tile (when
-// it is a new one) and its V stage, then for each level L = i + j the digit
-// pairs (i, j), both K halves of the 32 terms, into the level's 64 TMEM
-// columns; the commit arrives on bar_acc once they are done (also when a wait
-// ran out: then nothing was issued and the result is false).
-static __device__ __forceinline__ bool tile_mmas(uint32_t tmem, uint32_t sA, uint32_t sB, uint32_t bar_a, bool wait_a,
-                                                 uint32_t ph_a, uint32_t bar_b, uint32_t ph_b, uint32_t bar_acc) {
+// Thread 0: loads stage s of a tile (chunk s / 2, half s % 2) of row tile rb
+// and column tile cb into ring slot u % kUpdStages, u the stage's lifetime
+// index, once the slot's previous MMAs are done. False when that wait ran out.
+static __device__ __forceinline__ bool upd_produce(SliceSmem& sm, uint32_t ring, const CUtensorMap* map_a,
+                                                   const CUtensorMap* map_b, uint32_t u, int rb, int cb, int s) {
+  const uint32_t slot = u % kUpdStages, use = u / kUpdStages;
+  if (use > 0 && !tm_wait(su32(&sm.empty[slot]), (use - 1) & 1)) return false;
+  const uint32_t fb = su32(&sm.full[slot]);
+  const uint32_t sA = ring + slot * kStageBytes, sB = sA + kStageA;
+  const int x = kChunkDig * (s >> 1) + 128 * (s & 1);
+  tm_expect(fb, kStageBytes);
+  tm_load2d(sA, map_a, fb, x, rb * kUpdM);
+  tm_load2d(sA + kAtomA, map_a, fb, x + 64, rb * kUpdM);
+  tm_load2d(sB, map_b, fb, x, cb * kUpdN);
+  tm_load2d(sB + kAtomB, map_b, fb, x + 64, cb * kUpdN);
+  return true;
+}
+
+// Thread 0: stages [s_from, s_to) of the tile whose first stage has lifetime
+// index u0; *done counts the stages issued.
+static __device__ __noinline__ bool upd_produce_range(SliceSmem& sm, uint32_t ring, const CUtensorMap* map_a,
+                                                      const CUtensorMap* map_b, uint32_t u0, int rb, int cb,
+                                                      int s_from, int s_to, uint32_t* done) {
+  for (int s = s_from; s < s_to; ++s) {
+    if (!upd_produce(sm, ring, map_a, map_b, u0 + s, rb, cb, s)) return false;
+    ++*done;
+  }
+  return true;
+}
+
+// Thread 32: the MMAs of a tile, stage by stage as they arrive: per stage (a
+// half chunk), for each level L = i + j every digit pair (i, j) of that
+// half, 36 MMAs into the level's 64 TMEM columns; the tile's first stage
+// starts every level's sum. Each stage's commit frees its slot; the final
+// commit arrives on acc once all are done (also after a wait ran out, so that
+// the readers are released; the result is then false).
+static __device__ __noinline__ bool upd_mma_tile(SliceSmem& sm, uint32_t ring, uint32_t tmem, uint32_t u0, int S2) {
   bool ok = true;
-  if (wait_a) ok = tm_wait(bar_a, ph_a & 1);
-  ok = ok && tm_wait(bar_b, ph_b & 1);
-  if (ok) {
+  const uint32_t id = tm_idesc(1, kUpdM, kUpdN);  // BF16 x BF16 -> FP32
+  for (int s = 0; s < S2 && ok; ++s) {
+    const uint32_t u = u0 + s, slot = u % kUpdStages, use = u / kUpdStages;
+    ok = tm_wait(su32(&sm.full[slot]), use & 1);
+    if (!ok) break;
     tm_fence_after();
-    const uint32_t id = tm_idesc(1, kUpdM, kUpdN);  // BF16 x BF16 -> FP32
+    const uint32_t sA = ring + slot * kStageBytes, sB = sA + kStageA;
+#pragma unroll
     for (int L = 2; L <= kSlices + 1; ++L) {
-      int first = 1;
+#pragma unroll
       for (int i = 1; i < L; ++i) {
         const int j = L - i;
-        for (int h = 0; h < 2; ++h) {
-          const int ka = 32 * (i - 1) + 16 * h, kbb = 32 * (j - 1) + 16 * h;
-          const uint64_t da = tm_desc(sA + (ka / 64) * kUpdAtomA + (ka % 64) * 2);
-          const uint64_t db = tm_desc(sB + (kbb / 64) * kUpdAtomB + (kbb % 64) * 2);
-          tm_mma_f16(tmem + static_cast<uint32_t>((L - 2) * kUpdN), da, db, id, first ? 0 : 1);
-          first = 0;
-        }
+        const uint64_t da = tm_desc(sA + ((i - 1) >> 2) * kAtomA + ((i - 1) & 3) * 32);
+        const uint64_t db = tm_desc(sB + ((j - 1) >> 2) * kAtomB + ((j - 1) & 3) * 32);
+        tm_mma_f16(tmem + static_cast<uint32_t>((L - 2) * kUpdN), da, db, id, (s == 0 && i == 1) ? 0 : 1);
       }
     }
+    tm_commit(su32(&sm.empty[slot]));
   }
-  tm_commit(bar_acc);
+  tm_commit(su32(&sm.acc));
   return ok;
 }
 
-// W[r, c] += (U V)[r, c] for every r < n and every column c < n outside
-// [kb, kb + jb), over the tiles [t_lo, t_hi) of this block (row-major order
-// of the ceil(n / 128) x ceil(n / 64) tiles). dyn: this block's dynamic shared
-// memory; err: the grid's error word.
+// W[r, c] += (U V)[r, c] over the tiles [t_lo, t_hi) of this block (row-major
+// order of the ceil(n / 128) x ut.ncbt tiles that ut names), every r < n and
+// every column c < n of those tiles outside [ut.mk, ut.mk + ut.mj). dyn: this
+// block's dynamic shared memory; err: the grid's error word.
 static __device__ __noinline__ void sliced_update(SliceSmem& sm, unsigned char* dyn, const CUtensorMap* map_a,
                                                   const CUtensorMap* map_b, const SliceBufs& sb, double* W, int n,
-                                                  int kb, int jb, int t_lo, int t_hi, int* err) {
+                                                  const UpdTiles ut, int t_lo, int t_hi, int* err) {
   if (t_lo >= t_hi) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ncb = (n + kUpdN - 1) / kUpdN;
+  const int S2 = 2 * ut.nc;                               // stages per tile
+  const int npre = S2 < kUpdStages ? S2 : kUpdStages;     // stages of the next tile loaded ahead
   const uint32_t raw = su32(dyn);
-  const uint32_t sA = (raw + 1023u) & ~1023u;
-  const uint32_t sB[2] = {sA + kUpdABytes, sA + kUpdABytes + kUpdBBytes};
-  double* Ts = reinterpret_cast<double*>(dyn + (sA - raw) + kUpdABytes + 2 * kUpdBBytes);  // [kUpdM][kUpdTsStride]
-  const uint32_t barA = su32(&sm.bar[0]), barB[2] = {su32(&sm.bar[1]), su32(&sm.bar[2])}, barAcc = su32(&sm.bar[3]);
-  uint32_t phA = sm.phase[0], phB[2] = {sm.phase[1], sm.phase[2]}, phAcc = sm.phase[3];
-  const uint32_t tmem = sm.tmem;
-  __syncthreads();  // everyone has read the phases
-
-  auto issue = [&](int t, bool with_a, int st) {
-    const int rb = t / ncb, cb = t % ncb;
-    if (with_a) {
-      tm_expect(barA, kUpdABytes);
-      for (int a = 0; a < 4; ++a) tm_load2d(sA + a * kUpdAtomA, map_a, barA, a * 64, rb * kUpdM);
-    }
-    tm_expect(barB[st], kUpdBBytes);
-    for (int a = 0; a < 4; ++a) tm_load2d(sB[st] + a * kUpdAtomB, map_b, barB[st], a * 64, cb * kUpdN);
+  const uint32_t ring = (raw + 1023u) & ~1023u;
+  double* Ts = reinterpret_cast<double*>(dyn + (ring - raw) + kUpdStages * kStageBytes);  // [kUpdM][kUpdTsStride]
+  const uint32_t u_base = sm.stages, tile_base = sm.tiles, tmem = sm.tmem;
+  const uint32_t bar_acc = su32(&sm.acc);
+  __syncthreads();  // everyone has read the counters
+  auto tile_of = [&](int t, int* rb, int* cb) {
+    *rb = t / ut.ncbt;
+    int c = ut.cb0 + t % ut.ncbt;
+    if (c >= ut.gap_at) c += ut.gap;
+    *cb = c;
   };
-
-  // thread 0: phases issued on each barrier (lifetime counts, like phA ...)
-  uint32_t isA = phA, isB[2] = {phB[0], phB[1]}, isAcc = phAcc;
-  if (tid == 0) {
-    fence_proxy_async_global();  // the digits other blocks wrote before the barrier, for the copies below
-    issue(t_lo, true, 0);
-    ++isA;
-    ++isB[0];
+  bool bad = false;         // this thread saw a wait run out
+  uint32_t produced = 0;    // thread 0: stages issued
+  uint32_t committed = 0;   // thread 32: tiles committed
+  {
+    int rb, cb;
+    tile_of(t_lo, &rb, &cb);
+    if (tid == 0) bad = !upd_produce_range(sm, ring, map_a, map_b, u_base, rb, cb, 0, S2, &produced);
+    if (tid == 32) {
+      bad = !upd_mma_tile(sm, ring, tmem, u_base, S2);
+      ++committed;
+    }
   }
-  if (tid == 32 && !tile_mmas(tmem, sA, sB[0], barA, true, phA, barB[0], phB[0], barAcc)) atomicExch(&sm.failed, 1);
-  ++phA;
-  ++phB[0];
-  ++isAcc;
-  bool failed = false;
+  int fail = 0, done_tiles = 0;
   for (int t = t_lo; t < t_hi; ++t) {
-    const int k = t - t_lo, st = k & 1;
-    const int rb = t / ncb, cb = t % ncb;
+    const int k = t - t_lo;
+    int rb, cb, nrb = 0, ncb = 0;
+    tile_of(t, &rb, &cb);
     const int r0 = rb * kUpdM, c0 = cb * kUpdN;
     const bool has_next = t + 1 < t_hi;
-    const bool next_new_a = has_next && ((t + 1) / ncb != rb);
-    if (tid == 0 && has_next && !next_new_a) {  // the other V stage is free: its last reader was tile t - 1
-      issue(t + 1, false, st ^ 1);
-      ++isB[st ^ 1];
-    }
+    if (has_next) tile_of(t + 1, &nrb, &ncb);
+    const uint32_t u_next = u_base + static_cast<uint32_t>((k + 1) * S2);
     if (tid < kUpdN) sm.ecol[tid] = c0 + tid < n ? sb.bexp[c0 + tid] : 0;
     // tcgen05.ld is warp-collective: a warp reads the accumulators only if all its lanes saw them ready
-    const bool acc_ok = __all_sync(0xffffffffu, tm_wait(barAcc, phAcc & 1));
-    ++phAcc;
+    const bool acc_ok = __all_sync(0xffffffffu, tm_wait(bar_acc, (tile_base + k) & 1));
     tm_fence_after();
-    if (!acc_ok) atomicExch(&sm.failed, 1);
-    if (tid == 0 && has_next && next_new_a) {  // the U tile is free once this tile's MMAs are done
-      issue(t + 1, true, st ^ 1);
-      ++isA;
-      ++isB[st ^ 1];
-    }
+    bad = bad || !acc_ok;
+    // the ring is free (all of this tile's MMAs are done): the next tile's first stages
+    if (tid == 0 && has_next && !bad)
+      bad = !upd_produce_range(sm, ring, map_a, map_b, u_next, nrb, ncb, 0, npre, &produced);
     __syncthreads();  // the column exponents are in shared memory
     // levels -> exact dot products -> FP64, staged in Ts (warp w: TMEM lanes
     // 32 (w % 4) .. + 31 = tile rows, columns half (w / 4))
@@ -217,7 +276,14 @@ static __device__ __noinline__ void sliced_update(SliceSmem& sm, unsigned char* 
         tm_ld_wait();
         for (int e = 0; e < 8; ++e) {
           int32_t c[kSliceLevels];
-          for (int L = 0; L < kSliceLevels; ++L) c[L] = level_int(__uint_as_float(v[L][e]));
+          bool wide = false;  // a level sum above 2^22 (K > 32 only): the two-part conversion
+          for (int L = 0; L < kSliceLevels; ++L) {
+            const float f = __uint_as_float(v[L][e]);
+            wide = wide || fabsf(f) > 4194304.0f;
+            c[L] = level_int(f);
+          }
+          if (wide)
+            for (int L = 0; L < kSliceLevels; ++L) c[L] = level_int_wide(__uint_as_float(v[L][e]));
           Ts[lrow * kUpdTsStride + cc + e] = combine_levels_fp(c, er, sm.ecol[cc + e]);
         }
       }
@@ -227,8 +293,8 @@ static __device__ __noinline__ void sliced_update(SliceSmem& sm, unsigned char* 
     // W += Ts: warp w takes rows w, w + 8, ..., lanes along the row
     // (coalesced). All 32 loads of a thread are issued before any store, so
     // their latencies overlap (the compiler may not move a load above a store
-    // to memory it cannot prove distinct); the next tile's MMAs are issued
-    // while these loads are in flight.
+    // to memory it cannot prove distinct); meanwhile thread 0 loads the next
+    // tile's remaining stages and thread 32 issues its MMAs.
     constexpr int kPer = (kUpdM / 8) * 2;  // 16 rows x 2 column halves per thread
     double wv[kPer];
     if (acc_ok) {
@@ -236,49 +302,52 @@ static __device__ __noinline__ void sliced_update(SliceSmem& sm, unsigned char* 
       for (int it = 0; it < kPer; ++it) {
         const int rr = warp + 8 * (it >> 1), c = lane + 32 * (it & 1);
         const int gr = r0 + rr, gc = c0 + c;
-        const bool ok = gr < n && gc < n && (gc < kb || gc >= kb + jb);
+        const bool ok = gr < n && gc < n && (gc < ut.mk || gc >= ut.mk + ut.mj);
         wv[it] = ok ? __ldcg(W + (int64_t)gr * n + gc) : 0.0;
       }
     }
-    if (has_next) {
-      if (tid == 32 && sm.failed == 0 &&
-          !tile_mmas(tmem, sA, sB[st ^ 1], barA, next_new_a, phA, barB[st ^ 1], phB[st ^ 1], barAcc))
-        atomicExch(&sm.failed, 1);
-      if (next_new_a) ++phA;
-      ++phB[st ^ 1];
-      ++isAcc;
+    if (has_next && !bad) {
+      if (tid == 0) bad = !upd_produce_range(sm, ring, map_a, map_b, u_next, nrb, ncb, npre, S2, &produced);
+      if (tid == 32) {
+        bad = !upd_mma_tile(sm, ring, tmem, u_next, S2);
+        ++committed;
+      }
     }
     if (acc_ok) {
 #pragma unroll
       for (int it = 0; it < kPer; ++it) {
         const int rr = warp + 8 * (it >> 1), c = lane + 32 * (it & 1);
         const int gr = r0 + rr, gc = c0 + c;
-        if (gr < n && gc < n && (gc < kb || gc >= kb + jb))
+        if (gr < n && gc < n && (gc < ut.mk || gc >= ut.mk + ut.mj))
           W[(int64_t)gr * n + gc] = wv[it] + Ts[rr * kUpdTsStride + c];
       }
     }
-    __syncthreads();  // Ts free for the next tile
-    failed = sm.failed != 0;
-    if (failed) break;
+    ++done_tiles;
+    fail = __syncthreads_or(bad ? 1 : 0);  // also: Ts free for the next tile
+    if (fail) break;
   }
-  if (failed) {
+  if (fail) {
     // wait (bounded) for this block's copies and MMAs still in flight: the
-    // last phase issued on each barrier (a completed phase returns at once)
+    // last stages issued (each the latest use of its slot) and the last
+    // tile committed, then report the failure
+    if (tid == 32) sm.ecol[0] = static_cast<int32_t>(committed);
+    __syncthreads();
     if (tid == 0) {
-      if (isA > sm.phase[0]) tm_wait(barA, (isA - 1) & 1);
-      for (int s2 = 0; s2 < 2; ++s2)
-        if (isB[s2] > sm.phase[1 + s2]) tm_wait(barB[s2], (isB[s2] - 1) & 1);
-      if (isAcc > sm.phase[3]) tm_wait(barAcc, (isAcc - 1) & 1);
+      const uint32_t last = static_cast<uint32_t>(sm.ecol[0]);
+      const uint32_t first = produced > kUpdStages ? produced - kUpdStages : 0;
+      for (uint32_t p = first; p < produced; ++p) {
+        const uint32_t u = u_base + p;
+        tm_wait(su32(&sm.full[u % kUpdStages]), (u / kUpdStages) & 1);
+      }
+      if (last > 0) tm_wait(bar_acc, (tile_base + last - 1) & 1);
       atomicExch(err, 1);
     }
   }
   if (tid == 0) {
-    // the phases this block's barriers have completed (after a failure they
-    // no longer matter: the kernel skips every later update)
-    sm.phase[0] = phA;
-    sm.phase[1] = phB[0];
-    sm.phase[2] = phB[1];
-    sm.phase[3] = phAcc;
+    // lifetime counts (after a failure they no longer matter: the kernel
+    // skips every later update)
+    sm.stages = u_base + static_cast<uint32_t>(done_tiles * S2);
+    sm.tiles = tile_base + static_cast<uint32_t>(done_tiles);
   }
   __syncthreads();
 }

@@ -46,6 +46,7 @@ double h_sliced_dot(const double* u, const double* v, int k) {
 }
 
 int32_t h_level_int(float v) { return lg::level_int(v); }
+int32_t h_level_int_wide(float v) { return lg::level_int_wide(v); }
 double h_exact_int_to_double(int64_t x) { return lg::exact_int_to_double(x); }
 
 // the integer-only split against the FP64-scaled one: fixed-point integers

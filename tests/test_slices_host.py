@@ -52,6 +52,8 @@ def h():
     L.h_levels_to_double.restype = ctypes.c_int
     L.h_levels_to_double.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, p]
     L.h_combine_both.argtypes = [p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, p]
+    L.h_level_int_wide.restype = ctypes.c_int32
+    L.h_level_int_wide.argtypes = [ctypes.c_float]
     L.h_exact_int_to_double.restype = ctypes.c_double
     L.h_exact_int_to_double.argtypes = [ctypes.c_int64]
     L.h_levels32_agree.restype = ctypes.c_int
@@ -241,3 +243,13 @@ def test_exact_int_to_double(h):
     xs += [int(v) >> int(s) for v, s in zip(rng.integers(-(2 ** 53) + 1, 2 ** 53, 2000), rng.integers(0, 53, 2000))]
     for x in xs:
         assert h.h_exact_int_to_double(x) == float(x), x
+
+
+def test_level_sums_over_four_chunks(h):
+    # a K = 128 update accumulates four chunks of 32 terms per level: sums up
+    # to 4 * 2^22 = 2^24, still exact in FP32, converted by the two-part route
+    rng = np.random.default_rng(10)
+    vals = [0, 1, -1, 2 ** 24, -(2 ** 24), 2 ** 24 - 1, -(2 ** 24 - 1), 2 ** 23 + 1, 4095, 4096, 4097, -2049, 2048]
+    vals += [int(v) for v in rng.integers(-(2 ** 24), 2 ** 24 + 1, 20000)]
+    for v in vals:
+        assert h.h_level_int_wide(float(v)) == v, v
