@@ -274,17 +274,24 @@ static __device__ __noinline__ void sliced_update(SliceSmem& sm, unsigned char* 
         for (int L = 0; L < kSliceLevels; ++L)
           tm_ld8(tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) + static_cast<uint32_t>(L * kUpdN + cc), v[L]);
         tm_ld_wait();
-        for (int e = 0; e < 8; ++e) {
-          int32_t c[kSliceLevels];
-          bool wide = false;  // a level sum above 2^22 (K > 32 only): the two-part conversion
-          for (int L = 0; L < kSliceLevels; ++L) {
-            const float f = __uint_as_float(v[L][e]);
-            wide = wide || fabsf(f) > 4194304.0f;
-            c[L] = level_int(f);
-          }
-          if (wide)
+        // a level sum above 2^22 (possible for K > 32 only) needs the two-part
+        // conversion: one vote per warp and column group picks the loop
+        bool wide = false;
+        if (ut.nc > 1)
+          for (int L = 0; L < kSliceLevels; ++L)
+            for (int e = 0; e < 8; ++e) wide |= fabsf(__uint_as_float(v[L][e])) > 4194304.0f;
+        if (__any_sync(0xffffffffu, wide)) {
+          for (int e = 0; e < 8; ++e) {
+            int32_t c[kSliceLevels];
             for (int L = 0; L < kSliceLevels; ++L) c[L] = level_int_wide(__uint_as_float(v[L][e]));
-          Ts[lrow * kUpdTsStride + cc + e] = combine_levels_fp(c, er, sm.ecol[cc + e]);
+            Ts[lrow * kUpdTsStride + cc + e] = combine_levels_fp(c, er, sm.ecol[cc + e]);
+          }
+        } else {
+          for (int e = 0; e < 8; ++e) {
+            int32_t c[kSliceLevels];
+            for (int L = 0; L < kSliceLevels; ++L) c[L] = level_int(__uint_as_float(v[L][e]));
+            Ts[lrow * kUpdTsStride + cc + e] = combine_levels_fp(c, er, sm.ecol[cc + e]);
+          }
         }
       }
     }
