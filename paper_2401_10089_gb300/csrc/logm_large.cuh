@@ -152,17 +152,18 @@ inline EncodeTiledFn tensor_map_encoder() {
   return fn;
 }
 
-// 2-D map over a digit buffer: n_max rows of kDigRow BF16, box of 64 BF16
-// (128 bytes) x box_rows, 128-byte swizzle, zero fill outside.
-inline bool digit_map(CUtensorMap* m, void* base, int n_max, int box_rows) {
+// 2-D map over a digit buffer: n_max rows of kDigRow BF16, box of box_x BF16
+// x box_rows, 128-byte (box_x = 64) or 32-byte (box_x = 16) swizzle, zero
+// fill outside.
+inline bool digit_map(CUtensorMap* m, void* base, int n_max, int box_x, int box_rows) {
   EncodeTiledFn f = tensor_map_encoder();
   if (!f) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)kDigRow, (cuuint64_t)n_max};
   const cuuint64_t strides[1] = {(cuuint64_t)kDigRow * 2};
-  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           box_x == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -205,8 +206,8 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
   memset(&maps, 0, sizeof(maps));
   if (SLICED)
     for (int t = 0; t < 2; ++t)
-      if (!digit_map(&maps.a[t], ws + L.g[t].adig, p.n_max, kUpdM) ||
-          !digit_map(&maps.b[t], ws + L.g[t].bdig, p.n_max, kUpdN))
+      if (!digit_map(&maps.a[t], ws + L.g[t].adig, p.n_max, 64, kUpdM) ||
+          !digit_map(&maps.b[t], ws + L.g[t].bdig, p.n_max, 16, kUpdN))
         return cudaErrorNotSupported;
   w.n_max = p.n_max;
   const int64_t nn = (int64_t)p.n_max * p.n_max;

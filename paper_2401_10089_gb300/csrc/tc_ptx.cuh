@@ -32,6 +32,18 @@ static __device__ __forceinline__ uint64_t tm_desc(uint32_t saddr) {
   return d;
 }
 
+// The same for the 32-byte swizzle layout (rows of 16 BF16 = 32 B, 8-row
+// groups 256 B apart): layout type 6.
+static __device__ __forceinline__ uint64_t tm_desc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(256 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(6) << 61;
+  return d;
+}
+
 // Instruction descriptor: FP32 accumulator, A and B of format fmt (kind::tf32:
 // 2 = TF32; kind::f16: 0 = F16, 1 = BF16), both K-major, M x N.
 static __device__ __forceinline__ uint32_t tm_idesc(uint32_t fmt, int M, int N) {

@@ -9,13 +9,17 @@
 // digit s of that half at 16 s). Each block then runs its share of the
 // 128 x 64 output tiles of W:
 //   * thread 0 streams the digits through a ring of kUpdStages shared-memory
-//     stages with TMA, one stage per (chunk, half): 128 x 128 BF16 of U and
-//     64 x 128 of V, two 128-byte swizzle boxes each;
-//   * thread 32 issues, per stage, 36 tcgen05.mma (kind::f16, BF16 x BF16 ->
-//     FP32, M = 128, N = 64, K = 16): for every level L = i + j of the digit
-//     pairs (i, j) one MMA into that level's 64 TMEM columns (8 levels = all
-//     512 columns), accumulated over all stages of the tile. A level sum is an
-//     integer of magnitude <= nc 2^22 <= 2^24, so FP32 accumulation is exact;
+//     stages with TMA, one stage per (chunk, half): 128 x 128 BF16 of U (two
+//     128-byte swizzle boxes, 4 digits x 16 terms per row) and 64 x 128 of V
+//     (eight 32-byte swizzle boxes, one per digit: the digits' 64 columns
+//     stacked as 512 operand rows);
+//   * thread 32 issues, per stage, 12 tcgen05.mma (kind::f16, BF16 x BF16 ->
+//     FP32, M = 128, K = 16): digit i of U against the digits j = 1 .. 9 - i
+//     of V in pieces of up to four (N = 64 per digit, up to 256), written at
+//     TMEM column 64 (i + j - 2), so that the pair (i, j) lands in the 64
+//     columns of its level L = i + j (8 levels = all 512 columns),
+//     accumulated over all stages of the tile. A level sum is an integer of
+//     magnitude <= nc 2^22 <= 2^24, so FP32 accumulation is exact;
 //   * all eight warps read the levels back (tcgen05.ld), combine them into the
 //     exact integer dot product and round it to FP64 into a shared-memory
 //     tile; then the next tile's MMAs run while the warps add the staged tile
@@ -40,8 +44,9 @@ constexpr int kMaxChunks = 4;                                // K of one update:
 constexpr int kChunkDig = kSlices * kSliceK;                 // digits of one chunk of a row: 256 BF16
 constexpr int kDigRow = kMaxChunks * kChunkDig;              // digit buffer row: 1024 BF16
 constexpr int kUpdStages = 3;                                // TMA ring depth
-constexpr uint32_t kAtomA = kUpdM * 128, kAtomB = kUpdN * 128;  // one 128-byte swizzle box (4 digits x 16 terms)
-constexpr uint32_t kStageA = 2 * kAtomA, kStageB = 2 * kAtomB;  // half a chunk: 32 KB + 16 KB
+constexpr uint32_t kAtomA = kUpdM * 128;       // U: one 128-byte swizzle box (4 digits x 16 terms per row)
+constexpr uint32_t kDigB = kUpdN * 32;          // V: one digit of 16 terms for 64 columns (32-byte swizzle)
+constexpr uint32_t kStageA = 2 * kAtomA, kStageB = kSlices * kDigB;  // half a chunk: 32 KB + 16 KB
 constexpr uint32_t kStageBytes = kStageA + kStageB;
 constexpr int kUpdTsStride = kUpdN + 1;                      // staged tile: doubles per row (padded)
 constexpr uint32_t kUpdTsBytes = kUpdM * kUpdTsStride * 8;   // 65 KB
@@ -51,7 +56,7 @@ static_assert(kUpdTmemCols == 512, "eight levels of 64 columns fill TMEM");
 static_assert(kSlices == 8, "a stage holds two swizzle boxes of four digits");
 
 // Tensor maps of the digit buffers, per inversion group (2-D: kDigRow x n_max
-// BF16, boxes of 64 x 128 rows for U and 64 x 64 for V, 128-byte swizzle).
+// BF16; U: boxes of 64 x 128 rows, 128-byte swizzle; V: 16 x 64, 32-byte swizzle).
 struct SliceMaps {
   CUtensorMap a[2];
   CUtensorMap b[2];
@@ -161,8 +166,7 @@ static __device__ __forceinline__ bool upd_produce(SliceSmem& sm, uint32_t ring,
   tm_expect(fb, kStageBytes);
   tm_load2d(sA, map_a, fb, x, rb * kUpdM);
   tm_load2d(sA + kAtomA, map_a, fb, x + 64, rb * kUpdM);
-  tm_load2d(sB, map_b, fb, x, cb * kUpdN);
-  tm_load2d(sB + kAtomB, map_b, fb, x + 64, cb * kUpdN);
+  for (int j = 0; j < kSlices; ++j) tm_load2d(sB + j * kDigB, map_b, fb, x + 16 * j, cb * kUpdN);
   return true;
 }
 
@@ -179,14 +183,16 @@ static __device__ __noinline__ bool upd_produce_range(SliceSmem& sm, uint32_t ri
 }
 
 // Thread 32: the MMAs of a tile, stage by stage as they arrive: per stage (a
-// half chunk), for each level L = i + j every digit pair (i, j) of that
-// half, 36 MMAs into the level's 64 TMEM columns; the tile's first stage
-// starts every level's sum. Each stage's commit frees its slot; the final
-// commit arrives on acc once all are done (also after a wait ran out, so that
-// the readers are released; the result is then false).
+// half chunk) and digit i of U, digit i against the digits j = 1 .. 9 - i of
+// V in pieces of up to four (one MMA each, N = 64 per digit) at TMEM column
+// 64 (i + j - 2): 12 MMAs covering the 36 pairs of levels 2 .. 9. In the
+// tile's first stage the two pieces of digit 1 write every level once and
+// start the sums (no accumulate); every other MMA accumulates. Each stage's
+// commit frees its slot; the final commit arrives on acc once all are done
+// (also after a wait ran out, so that the readers are released; the result is
+// then false).
 static __device__ __noinline__ bool upd_mma_tile(SliceSmem& sm, uint32_t ring, uint32_t tmem, uint32_t u0, int S2) {
   bool ok = true;
-  const uint32_t id = tm_idesc(1, kUpdM, kUpdN);  // BF16 x BF16 -> FP32
   for (int s = 0; s < S2 && ok; ++s) {
     const uint32_t u = u0 + s, slot = u % kUpdStages, use = u / kUpdStages;
     ok = tm_wait(su32(&sm.full[slot]), use & 1);
@@ -194,13 +200,14 @@ static __device__ __noinline__ bool upd_mma_tile(SliceSmem& sm, uint32_t ring, u
     tm_fence_after();
     const uint32_t sA = ring + slot * kStageBytes, sB = sA + kStageA;
 #pragma unroll
-    for (int L = 2; L <= kSlices + 1; ++L) {
+    for (int i = 1; i <= kSlices; ++i) {
+      const uint64_t da = tm_desc(sA + ((i - 1) >> 2) * kAtomA + ((i - 1) & 3) * 32);
 #pragma unroll
-      for (int i = 1; i < L; ++i) {
-        const int j = L - i;
-        const uint64_t da = tm_desc(sA + ((i - 1) >> 2) * kAtomA + ((i - 1) & 3) * 32);
-        const uint64_t db = tm_desc(sB + ((j - 1) >> 2) * kAtomB + ((j - 1) & 3) * 32);
-        tm_mma_f16(tmem + static_cast<uint32_t>((L - 2) * kUpdN), da, db, id, (s == 0 && i == 1) ? 0 : 1);
+      for (int j0 = 1; j0 <= kSlices + 1 - i; j0 += 4) {
+        const int cnt = (kSlices + 2 - i - j0) < 4 ? (kSlices + 2 - i - j0) : 4;
+        const uint64_t db = tm_desc_sw32(sB + (j0 - 1) * kDigB);
+        tm_mma_f16(tmem + static_cast<uint32_t>((i + j0 - 2) * kUpdN), da, db, tm_idesc(1, kUpdM, kUpdN * cnt),
+                   (s == 0 && i == 1) ? 0 : 1);
       }
     }
     tm_commit(su32(&sm.empty[slot]));
