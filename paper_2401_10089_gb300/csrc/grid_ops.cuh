@@ -71,7 +71,7 @@ struct GridSmem {
   double bc[4];
   int work[4];
   unsigned long long ep[3];  // barrier episodes seen: whole grid, group 0, group 1
-  int winner;                // block holding the pivot candidate of the current column
+  int pivot_row;             // pivot row of the current Gauss-Jordan column (-1: no valid pivot)
   SliceSmem slc;             // tensor-core updates: barriers, phases, TMEM base
   int skip_upd;              // the grid's error word was set: no more tensor-core work
   int psrc[2 * kGridPanel];  // rows traced back through a panel's swaps
@@ -558,53 +558,80 @@ struct GridOps {
       double* Sout = buf ? Sp0 : Sp1;
       const unsigned long long* cvv = g.cand_v + buf * kMaxGrid;
       const int* cii = g.cand_i + buf * kMaxGrid;
-      // pivot: the largest candidate (smallest row on ties), and the row of position k
-      unsigned long long pv;
-      int p;
-      {
-        unsigned long long cv = 0;
-        int ci = 0x7fffffff;
-        for (int q = threadIdx.x; q < G; q += kThreads)
-          if (key_better(cvv[q], cii[q], cv, ci)) { cv = cvv[q]; ci = cii[q]; }
-        if (threadIdx.x < jb) S.rowk[threadIdx.x] = g.row_k[buf * kGridPanel + threadIdx.x];
-        block_argmax_key(cv, ci, S.red, &pv, &p);
-      }
-      if (pv == 0 || pv >= 0x7FF0000000000000ull || p < k || p >= n) return 1;  // zero, Inf or NaN
-      // warp 0: the winner's row, the reciprocal of the pivot (the same
-      // division in every lane: one warp instruction sequence) and the
-      // scaled pivot row; one block barrier publishes them
+      // warp 0: the pivot (the largest candidate, smallest row on ties: a
+      // warp argmax over the group's candidates, the same in every lane),
+      // the winner's row, the reciprocal of the pivot (the same division in
+      // every lane) and the scaled pivot row; warp 1: the row of position k.
+      // One block barrier publishes them.
       if (threadIdx.x < 32) {
         const int t = threadIdx.x;
+        unsigned long long pv = 0;
+        int p = 0x7fffffff;
+        for (int q = t; q < G; q += 32)
+          if (key_better(cvv[q], cii[q], pv, p)) {
+            pv = cvv[q];
+            p = cii[q];
+          }
+        for (int o = 16; o; o >>= 1) {
+          const unsigned long long ov = __shfl_xor_sync(0xffffffffu, pv, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, p, o);
+          if (key_better(ov, oi, pv, p)) {
+            pv = ov;
+            p = oi;
+          }
+        }
+        const bool ok = !(pv == 0 || pv >= 0x7FF0000000000000ull || p < k || p >= n);  // zero, Inf or NaN
         const double rp =
-            t < jb ? g.cand_row[((int64_t)buf * kMaxGrid + p / rows_per) * kGridPanel + t] : 0.0;
+            (ok && t < jb) ? g.cand_row[((int64_t)buf * kMaxGrid + p / rows_per) * kGridPanel + t] : 0.0;
         const double pivot = __shfl_sync(0xffffffffu, rp, c);
         const double rinv = 1.0 / pivot;
         if (t < jb) S.prow[t] = (t == c) ? rinv : rp * rinv;
-        if (t == 0) S.bc[0] = rinv;
-        if (glead) {
+        if (t == 0) {
+          S.bc[0] = rinv;
+          S.pivot_row = ok ? p : -1;
+        }
+        if (glead && ok) {
           g.pivval[k] = pivot;
           g.piv[k] = p;
         }
+      } else if (threadIdx.x < 64) {
+        const int t = threadIdx.x - 32;
+        if (t < jb) S.rowk[t] = g.row_k[buf * kGridPanel + t];
       }
       __syncthreads();
+      const int p = S.pivot_row;
+      if (p < 0) return 1;
       const double inv = S.bc[0];
+      // elimination of this block's rows: warp w takes rows w, w + 8, ..., lane
+      // = column; lane c + 1 keeps the next column's candidate
       unsigned long long cv = 0;
       int ci = 0x7fffffff;
-      for (int e = threadIdx.x; e < my_rows * jb; e += kThreads) {
-        const int rr = e / jb, cc = e % jb;
-        const int r = r_lo + rr;
-        double val;
-        if (r == k) {
-          val = S.prow[cc];
-        } else {
-          const double srcv = (r == p) ? S.rowk[cc] : Sin[rr * kGridPanel + cc];
-          const double f = (r == p) ? S.rowk[c] : Sin[rr * kGridPanel + c];
-          val = (cc == c) ? -f * inv : fma(-f, S.prow[cc], srcv);
-        }
-        Sout[rr * kGridPanel + cc] = val;
-        if (cc == c + 1 && r > k) {
-          const unsigned long long a = abs_key(val);
-          if (key_better(a, r, cv, ci)) { cv = a; ci = r; }
+      {
+        const int lane = threadIdx.x & 31;
+        const bool act = lane < jb;
+        const double prow = act ? S.prow[lane] : 0.0;
+        const double rowk = act ? S.rowk[lane] : 0.0;
+        const double rowk_c = S.rowk[c];
+        for (int rr = threadIdx.x >> 5; rr < my_rows; rr += kWarps) {
+          const int r = r_lo + rr;
+          double val = 0.0;
+          if (act) {
+            if (r == k) {
+              val = prow;
+            } else {
+              const double srcv = (r == p) ? rowk : Sin[rr * kGridPanel + lane];
+              const double f = (r == p) ? rowk_c : Sin[rr * kGridPanel + c];
+              val = (lane == c) ? -f * inv : fma(-f, prow, srcv);
+            }
+            Sout[rr * kGridPanel + lane] = val;
+          }
+          if (lane == c + 1 && r > k) {
+            const unsigned long long a = abs_key(val);
+            if (key_better(a, r, cv, ci)) {
+              cv = a;
+              ci = r;
+            }
+          }
         }
       }
       if (c + 1 < jb) {
