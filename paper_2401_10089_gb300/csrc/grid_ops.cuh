@@ -23,6 +23,7 @@
 namespace lg {
 
 constexpr int kGridPanel = 32;          // Gauss-Jordan panel width for large n
+constexpr int kSpStride = kGridPanel + 1;  // doubles per row of a panel in shared memory (column walks conflict-free)
 constexpr int kSuperCols = kMaxChunks * kGridPanel;  // tensor-core form: columns of a super-panel
 static_assert(kGridPanel == kSliceK, "a panel is one chunk of the tensor-core updates");
 constexpr int kColGroups = 16;          // row groups of the column passes (norms, transposed mat-vecs, updates)
@@ -92,7 +93,7 @@ struct GjCtx {
 
 // Dynamic shared memory of the whole-GPU kernel, used by one phase at a time:
 // this block's rows of the current Gauss-Jordan panel (row-major, two buffers
-// of rows_per x kGridPanel) and, in the tensor-core form, the transposed rows
+// of rows_per x kSpStride) and, in the tensor-core form, the transposed rows
 // of the earlier sub-panels' factors after them; the stage ring and staged
 // tile of the tensor-core updates; the DMMA tiles of the FP64-pipe products.
 extern __shared__ double grid_panel_smem[];
@@ -140,6 +141,38 @@ static __device__ void bounded_barrier(unsigned long long* bar, unsigned nblocks
   }
   // the acquire load that saw every arrival orders thread 0 after the other
   // blocks' releases; the block barrier orders the other threads after it
+  __syncthreads();
+}
+
+// bounded_barrier in two halves, so that a block can work between its
+// arrival and the wait: barrier_arrive publishes the block's writes (block
+// barrier, then thread 0's release add), barrier_wait polls for the others
+// (the same bound) and ends with a block barrier.
+static __device__ void barrier_arrive(unsigned long long* bar, unsigned nblocks, int* err, unsigned long long* ep) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *ep += 1;
+    if (*(volatile int*)err == 0) red_release_add(bar, 1ull);
+  }
+}
+static __device__ void barrier_wait(unsigned long long* bar, unsigned nblocks, int* err, unsigned long long* ep,
+                                    unsigned long long timeout_ns = kBarrierTimeoutNs) {
+  if (threadIdx.x == 0) {
+    volatile int* verr = err;
+    const unsigned long long target = *ep * nblocks;
+    if (*verr == 0) {
+      const unsigned long long t0 = global_ns();
+      unsigned long long polls = 0;
+      while (ld_acquire(bar) < target) {
+        if (*verr) break;
+        ++polls;
+        if (((polls & 63) == 0 && global_ns() - t0 > timeout_ns) || polls > kBarrierMaxPolls) {
+          atomicExch(err, 1);
+          break;
+        }
+      }
+    }
+  }
   __syncthreads();
 }
 
@@ -533,7 +566,7 @@ struct GridOps {
         const int rr = e / jb, c = e % jb;
         const int r = r_lo + rr;
         const double v = W[(int64_t)r * n + kb + c];
-        Sp0[rr * kGridPanel + c] = v;
+        Sp0[rr * kSpStride + c] = v;
         if (c == 0 && r >= kb) {
           const unsigned long long a = abs_key(v);
           if (key_better(a, r, cv, ci)) { cv = a; ci = r; }
@@ -547,10 +580,18 @@ struct GridOps {
         g.cand_i[lb] = bi;
       }
       if (bi >= r_lo && bi < r_hi && threadIdx.x < jb)
-        g.cand_row[(int64_t)lb * kGridPanel + threadIdx.x] = Sp0[(bi - r_lo) * kGridPanel + threadIdx.x];
-      if (kb >= r_lo && kb < r_hi && threadIdx.x < jb) g.row_k[threadIdx.x] = Sp0[(kb - r_lo) * kGridPanel + threadIdx.x];
+        g.cand_row[(int64_t)lb * kGridPanel + threadIdx.x] = Sp0[(bi - r_lo) * kSpStride + threadIdx.x];
+      if (kb >= r_lo && kb < r_hi && threadIdx.x < jb) g.row_k[threadIdx.x] = Sp0[(kb - r_lo) * kSpStride + threadIdx.x];
     }
     bounded_barrier(bar, gn, w.err, ep);
+    // The elimination of a column but its look-ahead column is deferred to
+    // the next step, where warps 1 .. 7 finish it while warp 0 finds the next
+    // pivot; its operands are kept in registers (lane = column).
+    bool dpend = false;
+    double d_prow = 0.0, d_rowk = 0.0, d_rowkc = 0.0, d_inv = 0.0;
+    int d_p = 0, d_k = 0, d_c = 0;
+    const double* d_in = Sp0;
+    double* d_out = Sp1;
     for (int c = 0; c < jb; ++c) {
       const int k = kb + c;
       const int buf = c & 1;
@@ -561,8 +602,9 @@ struct GridOps {
       // warp 0: the pivot (the largest candidate, smallest row on ties: a
       // warp argmax over the group's candidates, the same in every lane),
       // the winner's row, the reciprocal of the pivot (the same division in
-      // every lane) and the scaled pivot row; warp 1: the row of position k.
-      // One block barrier publishes them.
+      // every lane) and the scaled pivot row; warp 1: the row of position k;
+      // warps 1 .. 7: the previous column's deferred elimination. One block
+      // barrier publishes them.
       if (threadIdx.x < 32) {
         const int t = threadIdx.x;
         unsigned long long pv = 0;
@@ -594,38 +636,52 @@ struct GridOps {
           g.pivval[k] = pivot;
           g.piv[k] = p;
         }
-      } else if (threadIdx.x < 64) {
-        const int t = threadIdx.x - 32;
-        if (t < jb) S.rowk[t] = g.row_k[buf * kGridPanel + t];
+      } else {
+        if (threadIdx.x < 64) {
+          const int t = threadIdx.x - 32;
+          if (t < jb) S.rowk[t] = g.row_k[buf * kGridPanel + t];
+        }
+        if (dpend) {
+          const int lane = threadIdx.x & 31;
+          if (lane < jb && lane != d_c + 1)
+            for (int rr = (threadIdx.x >> 5) - 1; rr < my_rows; rr += kWarps - 1) {
+              const int r = r_lo + rr;
+              double v;
+              if (r == d_k) {
+                v = d_prow;
+              } else {
+                const double srcv = (r == d_p) ? d_rowk : d_in[rr * kSpStride + lane];
+                const double f = (r == d_p) ? d_rowkc : d_in[rr * kSpStride + d_c];
+                v = (lane == d_c) ? -f * d_inv : fma(-f, d_prow, srcv);
+              }
+              d_out[rr * kSpStride + lane] = v;
+            }
+        }
       }
       __syncthreads();
       const int p = S.pivot_row;
       if (p < 0) return 1;
       const double inv = S.bc[0];
-      // elimination of this block's rows: warp w takes rows w, w + 8, ..., lane
-      // = column; lane c + 1 keeps the next column's candidate
-      unsigned long long cv = 0;
-      int ci = 0x7fffffff;
-      {
-        const int lane = threadIdx.x & 31;
-        const bool act = lane < jb;
-        const double prow = act ? S.prow[lane] : 0.0;
-        const double rowk = act ? S.rowk[lane] : 0.0;
-        const double rowk_c = S.rowk[c];
-        for (int rr = threadIdx.x >> 5; rr < my_rows; rr += kWarps) {
+      // One element of the elimination: row rr (global r) of the block, column cc.
+      auto elim = [&](int rr, int r, int cc) -> double {
+        if (r == k) return S.prow[cc];
+        const double srcv = (r == p) ? S.rowk[cc] : Sin[rr * kSpStride + cc];
+        const double f = (r == p) ? S.rowk[c] : Sin[rr * kSpStride + c];
+        return (cc == c) ? -f * inv : fma(-f, S.prow[cc], srcv);
+      };
+      const int c1 = c + 1;
+      if (c1 < jb) {
+        // look-ahead: column c + 1 of every row first (lane = row), its
+        // candidate, then the candidate's full row and the row of position
+        // k + 1, published; the block arrives at the group barrier, and the
+        // rest of this column's elimination waits for the next step
+        unsigned long long cv = 0;
+        int ci = 0x7fffffff;
+        for (int rr = threadIdx.x; rr < my_rows; rr += kThreads) {
           const int r = r_lo + rr;
-          double val = 0.0;
-          if (act) {
-            if (r == k) {
-              val = prow;
-            } else {
-              const double srcv = (r == p) ? rowk : Sin[rr * kGridPanel + lane];
-              const double f = (r == p) ? rowk_c : Sin[rr * kGridPanel + c];
-              val = (lane == c) ? -f * inv : fma(-f, prow, srcv);
-            }
-            Sout[rr * kGridPanel + lane] = val;
-          }
-          if (lane == c + 1 && r > k) {
+          const double val = elim(rr, r, c1);
+          Sout[rr * kSpStride + c1] = val;
+          if (r > k) {
             const unsigned long long a = abs_key(val);
             if (key_better(a, r, cv, ci)) {
               cv = a;
@@ -633,23 +689,44 @@ struct GridOps {
             }
           }
         }
-      }
-      if (c + 1 < jb) {
         unsigned long long bv;
         int bi;
-        block_argmax_key(cv, ci, S.red, &bv, &bi);  // ends with a block barrier: Sout is complete
-        const int nb = (c + 1) & 1;
+        block_argmax_key(cv, ci, S.red, &bv, &bi);
+        const int nb = c1 & 1;
         if (threadIdx.x == 0) {
           g.cand_v[nb * kMaxGrid + lb] = bv;
           g.cand_i[nb * kMaxGrid + lb] = bi;
         }
-        if (bi >= r_lo && bi < r_hi && threadIdx.x < jb)
-          g.cand_row[((int64_t)nb * kMaxGrid + lb) * kGridPanel + threadIdx.x] =
-              Sout[(bi - r_lo) * kGridPanel + threadIdx.x];
-        if (k + 1 >= r_lo && k + 1 < r_hi && threadIdx.x < jb)
-          g.row_k[nb * kGridPanel + threadIdx.x] = Sout[(k + 1 - r_lo) * kGridPanel + threadIdx.x];
+        if (threadIdx.x < 32) {
+          if (bi >= r_lo && bi < r_hi && threadIdx.x < jb)
+            g.cand_row[((int64_t)nb * kMaxGrid + lb) * kGridPanel + threadIdx.x] = elim(bi - r_lo, bi, threadIdx.x);
+        } else if (threadIdx.x < 64) {
+          const int t = threadIdx.x - 32;
+          if (k + 1 >= r_lo && k + 1 < r_hi && t < jb) g.row_k[nb * kGridPanel + t] = elim(k + 1 - r_lo, k + 1, t);
+        }
+        barrier_arrive(bar, gn, w.err, ep);
+        const int lane = threadIdx.x & 31;
+        d_prow = lane < jb ? S.prow[lane] : 0.0;
+        d_rowk = lane < jb ? S.rowk[lane] : 0.0;
+        d_rowkc = S.rowk[c];
+        d_inv = inv;
+        d_p = p;
+        d_k = k;
+        d_c = c;
+        d_in = Sin;
+        d_out = Sout;
+        dpend = true;
+        barrier_wait(bar, gn, w.err, ep);
+      } else {
+        // the panel's last column: its whole elimination now (warp w: rows
+        // w, w + 8, ...; lane = column)
+        const int lane = threadIdx.x & 31;
+        if (lane < jb)
+          for (int rr = threadIdx.x >> 5; rr < my_rows; rr += kWarps)
+            Sout[rr * kSpStride + lane] = elim(rr, r_lo + rr, lane);
+        dpend = false;
+        bounded_barrier(bar, gn, w.err, ep);
       }
-      bounded_barrier(bar, gn, w.err, ep);
     }
     return 0;
   }
@@ -663,7 +740,7 @@ struct GridOps {
     for (int e = threadIdx.x; e < x.my_rows * jb; e += kThreads) {
       const int rr = e / jb, c = e % jb;
       const int r = x.r_lo + rr;
-      const double v = Sf[rr * kGridPanel + c];
+      const double v = Sf[rr * kSpStride + c];
       W[(int64_t)r * n + kb + c] = v;
       Pf[(int64_t)c * n + r] = v;
     }
@@ -751,7 +828,7 @@ struct GridOps {
     const int lane = threadIdx.x & 31, i8 = lane & 7;
     const int gw = x.gt >> 5, nw = x.gnt >> 5;
     const int ncb = (n + kUpdN - 1) / kUpdN;
-    double* UsT = grid_panel_smem + 2 * x.rows_per * kGridPanel;  // [32 q][32]: rows J_q of U_0 .. U_{q-1}, transposed
+    double* UsT = grid_panel_smem + 2 * x.rows_per * kSpStride;  // [32 q][32]: rows J_q of U_0 .. U_{q-1}, transposed
     for (int K0 = 0; K0 < n; K0 += kSuperCols) {
       const int B = min(kSuperCols, n - K0);
       const int m = (B + kGridPanel - 1) / kGridPanel;
@@ -761,7 +838,7 @@ struct GridOps {
         const double* Sf = (jb & 1) ? x.Sp1 : x.Sp0;
         for (int e = threadIdx.x; e < x.my_rows * jb; e += kThreads) {
           const int rr = e / jb, c = e % jb;
-          W[(int64_t)(x.r_lo + rr) * n + kb + c] = Sf[rr * kGridPanel + c];
+          W[(int64_t)(x.r_lo + rr) * n + kb + c] = Sf[rr * kSpStride + c];
         }
         // U_q = P_q - I_{J_q}, this block's rows, eight lanes per row: FP64
         // into block q of g.ucat, and its digits (one chunk) for the narrow update
@@ -771,7 +848,7 @@ struct GridOps {
           double u[4];
           for (int t = 0; t < 4; ++t) {
             const int c = 4 * i8 + t;
-            u[t] = (valid && c < jb) ? Sf[rr * kGridPanel + c] - (r == kb + c ? 1.0 : 0.0) : 0.0;
+            u[t] = (valid && c < jb) ? Sf[rr * kSpStride + c] - (r == kb + c ? 1.0 : 0.0) : 0.0;
           }
           if (valid) {
             double* up = g.ucat + (int64_t)r * kSuperCols + q * kGridPanel + 4 * i8;
@@ -918,8 +995,8 @@ struct GridOps {
     x.r_lo = x.lb * x.rows_per;
     x.r_hi = min(n, x.r_lo + x.rows_per);
     x.my_rows = x.r_hi > x.r_lo ? x.r_hi - x.r_lo : 0;
-    x.Sp0 = grid_panel_smem;                             // [rows_per][kGridPanel]
-    x.Sp1 = grid_panel_smem + x.rows_per * kGridPanel;
+    x.Sp0 = grid_panel_smem;                             // [rows_per][kSpStride]
+    x.Sp1 = grid_panel_smem + x.rows_per * kSpStride;
     x.bar = bar;
     x.ep = ep;
     const int lb = x.lb, gt = x.gt, gnt = x.gnt, G = x.G;

@@ -231,7 +231,7 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
     int gsz = sms * want;
     if (gsz > kMaxGrid) gsz = kMaxGrid;
     const int min_group = gsz / 2 >= 8 ? gsz / 2 : gsz;
-    size_t d = 2 * (size_t)((p.n_max + min_group - 1) / min_group) * kGridPanel * sizeof(double);
+    size_t d = 2 * (size_t)((p.n_max + min_group - 1) / min_group) * kSpStride * sizeof(double);
     if (SLICED) d += sizeof(double) * (kSuperCols - kGridPanel) * kGridPanel;
     if (d < sizeof(GemmSmem)) d = sizeof(GemmSmem);
     if (SLICED && d < kUpdSmemBytes) d = kUpdSmemBytes;
