@@ -152,18 +152,19 @@ inline EncodeTiledFn tensor_map_encoder() {
   return fn;
 }
 
-// 2-D map over a digit buffer: n_max rows of kDigRow BF16, box of box_x BF16
-// x box_rows, 128-byte (box_x = 64) or 32-byte (box_x = 16) swizzle, zero
-// fill outside.
-inline bool digit_map(CUtensorMap* m, void* base, int n_max, int box_x, int box_rows) {
+// 3-D map over a digit buffer of n_max rows of kDigRow BF16, read as
+// (term within a group of gx, row, group): box gx x box_rows x box_groups,
+// 128-byte (gx = 64) or 32-byte (gx = 16) swizzle, zero fill outside. The
+// copy lands in shared memory group-major: [group][row][gx terms].
+inline bool digit_map(CUtensorMap* m, void* base, int n_max, int gx, int box_rows, int box_groups) {
   EncodeTiledFn f = tensor_map_encoder();
   if (!f) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)kDigRow, (cuuint64_t)n_max};
-  const cuuint64_t strides[1] = {(cuuint64_t)kDigRow * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-           box_x == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  const cuuint64_t dims[3] = {(cuuint64_t)gx, (cuuint64_t)n_max, (cuuint64_t)(kDigRow / gx)};
+  const cuuint64_t strides[2] = {(cuuint64_t)kDigRow * 2, (cuuint64_t)gx * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)gx, (cuuint32_t)box_rows, (cuuint32_t)box_groups};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           gx == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -206,8 +207,8 @@ cudaError_t launch_large_mode(const SmallParams& p, char* ws, cudaStream_t st) {
   memset(&maps, 0, sizeof(maps));
   if (SLICED)
     for (int t = 0; t < 2; ++t)
-      if (!digit_map(&maps.a[t], ws + L.g[t].adig, p.n_max, 64, kUpdM) ||
-          !digit_map(&maps.b[t], ws + L.g[t].bdig, p.n_max, 16, kUpdN))
+      if (!digit_map(&maps.a[t], ws + L.g[t].adig, p.n_max, 64, kUpdM, 2) ||
+          !digit_map(&maps.b[t], ws + L.g[t].bdig, p.n_max, 16, kUpdN, kSlices))
         return cudaErrorNotSupported;
   w.n_max = p.n_max;
   const int64_t nn = (int64_t)p.n_max * p.n_max;

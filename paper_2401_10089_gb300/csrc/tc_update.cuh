@@ -9,10 +9,10 @@
 // digit s of that half at 16 s). Each block then runs its share of the
 // 128 x 64 output tiles of W:
 //   * thread 0 streams the digits through a ring of kUpdStages shared-memory
-//     stages with TMA, one stage per (chunk, half): 128 x 128 BF16 of U (two
-//     128-byte swizzle boxes, 4 digits x 16 terms per row) and 64 x 128 of V
-//     (eight 32-byte swizzle boxes, one per digit: the digits' 64 columns
-//     stacked as 512 operand rows);
+//     stages with TMA, one stage per (chunk, half): 128 x 128 BF16 of U (one
+//     3-D copy: two 128-byte swizzle atoms of 4 digits x 16 terms per row)
+//     and 64 x 128 of V (one 3-D copy, 32-byte swizzle: per digit its 64
+//     columns, stacked as 512 operand rows);
 //   * thread 32 issues, per stage, 12 tcgen05.mma (kind::f16, BF16 x BF16 ->
 //     FP32, M = 128, K = 16): digit i of U against the digits j = 1 .. 9 - i
 //     of V in pieces of up to four (N = 64 per digit, up to 256), written at
@@ -22,8 +22,8 @@
 //     magnitude <= nc 2^22 <= 2^24, so FP32 accumulation is exact;
 //   * all eight warps read the levels back (tcgen05.ld), combine them into the
 //     exact integer dot product and round it to FP64 into a shared-memory
-//     tile; then the next tile's MMAs run while the warps add the staged tile
-//     to W row by row (coalesced).
+//     tile; then the next tile's copies and MMAs run (threads 0 and 32)
+//     while warps 2 .. 7 add the staged tile to W row by row (coalesced).
 // Per element that is four FP64 instructions (conversion and addition) for K
 // terms instead of K FP64 FMAs.
 //
@@ -55,8 +55,10 @@ constexpr int kUpdTmemCols = kSliceLevels * kUpdN;           // 512
 static_assert(kUpdTmemCols == 512, "eight levels of 64 columns fill TMEM");
 static_assert(kSlices == 8, "a stage holds two swizzle boxes of four digits");
 
-// Tensor maps of the digit buffers, per inversion group (2-D: kDigRow x n_max
-// BF16; U: boxes of 64 x 128 rows, 128-byte swizzle; V: 16 x 64, 32-byte swizzle).
+// Tensor maps of the digit buffers, per inversion group, 3-D views of the
+// n_max x kDigRow BF16 buffers: U as (64 terms, row, 64-term group) with
+// boxes 64 x 128 x 2, 128-byte swizzle; V as (16 terms, column, 16-term
+// group) with boxes 16 x 64 x 8, 32-byte swizzle.
 struct SliceMaps {
   CUtensorMap a[2];
   CUtensorMap b[2];
@@ -164,9 +166,8 @@ static __device__ __forceinline__ bool upd_produce(SliceSmem& sm, uint32_t ring,
   const uint32_t sA = ring + slot * kStageBytes, sB = sA + kStageA;
   const int x = kChunkDig * (s >> 1) + 128 * (s & 1);
   tm_expect(fb, kStageBytes);
-  tm_load2d(sA, map_a, fb, x, rb * kUpdM);
-  tm_load2d(sA + kAtomA, map_a, fb, x + 64, rb * kUpdM);
-  for (int j = 0; j < kSlices; ++j) tm_load2d(sB + j * kDigB, map_b, fb, x + 16 * j, cb * kUpdN);
+  tm_load3d(sA, map_a, fb, 0, rb * kUpdM, x / 64);
+  tm_load3d(sB, map_b, fb, 0, cb * kUpdN, x / 16);
   return true;
 }
 
@@ -304,19 +305,21 @@ static __device__ __noinline__ void sliced_update(SliceSmem& sm, unsigned char* 
     }
     tm_fence_before();
     __syncthreads();  // TMEM read, Ts complete
-    // W += Ts: warp w takes rows w, w + 8, ..., lanes along the row
-    // (coalesced). All 32 loads of a thread are issued before any store, so
+    // W += Ts: warp w = 2 .. 7 takes rows w - 2, w + 4, ..., lanes along the
+    // row (coalesced). All loads of a thread are issued before any store, so
     // their latencies overlap (the compiler may not move a load above a store
     // to memory it cannot prove distinct); meanwhile thread 0 loads the next
     // tile's remaining stages and thread 32 issues its MMAs.
-    constexpr int kPer = (kUpdM / 8) * 2;  // 16 rows x 2 column halves per thread
+    constexpr int kWW = 6;                                   // warps on W
+    constexpr int kPer = 2 * ((kUpdM + kWW - 1) / kWW);      // rows x 2 column halves per thread
+    const int ww = warp - (8 - kWW);
     double wv[kPer];
-    if (acc_ok) {
+    if (acc_ok && ww >= 0) {
 #pragma unroll
       for (int it = 0; it < kPer; ++it) {
-        const int rr = warp + 8 * (it >> 1), c = lane + 32 * (it & 1);
+        const int rr = ww + kWW * (it >> 1), c = lane + 32 * (it & 1);
         const int gr = r0 + rr, gc = c0 + c;
-        const bool ok = gr < n && gc < n && (gc < ut.mk || gc >= ut.mk + ut.mj);
+        const bool ok = rr < kUpdM && gr < n && gc < n && (gc < ut.mk || gc >= ut.mk + ut.mj);
         wv[it] = ok ? __ldcg(W + (int64_t)gr * n + gc) : 0.0;
       }
     }
@@ -327,12 +330,12 @@ static __device__ __noinline__ void sliced_update(SliceSmem& sm, unsigned char* 
         ++committed;
       }
     }
-    if (acc_ok) {
+    if (acc_ok && ww >= 0) {
 #pragma unroll
       for (int it = 0; it < kPer; ++it) {
-        const int rr = warp + 8 * (it >> 1), c = lane + 32 * (it & 1);
+        const int rr = ww + kWW * (it >> 1), c = lane + 32 * (it & 1);
         const int gr = r0 + rr, gc = c0 + c;
-        if (gr < n && gc < n && (gc < ut.mk || gc >= ut.mk + ut.mj))
+        if (rr < kUpdM && gr < n && gc < n && (gc < ut.mk || gc >= ut.mk + ut.mj))
           W[(int64_t)gr * n + gc] = wv[it] + Ts[rr * kUpdTsStride + c];
       }
     }
