@@ -858,18 +858,25 @@ struct GridOps {
           if (m > 1)
             slice_row8_1(u[0], u[1], u[2], u[3], i8, valid, g.sl.adig + (int64_t)r * kDigRow, g.sl.aexp + r);
         }
+        // the sub-panel's row swaps as one permutation of the rows they
+        // touch: position S.ppos[e] receives the row that was at S.psrc[e]
+        // (traced back through the swaps; e < jb: the positions J_q in order,
+        // then the pivot rows)
+        if ((int)threadIdx.x < 2 * jb) {
+          const int idx = threadIdx.x;
+          const int pos = idx < jb ? kb + idx : g.piv[kb + idx - jb];
+          int s = pos;
+          for (int t = jb - 1; t >= 0; --t) {
+            const int k = kb + t, p = g.piv[k];
+            s = s == k ? p : (s == p ? k : s);
+          }
+          S.ppos[idx] = pos;
+          S.psrc[idx] = s;
+        }
+        __syncthreads();
         // rows J_q of U_0 .. U_{q-1} as this sub-panel's swaps leave them,
         // transposed into shared memory (UsT[32 p + c2][c] = U_p[kb + c, c2])
         if (q > 0) {
-          if ((int)threadIdx.x < jb) {
-            int s = kb + threadIdx.x;
-            for (int t = jb - 1; t >= 0; --t) {
-              const int k = kb + t, p = g.piv[k];
-              s = s == k ? p : (s == p ? k : s);
-            }
-            S.psrc[threadIdx.x] = s;
-          }
-          __syncthreads();
           for (int e = threadIdx.x; e < q * kGridPanel * kGridPanel; e += kThreads) {
             const int c = e % kGridPanel, kq = e / kGridPanel;
             UsT[e] = c < jb ? g.ucat[(int64_t)S.psrc[c] * kSuperCols + kq] : 0.0;
@@ -878,29 +885,28 @@ struct GridOps {
         }
         // every column outside J_q, eight lanes per column (warps walk the
         // columns four at a time, every block of the group taking part): the
-        // first lane applies the sub-panel's row swaps; then, inside the
-        // super-panel, the lanes split the pivot rows W[J_q, j] into digits
-        // for the narrow update; outside it they form v_q[:, j] (lane i8:
-        // rows 4 i8 .. 4 i8 + 3) into g.vcat
+        // lanes apply the swaps' permutation to the column (all loads, then
+        // all stores; lane i8 holds positions 4 i8 .. + 3 of J_q, the new
+        // pivot rows W[J_q, j], and of the pivot rows); then, inside the
+        // super-panel, they split W[J_q, j] into digits for the narrow update;
+        // outside it they form v_q[:, j] (rows 4 i8 .. 4 i8 + 3) into g.vcat
         for (int j4 = gw * 4; j4 < n; j4 += nw * 4) {
           const int j = j4 + (lane >> 3);
           const bool valid = j < n && (j < kb || j >= kb + jb);
           const bool inside = j >= K0 && j < K0 + B;
-          if (valid && i8 == 0)
-            for (int c = 0; c < jb; ++c) {
-              const int k = kb + c, p = g.piv[k];
-              if (p != k) {
-                const double t0 = W[(int64_t)k * n + j];
-                W[(int64_t)k * n + j] = W[(int64_t)p * n + j];
-                W[(int64_t)p * n + j] = t0;
-              }
-            }
-          __syncwarp();
-          double v[4];
+          double v[4], pr[4];
           for (int t = 0; t < 4; ++t) {
-            const int c = 4 * i8 + t;
-            v[t] = (valid && c < jb) ? W[(int64_t)(kb + c) * n + j] : 0.0;
+            const int e = 4 * i8 + t;
+            v[t] = (valid && e < jb) ? W[(int64_t)S.psrc[e] * n + j] : 0.0;
+            pr[t] = (valid && e < jb) ? W[(int64_t)S.psrc[jb + e] * n + j] : 0.0;
           }
+          __syncwarp();  // every load of the column before any store
+          if (valid)
+            for (int t = 0; t < 4; ++t) {
+              const int e = 4 * i8 + t;
+              if (e < jb && S.psrc[e] != S.ppos[e]) W[(int64_t)S.ppos[e] * n + j] = v[t];
+              if (e < jb && S.psrc[jb + e] != S.ppos[jb + e]) W[(int64_t)S.ppos[jb + e] * n + j] = pr[t];
+            }
           if (m > 1)
             slice_row8_1(v[0], v[1], v[2], v[3], i8, valid && inside, g.sl.bdig + (int64_t)j * kDigRow,
                          g.sl.bexp + j);
