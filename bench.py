@@ -478,8 +478,14 @@ def main():
             traffic = 8 * (7.813095e9 + 88.806196e9)
             traffic_note = ("bytes per launch: 8 x the DRAM bytes ncu measured on the 2048^2 case of the same "
                             "kernel and plan (traffic grows with n^3); far below HBM bandwidth, FP64-pipe bound")
-        else:
-            traffic = None
+        elif big and args.big_n == NBIG and args.fp64_products == "tc_sliced":
+            # ncu on the 2048^2 case of the tensor-core form (same plan): 20.64 GB
+            # read + 34.37 GB written, mostly W read and written once per
+            # 128-column super-panel and the digit tiles, both growing with n^3
+            traffic = 8 * (20.642669e9 + 34.367190e9)
+            traffic_note = ("bytes per launch: 8 x the DRAM bytes ncu measured on the 2048^2 case of the same "
+                            "kernel and plan (traffic grows with n^3); far below HBM bandwidth, latency and "
+                            "barrier bound (profiles/k_logm_large_tc_sliced_2048.md)")
         parts = {"batch256": {"ms": ms_a, "matrices_per_s": count / (ms_a * 1e-3),
                               "tflops": flops_a / (ms_a * 1e-3) / 1e12,
                               "frac": flops_a / (ms_a * 1e-3) / 1e12 / peak_a,

@@ -95,10 +95,12 @@ typedef struct logm_batch {
  * an implementation choice for the left divisions of Sec. 6, eq. (ScalDB). */
 #define LOGM_FP64_PIPE 0      /* FP64 FMAs (DMMA tiles) */
 #define LOGM_FP64_TC_SLICED 1 /* each operand split into eight exact BF16 digits (per-row and
-                                 per-column powers of two), digit products accumulated exactly
-                                 in FP32 on the tensor cores (tcgen05), the exact integer dot
-                                 product rounded to FP64 once; the rank-32 updates of the
-                                 inversions run this way, everything else as with PIPE */
+                                 per-column powers of two over up to 128 terms), digit products
+                                 accumulated exactly in FP32 on the tensor cores (tcgen05), the
+                                 exact integer dot product rounded to FP64 once; the inversions
+                                 run as blocked Gauss-Jordan (same pivots, updates outside a
+                                 128-column super-panel gathered into one product of 128 terms)
+                                 and the graph products this way, everything else as with PIPE */
 
 typedef struct logm_options {
   int32_t k_max;          /* largest number of graph products, 1..5 (Table Table_theta;
