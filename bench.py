@@ -171,12 +171,12 @@ def cpu_baseline(A_np, sample: int):
             "seconds": dt}, Ls, ds
 
 
-def arm_config(count, big, big_n, world, fp64_products="pipe"):
+def arm_config(count, big, big_n, world, fp64_products="pipe", n=N):
     """The `config` of the JSON line: what the arm runs each step."""
-    return {"workload": WORKLOAD if (count == COUNT and big and big_n == NBIG) else
-            f"{count} x 256x256 A = I + E (||E||_1 ~ U[0.2, 5])" + (f" + one {big_n}^2 Q T Q^T" if big else "")
+    return {"workload": WORKLOAD if (count == COUNT and n == N and big and big_n == NBIG) else
+            f"{count} x {n}x{n} A = I + E (||E||_1 ~ U[0.2, 5])" + (f" + one {big_n}^2 Q T Q^T" if big else "")
             + ", seeded, FP64 path",
-            "count": count, "n": N, "n_big": big_n if big else None, "precision": "fp64",
+            "count": count, "n": n, "n_big": big_n if big else None, "precision": "fp64",
             "fp64_products": fp64_products,
             "l2": "inputs larger than the 129 MB L2; no flush", "parallelism": f"batch-sharded x{world}"}
 
@@ -228,6 +228,11 @@ def main():
     ap.add_argument("--count", type=int, default=COUNT, help="matrices per rank (smaller for profiling)")
     ap.add_argument("--no-big", action="store_true", help="leave out the 4096 x 4096 matrix")
     ap.add_argument("--big-n", type=int, default=NBIG, help="size of the large matrix (smaller for profiling)")
+    ap.add_argument("--n", type=int, default=N, help="size of the batch's matrices (other sizes for profiling)")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FP64 / TF32 peak measurements (profiling)")
+    ap.add_argument("--config", type=int, default=None,
+                    help="one-block kernel configuration for every size bucket that allows it (profiling; "
+                         "default: the tuned table)")
     ap.add_argument("--fp64-products", default="tc_sliced", choices=["tc_sliced", "pipe"],
                     help="FP64 products of the whole-GPU kernel: exact BF16 digit products on the tensor cores "
                          "(default) or FP64 FMAs")
@@ -251,8 +256,12 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    count = args.count
-    A_np = workloads.identity_plus(count, N, seed=1 + rank)
+    count, n = args.count, args.n
+    if args.config is not None:
+        from paper_2401_10089_gb300 import autotune
+        lg.set_tuning([args.config if args.config in autotune.CANDIDATES[b] else t
+                       for b, t in enumerate(lg.get_tuning())])
+    A_np = workloads.identity_plus(count, n, seed=1 + rank)
     A_host = torch.from_numpy(A_np).pin_memory()
     A_dev = A_host.to(dev)
     big = not args.no_big
@@ -304,7 +313,7 @@ def main():
     clocks = clk.summary()
     ms_max = shard.max_over_ranks(ms, device=dev)  # the slowest rank's step
 
-    flops_a = algorithmic_flops(stats.cpu().numpy(), N)
+    flops_a = algorithmic_flops(stats.cpu().numpy(), n)
     flops_b = algorithmic_flops(stats_b.cpu().numpy(), args.big_n) if big else 0.0
     info_np = info.cpu().numpy()
     s_np, k_np = s.cpu().numpy(), k.cpu().numpy()
@@ -366,7 +375,7 @@ def main():
         # the split-precision forms run the same plan as the FP64 path (same s, k),
         # but their products are not in the FP64 kernel's tally: count the FP64 run's
         split = "precision" in vopts
-        fl_a = flops_a if split else algorithmic_flops(st_fa.cpu().numpy(), N)
+        fl_a = flops_a if split else algorithmic_flops(st_fa.cpu().numpy(), n)
         errs_a = ((Lp - L).flatten(1).norm(dim=1) / L.flatten(1).norm(dim=1)).cpu().numpy()
         ent = {"options": vopts,
                "batch256": {"ms": ms_fa, "matrices_per_s": count / (ms_fa * 1e-3),
@@ -444,8 +453,11 @@ def main():
     if rank == 0:
         # FP64 and TF32 dense peaks measured on this GPU (cuBLAS GEMM loops of a
         # few seconds, outside the timed region, clocks sampled meanwhile)
-        peaks = {"fp64": measure_gemm_peak(torch, dev, torch.float64, local),
-                 "tf32": measure_gemm_peak(torch, dev, torch.float32, local, tf32=True)}
+        if args.no_peaks:  # profiling runs: no reference GEMM loops (the fractions are then NaN)
+            peaks = {"fp64": {"tflops": float("nan"), "seconds": 0.0}, "tf32": {"tflops": float("nan")}}
+        else:
+            peaks = {"fp64": measure_gemm_peak(torch, dev, torch.float64, local),
+                     "tf32": measure_gemm_peak(torch, dev, torch.float32, local, tf32=True)}
         peak = peak_a = peaks["fp64"]["tflops"]
         peak_note = ("FP64 dense of measured: cuBLAS DGEMM 8192^3 (torch.matmul float64) back to back for "
                      f"{peaks['fp64']['seconds']:.1f} s in this run")
@@ -502,7 +514,7 @@ def main():
             "matrices_per_s": n_mats * world / (ms_max * 1e-3), "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": arm_config(count, big, args.big_n, world, args.fp64_products),
+            "config": arm_config(count, big, args.big_n, world, args.fp64_products, n),
             "parts": parts,
             "forms": forms,
             "roofline": {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
