@@ -414,6 +414,22 @@ LG_HD double combine_levels_fp(const int32_t* c, int32_t eu, int32_t ev) {
   return ldexp(t, E);  // rare: subnormal or overflowing result
 }
 
+// combine_levels_fp without branches for the common case: *slow is set
+// when the result needs combine_levels_fp instead (a non-finite row or
+// column, or a subnormal or overflowing result); the value returned is then
+// meaningless.
+LG_HD double combine_levels_fast(const int32_t* c, int32_t eu, int32_t ev, bool* slow) {
+  int64_t hi, lo;
+  level_halves(c, &hi, &lo);
+  const double t = fma(half_to_double(hi), 4294967296.0, half_to_double(lo));
+  const int E = eu + ev - kSliceScale;
+  const uint64_t b = lg_dbits(t);
+  const int be = static_cast<int>((b >> 52) & 0x7FF) + E;
+  const bool zero = (hi | lo) == 0;
+  *slow = (!zero && (be < 1 || be > 2046)) || eu == kSliceNonFinite || ev == kSliceNonFinite;
+  return zero ? 0.0 : lg_bitsd(b + (static_cast<uint64_t>(static_cast<int64_t>(E)) << 52));
+}
+
 // u.v as combine_levels_int, with the branch-free 32-bit conversion.
 LG_HD double combine_levels_int32(const int32_t* c, int32_t eu, int32_t ev) {
   if (eu == kSliceNonFinite || ev == kSliceNonFinite) return lg_bitsd(0x7FF8000000000000ull);  // NaN

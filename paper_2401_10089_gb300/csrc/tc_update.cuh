@@ -295,11 +295,22 @@ static __device__ __noinline__ void sliced_update(SliceSmem& sm, unsigned char* 
             Ts[lrow * kUpdTsStride + cc + e] = combine_levels_fp(c, er, sm.ecol[cc + e]);
           }
         } else {
+          // branch-free for every element; the rare ones (a non-finite row or
+          // column, a subnormal or overflowing result) again through the full route
+          bool slow = false;
           for (int e = 0; e < 8; ++e) {
             int32_t c[kSliceLevels];
             for (int L = 0; L < kSliceLevels; ++L) c[L] = level_int(__uint_as_float(v[L][e]));
-            Ts[lrow * kUpdTsStride + cc + e] = combine_levels_fp(c, er, sm.ecol[cc + e]);
+            bool sl;
+            Ts[lrow * kUpdTsStride + cc + e] = combine_levels_fast(c, er, sm.ecol[cc + e], &sl);
+            slow = slow || sl;
           }
+          if (__any_sync(0xffffffffu, slow) && slow)
+            for (int e = 0; e < 8; ++e) {
+              int32_t c[kSliceLevels];
+              for (int L = 0; L < kSliceLevels; ++L) c[L] = level_int(__uint_as_float(v[L][e]));
+              Ts[lrow * kUpdTsStride + cc + e] = combine_levels_fp(c, er, sm.ecol[cc + e]);
+            }
         }
       }
     }

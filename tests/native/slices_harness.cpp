@@ -47,6 +47,13 @@ double h_sliced_dot(const double* u, const double* v, int k) {
 
 int32_t h_level_int(float v) { return lg::level_int(v); }
 int32_t h_level_int_wide(float v) { return lg::level_int_wide(v); }
+double h_combine_fp(const int32_t* c, int32_t eu, int32_t ev) { return lg::combine_levels_fp(c, eu, ev); }
+double h_combine_fast(const int32_t* c, int32_t eu, int32_t ev, int32_t* slow) {
+  bool sl = false;
+  const double r = lg::combine_levels_fast(c, eu, ev, &sl);
+  *slow = sl ? 1 : 0;
+  return r;
+}
 double h_exact_int_to_double(int64_t x) { return lg::exact_int_to_double(x); }
 
 // the integer-only split against the FP64-scaled one: fixed-point integers

@@ -54,6 +54,10 @@ def h():
     L.h_combine_both.argtypes = [p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, p]
     L.h_level_int_wide.restype = ctypes.c_int32
     L.h_level_int_wide.argtypes = [ctypes.c_float]
+    L.h_combine_fast.restype = ctypes.c_double
+    L.h_combine_fast.argtypes = [p, ctypes.c_int32, ctypes.c_int32, p]
+    L.h_combine_fp.restype = ctypes.c_double
+    L.h_combine_fp.argtypes = [p, ctypes.c_int32, ctypes.c_int32]
     L.h_exact_int_to_double.restype = ctypes.c_double
     L.h_exact_int_to_double.argtypes = [ctypes.c_int64]
     L.h_levels32_agree.restype = ctypes.c_int
@@ -253,3 +257,33 @@ def test_level_sums_over_four_chunks(h):
     vals += [int(v) for v in rng.integers(-(2 ** 24), 2 ** 24 + 1, 20000)]
     for v in vals:
         assert h.h_level_int_wide(float(v)) == v, v
+
+
+def test_branch_free_combination_matches_or_defers(h):
+    # the epilogue's branch-free route gives combine_levels_fp's value bit for
+    # bit, or flags the element for it: exactly when a scale is non-finite or
+    # the result would be subnormal or overflow (zero stays zero)
+    rng = np.random.default_rng(11)
+    nonfin = -0x40000000
+    cases = []
+    for _ in range(4000):
+        c = rng.integers(-(2 ** 24), 2 ** 24 + 1, 8).astype(np.int32)
+        if rng.random() < 0.1:
+            c[:] = 0
+        eu, ev = (int(x) for x in rng.integers(-1100, 1100, 2))
+        cases.append((c, eu, ev))
+    for eu, ev in ((nonfin, 3), (5, nonfin), (-1022, -60), (1023, 200), (0, 0)):
+        cases.append((rng.integers(-1000, 1000, 8).astype(np.int32), eu, ev))
+    n_slow = 0
+    for c, eu, ev in cases:
+        slow = np.zeros(1, dtype=np.int32)
+        r = h.h_combine_fast(_ptr(c), eu, ev, _ptr(slow))
+        ref = h.h_combine_fp(_ptr(c), eu, ev)
+        if slow[0]:
+            n_slow += 1
+            finite = eu != nonfin and ev != nonfin
+            a = abs(ref)
+            assert (not finite) or a == float("inf") or a < 2.2250738585072014e-308, (c, eu, ev, ref)
+        else:
+            assert np.float64(r).tobytes() == np.float64(ref).tobytes(), (c, eu, ev, r, ref)
+    assert 0 < n_slow < len(cases)
