@@ -491,10 +491,10 @@ def main():
             traffic_note = ("bytes per launch: 8 x the DRAM bytes ncu measured on the 2048^2 case of the same "
                             "kernel and plan (traffic grows with n^3); far below HBM bandwidth, FP64-pipe bound")
         elif big and args.big_n == NBIG and args.fp64_products == "tc_sliced":
-            # ncu on the 2048^2 case of the tensor-core form (same plan): 20.64 GB
+            # ncu on the 2048^2 case of the tensor-core form (same plan): 20.66 GB
             # read + 34.37 GB written, mostly W read and written once per
             # 128-column super-panel and the digit tiles, both growing with n^3
-            traffic = 8 * (20.642669e9 + 34.367190e9)
+            traffic = 8 * (20.661627e9 + 34.370699e9)
             traffic_note = ("bytes per launch: 8 x the DRAM bytes ncu measured on the 2048^2 case of the same "
                             "kernel and plan (traffic grows with n^3); far below HBM bandwidth, latency and "
                             "barrier bound (profiles/k_logm_large_tc_sliced_2048.md)")
