@@ -328,6 +328,10 @@ def main():
     if e2e_steps:  # one device workspace for both calls, allocated outside the timed region
         need = max(lg.logm_host_workspace_size(A_host), lg.logm_host_workspace_size(B_host) if big else 0)
         ws_e2e = torch.empty(need, dtype=torch.uint8, device=dev)
+    if e2e_steps:  # one untimed call first, like the warm-up steps of the device timing
+        lg.logm_execute_host(A_host, out=L_host, device=dev, workspace=ws_e2e, **main)
+        if big:
+            lg.logm_execute_host(B_host, out=LB_host, device=dev, workspace=ws_e2e, **main)
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):

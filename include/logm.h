@@ -243,8 +243,8 @@ int logm_execute_noalloc(const logm_batch* batch, const logm_options* opts, cons
  *   A_host   : host, count * n^2 elements of the batch dtype, row-major.
  *   L_host   : host, same size; s_host, k_host (may be NULL), info_host: host int32[count].
  *   ws       : device, >= logm_host_workspace_size() bytes, 256-byte aligned:
- *              device copies of A and L, the three int32 arrays, then the
- *              workspace of logm_execute.
+ *              the workspace of logm_execute, then device copies of A and L
+ *              and the three int32 arrays.
  * Returns as logm_execute, or LOGM_ERR_CUDA if a copy cannot be enqueued. */
 size_t logm_host_workspace_size(const logm_batch* batch, const logm_options* opts);
 int logm_execute_host(const logm_batch* batch, const logm_options* opts, const void* A_host, void* L_host,
