@@ -79,3 +79,26 @@ def test_execute_host_argument_checks():
     o.k_max = 6
     rc = L.logm_execute_host(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, 0, None)
     assert rc == _lib.ERR_INVALID_ARG
+
+
+def test_host_workspace_layout_size():
+    # logm_execute_host's device workspace: logm_execute's own workspace first
+    # (at the caller's aligned base), then the device copies of A and L and
+    # the three int32 result arrays, each rounded up to 256 bytes
+    from paper_2401_10089_gb300 import _lib
+    L = _lib.load()
+    L.logm_workspace_size.restype = ctypes.c_size_t
+    L.logm_host_workspace_size.restype = ctypes.c_size_t
+    o = _lib.LogmOptions()
+    o.k_max, o.precision, o.max_sqrt, o.max_db_iter = 5, 0, 40, 50
+
+    def r256(x):
+        return (x + 255) // 256 * 256
+
+    for n, count, dtype, esz in ((32, 4, 0, 8), (300, 1, 0, 8), (256, 512, 0, 8), (48, 20, 1, 4)):
+        b = _lib.LogmBatch()
+        b.count, b.dtype, b.n_uniform, b.n_max = count, dtype, n, n
+        inner = L.logm_workspace_size(ctypes.byref(b), ctypes.byref(o))
+        host = L.logm_host_workspace_size(ctypes.byref(b), ctypes.byref(o))
+        assert inner > 0
+        assert host == r256(inner) + 2 * r256(count * n * n * esz) + r256(12 * count)
