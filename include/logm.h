@@ -103,10 +103,14 @@ typedef struct logm_batch {
                                  and the graph products this way, everything else as with PIPE */
 
 typedef struct logm_options {
-  int32_t k_max;          /* largest number of graph products, 1..5 (Table Table_theta;
+  int32_t k_max;          /* largest number of graph products, 1..6 (Table Table_theta;
                              k = 3 is T_8 by eq. eqP8pol, k = 4 the 14+ scheme of Sec. 3
                              with coefficients solved from T_14, k = 5 Table
-                             table_simple_experiment) */
+                             table_simple_experiment, k = 6 a degree-64 scheme in the same
+                             form fitted to -log(1 - x), m_6 = 20+, Theta_6 = 0.372).
+                             k_max = 6: FP64 products only (else LOGM_ERR_INVALID_ARG), and
+                             n_max <= 256 without a backward context (else
+                             LOGM_ERR_UNSUPPORTED); Theta_6 is fixed */
   int32_t precision;      /* LOGM_PREC_* of the graph products */
   int32_t max_sqrt;       /* maxiter of Algorithm 1 (default 40) */
   int32_t max_db_iter;    /* cap on Denman-Beavers iterations per root (default 50) */
@@ -163,11 +167,15 @@ int logm_sqrt(const logm_batch* batch, const logm_options* opts, void* A, void* 
  * Table table_simple_experiment for k = 5, exact Taylor T_2, T_4 (eq.
  * Taylor_log) for k = 1, 2, T_8 with three products (eq. eqP8pol, its
  * coefficients solved in closed form) for k = 3 and the 14+ scheme (degree
- * 16, T_14 matched, coefficients solved numerically) for k = 4.
+ * 16, T_14 matched, coefficients solved numerically) for k = 4; with FP64
+ * products and n <= 256 also k = 6 (degree 64, coefficients fitted to
+ * -log(1 - x), Taylor terms matched to order 34).
  *   X    : device (dtype per batch).
  *   P3   : device or NULL; X^2 if the caller has it (saves one product, as
  *          Algorithm 1 does with A_I2 when s >= 1).
- *   k_dev: device int32[count], each 1..5.
+ *   k_dev: device int32[count], each 1..5; also 6 with FP64 products on
+ *          matrices with n <= 256 (Z of a matrix with another k is left
+ *          unwritten).
  *   Z    : device output (dtype per batch).
  *   precision: LOGM_PREC_* for the products. */
 int logm_graph_eval(const logm_batch* batch, int32_t precision, const void* X, const void* P3,

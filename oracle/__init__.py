@@ -14,7 +14,8 @@ paper it follows:
                       Taylor polynomials of eq. (Taylor_log) for k = 1, 2,
                       T_8 by eq. (eqP8pol) for k = 3 (``coeffs_k3``) and the
                       14+ scheme for k = 4 (``coeffs_k4``, solved here; the
-                      paper does not print it).
+                      paper does not print it) and a 20+ scheme for k = 6
+                      (``coeffs_k6``, fitted by ``derive_k6.py``; opt-in).
 * ``sqrtm_db``     -- scaled Denman-Beavers iteration, eq. (ScalDB), Sec. 6, or
                       its product form (``form=1``, the variant cited in Sec. 2);
                       ``logm`` runs eq. (ScalDB) as written at every level unless
@@ -45,12 +46,13 @@ _LIB_PATH = os.path.join(_BUILD, "liblogm_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-# Theta_{m_k} of Table Table_theta (Sec. 5) for k = 1..5.
-THETA_TABLE = (1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1)
+# Theta_{m_k} of Table Table_theta (Sec. 5) for k = 1..6.
+THETA_TABLE = (1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1, 3.72e-1)
 # Orders with coefficients: T_2, T_4 (eq. Taylor_log), T_8 (eq. eqP8pol), the
-# 14+ scheme (k = 4, solved here) and Table table_simple_experiment.
-AVAILABLE_K = (1, 2, 3, 4, 5)
-M_OF_K = {1: 2, 2: 4, 3: 8, 4: 14, 5: 14}
+# 14+ scheme (k = 4, solved here), Table table_simple_experiment and the
+# 20+ scheme (k = 6, fitted here; opt-in, the default k_max stays 5).
+AVAILABLE_K = (1, 2, 3, 4, 5, 6)
+M_OF_K = {1: 2, 2: 4, 3: 8, 4: 14, 5: 14, 6: 20}
 # Status codes, written out on their own (same meanings as the library's).
 OK, SINGULAR, NO_CONVERGENCE, MAX_SQRT, NONFINITE = 0, 1, 2, 3, 4
 
@@ -65,7 +67,7 @@ class Opts(ctypes.Structure):
         ("db_form", ctypes.c_int32),
         ("balance", ctypes.c_int32),
         ("reuse_root", ctypes.c_int32),
-        ("theta", ctypes.c_double * 5),
+        ("theta", ctypes.c_double * 6),
     ]
 
 
@@ -130,6 +132,7 @@ def lib():
             L.orc_expm_taylor.argtypes = [i, p, p]
             L.orc_frechet_adjoint.argtypes = [i, p, p, p, p]
             L.orc_coeffs_k5.argtypes = [p, p, p]
+            L.orc_coeffs_k6.argtypes = [p, p, p]
             _lib = L
     return _lib
 
@@ -153,8 +156,8 @@ def make_opts(k_max=5, max_sqrt=40, max_db_iter=50, force_s=-1, force_k=0, theta
     o.force_s, o.force_k = force_s, force_k
     o.db_form, o.balance, o.reuse_root = db_form, balance, reuse_root
     th = THETA_TABLE if theta is None else theta
-    for t in range(5):
-        o.theta[t] = th[t]
+    for t in range(6):
+        o.theta[t] = th[t] if t < len(th) else THETA_TABLE[t]
     return o
 
 
@@ -188,6 +191,16 @@ def coeffs_k5():
     g = np.zeros(14)
     y = np.zeros(7)
     lib().orc_coeffs_k5(_ptr(h), _ptr(g), _ptr(y))
+    return h, g, y
+
+
+def coeffs_k6():
+    """h (20), g (20), y (8) of the k = 6 scheme in the order h_{2,2..3},
+    h_{3,2..4}, ..., h_{6,2..7}; y = y_1..y_8 (y_1 = 0, y_2 = 1)."""
+    h = np.zeros(20)
+    g = np.zeros(20)
+    y = np.zeros(8)
+    lib().orc_coeffs_k6(_ptr(h), _ptr(g), _ptr(y))
     return h, g, y
 
 

@@ -62,7 +62,7 @@
 
 #define ORC_U 0x1p-53 /* unit roundoff of IEEE binary64 */
 
-int orc_version(void) { return 3; }
+int orc_version(void) { return 4; }
 
 /* ------------------------------------------------------------------------ */
 /* Coefficients of the degree-optimal form, eq. (five_mult_degopt).         */
@@ -157,15 +157,42 @@ static const double K4_C[13] = {
 
 void orc_coeffs_k4(double* c) { memcpy(c, K4_C, sizeof(K4_C)); }
 
+/* k = 6 (degree 64, Taylor terms of -log(1 - x) matched to order 34). The
+ * paper prints no coefficients for k >= 6, only Theta_6 = 0.372 (m_6 = 20+)
+ * in Table Table_theta; these were fitted in the paper's form, eq.
+ * (five_mult_degopt) with P_3 = X^2 and y_1 = 0, y_2 = 1, by
+ * oracle/derive_k6.py, whose output they are. The tests check them against
+ * the paper's criteria: the Taylor terms, Theta_6 by eqs. (Eb), (theta_Eb)
+ * and the stability indicator of Sec. 4. */
+static const double K6_H[20] = {
+    -0.03542133528022389, 0.5305162167939017,  /* h_{2,2..3} */
+    1.1735695507060024, 0.42664399607790565, -1.4401144598828934,  /* h_{3,2..4} */
+    -0.37722719586021003, 1.1748267828138759, -0.4355749562164976, -0.55350435103941,  /* h_{4,2..5} */
+    -0.13552704716524286, 0.483097031151113, -2.879391574437424, -0.779847925333845, -0.8268140965713336,  /* h_{5,2..6} */
+    4.549413425481621, -3.6536822467517673, -5.744611071943747, 3.2747363248058474, -3.4999222429973935, 5.3137561222344525}; /* h_{6,2..7} */
+static const double K6_G[20] = {
+    -0.25821891505961464, -0.5021334801772399,  /* g_{2,2..3} */
+    1.1247378095155132, -0.7530860083722153, 2.656179396111579,  /* g_{3,2..4} */
+    -0.5198936929205077, -0.669272512275526, -1.2980185589839237, 0.5165656321507225,  /* g_{4,2..5} */
+    0.1625662254422074, -0.2675459778240617, -0.03466835614054706, 0.328082088789197, -0.34992616877127714,  /* g_{5,2..6} */
+    -1.3970630865902485, 2.542415746918083, -0.048059210298082834, 0.9420478294952318, -2.416723959179748, 1.3390816588113656}; /* g_{6,2..7} */
+static const double K6_Y[8] = {0.0, 1.0, 0.8200410102947662, -0.4825318072757668, -0.12989653721591463, -0.40476811140333024, 0.12143584229947445, 0.00977242585180227};
+
+void orc_coeffs_k6(double* h, double* g, double* y) {
+  memcpy(h, K6_H, sizeof(K6_H));
+  memcpy(g, K6_G, sizeof(K6_G));
+  memcpy(y, K6_Y, sizeof(K6_Y));
+}
+
 /* A degree-optimal scheme with k products: P_1 = I, P_2 = X and, for
  * j = 1..k, P_{j+2} = (sum_{i=1}^{j+1} h_{j,i} P_i)(sum_{i=1}^{j+1} g_{j,i} P_i);
  * z = sum_{i=1}^{k+2} y_i P_i (eq. five_mult_degopt). Indices are 1-based in
  * the arrays below (entry 0 unused) so that they read like the paper. */
 typedef struct {
   int k;
-  double h[6][8];
-  double g[6][8];
-  double y[8];
+  double h[7][9];
+  double g[7][9];
+  double y[9];
 } orc_scheme;
 
 static void scheme_for(int k, orc_scheme* S) {
@@ -234,16 +261,25 @@ static void scheme_for(int k, orc_scheme* S) {
         S->g[j][i] = K5_G[t];
       }
     for (int i = 1; i <= 7; ++i) S->y[i] = K5_Y[i - 1];
+  } else if (k == 6) {
+    int t = 0;
+    for (int j = 2; j <= 6; ++j)
+      for (int i = 2; i <= j + 1; ++i, ++t) {
+        S->h[j][i] = K6_H[t];
+        S->g[j][i] = K6_G[t];
+      }
+    for (int i = 1; i <= 8; ++i) S->y[i] = K6_Y[i - 1];
   }
 }
 
-/* m_k of Table Table_theta: 2, 4, 8, 14+ (k = 4, degree 16) and 14+ (k = 5,
- * degree 32); the "+" schemes are tested with alpha_14. */
-static int m_of_k(int k) { return k == 1 ? 2 : (k == 2 ? 4 : (k == 3 ? 8 : 14)); }
+/* m_k of Table Table_theta: 2, 4, 8, 14+ (k = 4, degree 16), 14+ (k = 5,
+ * degree 32) and 20+ (k = 6, degree 64); the "+" schemes are tested with
+ * alpha_14 and alpha_20. */
+static int m_of_k(int k) { return k == 1 ? 2 : (k == 2 ? 4 : (k == 3 ? 8 : (k == 6 ? 20 : 14))); }
 
 static int theta_index(int k) { return k - 1; }
 
-static int k_available(int k) { return k >= 1 && k <= 5; }
+static int k_available(int k) { return k >= 1 && k <= 6; }
 
 /* ------------------------------------------------------------------------ */
 /* Dense linear algebra, textbook forms.                                    */
@@ -723,7 +759,7 @@ int orc_graph_eval(int n, int k, const double* X, const double* P3, double* Z) {
   orc_scheme S;
   scheme_for(k, &S);
   const size_t nn = (size_t)n * n;
-  double* P[8] = {0};
+  double* P[9] = {0};
   for (int i = 1; i <= k + 2; ++i) P[i] = alloc_mat(n);
   double* Lf = alloc_mat(n);
   double* Rf = alloc_mat(n);
@@ -860,9 +896,9 @@ static int alpha_test(int n, const double* B, const double* AI2, double nB, doub
  *  k+1 at once when alpha_{m_k} > Theta_k but <= Theta_{k+1}. */
 static int order_search(int n, const double* B, const double* AI2, double nB, double nI2,
                         const orc_opts* o, const est_state* loop_est, int* n_est, margin_t* mt) {
-  int cands[5], nc = 0;
-  const int all[5] = {1, 2, 3, 4, 5};
-  for (int t = 0; t < 5; ++t)
+  int cands[6], nc = 0;
+  const int all[6] = {1, 2, 3, 4, 5, 6};
+  for (int t = 0; t < 6; ++t)
     if (all[t] <= o->k_max) cands[nc++] = all[t];
   if (nc == 0) return o->k_max;
   /* min_im */

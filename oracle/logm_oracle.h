@@ -27,7 +27,7 @@ enum {
 };
 
 typedef struct {
-  int32_t k_max;       /* largest number of graph products: 1..5 */
+  int32_t k_max;       /* largest number of graph products: 1..6 */
   int32_t max_sqrt;    /* maxiter of Algorithm 1 */
   int32_t max_db_iter; /* cap on Denman-Beavers iterations per square root */
   int32_t force_s;     /* < 0: choose s by the bound; >= 0: take exactly s roots */
@@ -36,12 +36,12 @@ typedef struct {
   int32_t balance;     /* 0: T = I; 1: diagonal balancing (Algorithm 1, Step 1) */
   int32_t reuse_root;  /* 0: eq. (ScalDB) as written at every level; 1: later levels
                           start from the previous level's Y as A^{-1} (opt-in) */
-  double theta[5];     /* Theta_{m_k} for k = 1..5 (Table Table_theta) */
+  double theta[6];     /* Theta_{m_k} for k = 1..6 (Table Table_theta) */
 } orc_opts;
 
 typedef struct {
   int32_t s;              /* square roots taken */
-  int32_t k;              /* graph products used (1..5) */
+  int32_t k;              /* graph products used (1..6) */
   int32_t info;           /* ORC_* status */
   int32_t db_iters;       /* total Denman-Beavers iterations over all levels */
   int32_t n_estimates;    /* calls of the 1-norm power estimator */
@@ -68,6 +68,11 @@ void orc_coeffs_k3(double* c);
 /* k = 4 coefficients of the 14+ scheme (solved here, see logm_oracle.c):
  * c[13] = c3, c4, d1, d2, e2, f1, f2, f4, g1, g4, y3, y4, y5. */
 void orc_coeffs_k4(double* c);
+
+/* k = 6 coefficients (derived here: the paper prints none for k >= 6, see
+ * logm_oracle.c): h[20] = h_{2,2..3}, h_{3,2..4}, h_{4,2..5}, h_{5,2..6},
+ * h_{6,2..7}; g the same; y[8] = y_1..y_8. */
+void orc_coeffs_k6(double* h, double* g, double* y);
 
 void orc_gemm(int n, const double* A, const double* B, double* C);
 double orc_norm1(int n, const double* A);

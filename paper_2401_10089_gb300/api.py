@@ -83,7 +83,8 @@ _FP64_PRODUCTS = {"pipe": 0, "tc_sliced": 1}
 
 def _options(k_max=5, precision="fp64", max_sqrt=40, max_db_iter=50, theta=None, db_form="two_inverse",
              balance=False, fp64_products="pipe") -> _lib.LogmOptions:
-    """k_max in 1..5; db_form "two_inverse" (eq. ScalDB) or "product";
+    """k_max in 1..6 (6: FP64 products, n <= 256, no adjoint); db_form
+    "two_inverse" (eq. ScalDB) or "product";
     balance: diagonal balancing of Algorithm 1, Step 1; theta: Theta_{m_k} for
     k = 1..5 (0 = the paper's Table Table_theta); fp64_products: "pipe" (FP64
     FMAs) or "tc_sliced" (the whole-GPU kernel's inversion updates from exact

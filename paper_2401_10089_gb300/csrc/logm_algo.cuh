@@ -54,6 +54,33 @@ static __constant__ double c_k4[13] = {
     0.1463535711919622,  0.9787518426666669,   0.5020605793026582,  0.6095606808527384,
     1.2091753609836204};
 
+// k = 6 (m_6 = 20+, degree 64, Theta_6 = 0.372 of Table Table_theta), taken
+// by the one-block-per-matrix kernels only (LG_WITH_K6 = 1). The paper prints
+// no coefficients for k >= 6; these were fitted to -log(1 - x) in the same
+// degree-optimal form (P_3 = X^2, y_1 = 0, y_2 = 1), with the Taylor terms
+// matched to order 34 and the backward-error Theta of eqs. (Eb), (theta_Eb)
+// above 0.372. h_{j,i}, g_{j,i} for j = 2..6, i = 2..j+1 in that order;
+// y_3 .. y_8.
+#ifndef LG_WITH_K6
+#define LG_WITH_K6 0
+#endif
+#if LG_WITH_K6
+static __constant__ double c_h6[20] = {
+    -0.03542133528022389, 0.5305162167939017, 1.1735695507060024, 0.42664399607790565,
+    -1.4401144598828934, -0.37722719586021003, 1.1748267828138759, -0.4355749562164976,
+    -0.55350435103941, -0.13552704716524286, 0.483097031151113, -2.879391574437424,
+    -0.779847925333845, -0.8268140965713336, 4.549413425481621, -3.6536822467517673,
+    -5.744611071943747, 3.2747363248058474, -3.4999222429973935, 5.3137561222344525};
+static __constant__ double c_g6[20] = {
+    -0.25821891505961464, -0.5021334801772399, 1.1247378095155132, -0.7530860083722153,
+    2.656179396111579, -0.5198936929205077, -0.669272512275526, -1.2980185589839237,
+    0.5165656321507225, 0.1625662254422074, -0.2675459778240617, -0.03466835614054706,
+    0.328082088789197, -0.34992616877127714, -1.3970630865902485, 2.542415746918083,
+    -0.048059210298082834, 0.9420478294952318, -2.416723959179748, 1.3390816588113656};
+static __constant__ double c_y6[6] = {0.8200410102947662, -0.4825318072757668, -0.12989653721591463, -0.40476811140333024, 0.12143584229947445, 0.00977242585180227};
+constexpr double kTheta6 = kThetaPaper[5];
+#endif
+
 constexpr double kUnitRoundoff = 0x1p-53;
 
 struct Slot {
@@ -62,6 +89,23 @@ struct Slot {
 
 static __device__ __forceinline__ int m_of_k(int k) { return k == 1 ? 2 : (k == 2 ? 4 : (k == 3 ? 8 : 14)); }
 static __device__ __forceinline__ int theta_slot(int k) { return k - 1; }
+
+// m_k (LG_M_OF) and Theta_{m_k} (LG_THETA) of order k, and the largest order
+// (LG_MAX_ORDER). Theta_1..Theta_5 come from the caller's options (theta[0..4]);
+// Theta_6 is the table's. Without k = 6 these are the plain table lookups.
+#if LG_WITH_K6
+static __device__ __forceinline__ int m_of_order(int k) { return k == 6 ? 20 : m_of_k(k); }
+static __device__ __forceinline__ double theta_of(const double* theta, int k) {
+  return k == 6 ? kTheta6 : theta[theta_slot(k)];
+}
+#define LG_M_OF(k) m_of_order(k)
+#define LG_THETA(th, k) theta_of(th, k)
+#define LG_MAX_ORDER 6
+#else
+#define LG_M_OF(k) m_of_k(k)
+#define LG_THETA(th, k) th[theta_slot(k)]
+#define LG_MAX_ORDER 5
+#endif
 
 // k = 3 (Sec. 2, eq. eqP8pol): T_8 of eq. (Taylor_log) with three products,
 //   y02 = X^2 (c4 X^2 + c3 X),
@@ -348,18 +392,23 @@ static __device__ int alpha_test(Ops& ops, const double* Acur, const double* AI2
 // loop's estimates (eqs. min_in, min_inp), max_in from the rough bound (eq.
 // roughmax_even; every available m_k is even), then an increasing scan that
 // takes k+1 at once when alpha_{m_k} is above Theta_k but not above Theta_{k+1}.
+#if LG_WITH_K6
+#define LG_OUTLINED __noinline__  // keeps the k = 6 plan out of the hot loops' registers
+#else
+#define LG_OUTLINED
+#endif
 template <class Ops>
 static __device__ int order_search(Ops& ops, const double* Acur, const double* AI2, int n, double nB, double nI2,
                             int k_max, const double* theta, const EstState* loop_est) {
-  int cands[5], nc = 0;
-  for (int kk = 1; kk <= 5; ++kk)
+  int cands[LG_MAX_ORDER], nc = 0;
+  for (int kk = 1; kk <= LG_MAX_ORDER; ++kk)
     if (kk <= k_max) cands[nc++] = kk;
   if (nc == 0) return k_max;
   int lo = 0;
   if (loop_est && loop_est->t_m >= 0.0) {
     const int mm = loop_est->m;
     while (lo < nc - 1) {
-      const double th = theta[theta_slot(cands[lo])];
+      const double th = LG_THETA(theta, cands[lo]);
       int ok = loop_est->t_m <= ipow(th, mm);
       if (ok && loop_est->t_m1 >= 0.0) ok = loop_est->t_m1 <= ipow(th, mm + 1);
       if (ok) break;
@@ -368,8 +417,8 @@ static __device__ int order_search(Ops& ops, const double* Acur, const double* A
   }
   int hi = nc - 1;
   for (int t = 0; t < nc; ++t) {
-    const int m = m_of_k(cands[t]);
-    const double th = theta[theta_slot(cands[t])];
+    const int m = LG_M_OF(cands[t]);
+    const double th = LG_THETA(theta, cands[t]);
     if (ipow(nI2, m / 2) * nB <= ipow(th, m + 1)) {
       hi = t;
       break;
@@ -377,12 +426,12 @@ static __device__ int order_search(Ops& ops, const double* Acur, const double* A
   }
   if (lo >= hi) return cands[hi];
   for (int t = lo; t < hi; ++t) {
-    const int m = m_of_k(cands[t]);
-    const double th = theta[theta_slot(cands[t])];
+    const int m = LG_M_OF(cands[t]);
+    const double th = LG_THETA(theta, cands[t]);
     EstState st{-1.0, -1.0, m, 0};
     double a;
     if (alpha_test(ops, Acur, AI2, n, nB, nI2, m, th, st, &a)) return cands[t];
-    const double thn = theta[theta_slot(cands[t + 1])];
+    const double thn = LG_THETA(theta, cands[t + 1]);
     const double t1 = (st.t_m >= 0.0) ? st.t_m : (m == 2 ? nI2 : ipow(nI2, m / 2));
     if (t1 <= ipow(thn, m)) {
       double t2 = st.t_m1;
@@ -587,8 +636,75 @@ static __device__ __forceinline__ double y64(int k, int i) {  // y_i, i = 2..k+2
 // (Acur), P_3 = X^2 (A2) given. For Algorithm 1, scale = -2^s (eq. logipASTM
 // and the final squaring step): a power of two, so it changes no rounding.
 // ---------------------------------------------------------------------------
+#if LG_WITH_K6
+// k = 6 in the slot's seven matrices. P_2 .. P_6 fill Acur, A2, Y, W1, W2 and
+// the factors of P_7 = (sum h_{5,i} P_i)(sum g_{5,i} P_i) take T1, T2. Before
+// that product, one elementwise pass replaces P_2 .. P_6 by the three
+// combinations of them the rest needs (same element in, same element out, so
+// in place): C_L = sum_{i<=6} h_{6,i} P_i, C_R = sum_{i<=6} g_{6,i} P_i and
+// C_Y = sum_{i<=6} y_i P_i. Then P_7 goes to W1, the last factors are
+// C_L + h_{6,7} P_7 and C_R + g_{6,7} P_7, and the last product's epilogue
+// adds scale (C_Y + y_7 P_7): z = y_8 P_8 + sum_{i<=7} y_i P_i.
+template <class Ops>
+static __device__ LG_OUTLINED void graph_eval_k6(Ops& ops, int n, Slot& M, double scale, OutView out) {
+  double* P[7] = {nullptr, nullptr, M.Acur, M.A2, M.Y, M.W1, M.W2};
+  EpiTerms none;
+  none.count = 0;
+  int t = 0;  // index of h_{j,2} in c_h6
+  for (int j = 2; j <= 5; t += j, ++j) {
+    EpiTerms hl, gl;
+    hl.count = gl.count = j;
+    for (int i = 2; i <= j + 1; ++i) {
+      hl.M[i - 2] = gl.M[i - 2] = P[i];
+      hl.c[i - 2] = c_h6[t + i - 2];
+      gl.c[i - 2] = c_g6[t + i - 2];
+    }
+    ops.lincomb(n, hl, M.T1);
+    ops.lincomb(n, gl, M.T2);
+    if (j < 5) {
+      ops.tally(2, 1);
+      ops.gemm(n, M.T1, 0.0, M.T2, 0.0, 1.0, none, OutView{P[j + 2], 0});
+    }
+  }
+  // t = 14: h_{6,2..7}, g_{6,2..7}
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t e = ops.tid(); e < nn; e += ops.nthreads()) {
+    double v[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) v[i] = P[i + 2][e];
+    double cl = 0.0, cr = 0.0, cy = v[0];  // y_2 = 1
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      cl = fma(c_h6[t + i], v[i], cl);
+      cr = fma(c_g6[t + i], v[i], cr);
+    }
+#pragma unroll
+    for (int i = 1; i < 5; ++i) cy = fma(c_y6[i - 1], v[i], cy);
+    P[2][e] = cl;
+    P[3][e] = cr;
+    P[4][e] = cy;
+  }
+  ops.sync();
+  ops.tally(2, 1);
+  ops.gemm(n, M.T1, 0.0, M.T2, 0.0, 1.0, none, OutView{M.W1, 0});  // P_7
+  EpiTerms l6{{M.Acur, M.W1}, {1.0, c_h6[t + 5]}, 2};
+  EpiTerms r6{{M.A2, M.W1}, {1.0, c_g6[t + 5]}, 2};
+  ops.lincomb(n, l6, M.W2);
+  ops.lincomb(n, r6, M.T1);
+  EpiTerms e{{M.Y, M.W1}, {scale, scale * c_y6[4]}, 2};
+  ops.tally(2, 1);
+  ops.gemm(n, M.W2, 0.0, M.T1, 0.0, scale * c_y6[5], e, out);
+}
+#endif
+
 template <class Ops>
 static __device__ void graph_eval(Ops& ops, int k, int n, Slot& M, double scale, OutView out) {
+#if LG_WITH_K6
+  if (k == 6) {
+    graph_eval_k6(ops, n, M, scale, out);
+    return;
+  }
+#endif
   double* P2 = M.Acur;
   double* P3 = M.A2;
   if (k == 1) {  // z = X + X^2/2 (Taylor T_2)
@@ -760,8 +876,8 @@ static __device__ void run_execute(Ops& ops, const SmallParams& p, int b, int n,
   }
   double* dvec = p.balance ? p.bal + (int64_t)b * p.bal_stride : nullptr;
   if (dvec) balance_matrix(ops, M.Acur, n, dvec);
-  const int m = m_of_k(km);
-  const double th = p.theta[theta_slot(km)];
+  const int m = LG_M_OF(km);
+  const double th = LG_THETA(p.theta, km);
   double nB = ops.norm1(M.Acur, n, 1.0), nI2 = 0.0;
   int s = 0, have_ai2 = 0, info = 0, finish = nB <= th;
   double alpha = nB;
@@ -848,8 +964,8 @@ static __device__ void run_plan(Ops& ops, const SmallParams& p, int b, int n, in
     }
     return;
   }
-  const int m = m_of_k(km);
-  const double th = p.theta[theta_slot(km)];
+  const int m = LG_M_OF(km);
+  const double th = LG_THETA(p.theta, km);
   const double nB = ops.norm1(M.Acur, n, 1.0);
   EstState st{-1.0, -1.0, m, 0};
   int fin;
@@ -904,7 +1020,7 @@ static __device__ void run_sqrt(Ops& ops, const SmallParams& p, int b, int n, in
 template <class Ops>
 static __device__ void run_graph(Ops& ops, const SmallParams& p, int b, int n, int64_t off, Slot& M) {
   const int k = p.k_in[b];
-  if (!(k >= 1 && k <= 5)) {
+  if (!(k >= 1 && k <= LG_MAX_ORDER)) {
     if (ops.leader() && p.info) p.info[b] = -1;
     return;
   }

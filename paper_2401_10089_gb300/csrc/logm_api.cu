@@ -59,8 +59,9 @@ int batch_n_max(const logm_batch* b) {
 
 int opts_ok(const logm_options* o) {
   if (!o) return 0;
-  if (o->k_max < 1 || o->k_max > 5) return 0;
+  if (o->k_max < 1 || o->k_max > 6) return 0;
   if (o->precision < LOGM_PREC_FP64 || o->precision > LOGM_PREC_BF16X3) return 0;
+  if (o->k_max == 6 && o->precision != LOGM_PREC_FP64) return 0;  // split-precision graph: k <= 5
   if (o->max_sqrt < 0 || o->max_sqrt > 1000) return 0;
   if (o->max_db_iter < 1 || o->max_db_iter > 1000) return 0;
   if (o->db_form != LOGM_DB_TWO_INVERSE && o->db_form != LOGM_DB_PRODUCT) return 0;
@@ -281,6 +282,7 @@ int logm_execute_host(const logm_batch* batch, const logm_options* opts, const v
                       void* stream) {
   if (batch_n_max(batch) <= 0 || !opts_ok(opts)) return LOGM_ERR_INVALID_ARG;
   if (batch->n_uniform <= 0) return LOGM_ERR_UNSUPPORTED;
+  if (opts->k_max == 6 && batch->n_uniform > lg::kSmallMaxN) return LOGM_ERR_UNSUPPORTED;
   if (batch->count == 0) return LOGM_SUCCESS;
   if (!A_host || !L_host || !info_host) return LOGM_ERR_INVALID_ARG;
   const size_t need = logm_host_workspace_size(batch, opts);
@@ -378,6 +380,7 @@ int logm_plan(const logm_batch* batch, const logm_options* opts, const void* A, 
               size_t ws_bytes, void* stream) {
   const int n_max = batch_n_max(batch);
   if (n_max <= 0 || !opts_ok(opts)) return LOGM_ERR_INVALID_ARG;
+  if (opts->k_max == 6 && n_max > lg::kSmallMaxN) return LOGM_ERR_UNSUPPORTED;
   if (batch->count == 0) return LOGM_SUCCESS;
   if (!A || !finish_dev || !k_dev || !alpha_dev || !info_dev) return LOGM_ERR_INVALID_ARG;
   if (int r = check_ws(batch, ws, ws_bytes)) return r;
@@ -458,6 +461,8 @@ int logm_execute(const logm_batch* batch, const logm_options* opts, const void* 
                  void* ws, size_t ws_bytes, void* stream) {
   const int n_max = batch_n_max(batch);
   if (n_max <= 0 || !opts_ok(opts)) return LOGM_ERR_INVALID_ARG;
+  // k = 6: one-block-per-matrix kernels only, and no adjoint for it
+  if (opts->k_max == 6 && (n_max > lg::kSmallMaxN || ctx)) return LOGM_ERR_UNSUPPORTED;
   if (batch->count == 0) return LOGM_SUCCESS;
   if (!A || !L || !info_dev) return LOGM_ERR_INVALID_ARG;
   if (int r = check_ws(batch, ws, ws_bytes, opts->precision)) return r;
@@ -513,6 +518,7 @@ int logm_backward(const logm_batch* batch, const logm_options* opts, const void*
                   void* stream) {
   const int n_max = batch_n_max(batch);
   if (n_max <= 0 || !opts_ok(opts)) return LOGM_ERR_INVALID_ARG;
+  if (opts->k_max == 6) return LOGM_ERR_UNSUPPORTED;
   if (batch->count == 0) return LOGM_SUCCESS;
   if (!A || !ctx || !dL || !dA || !info_dev) return LOGM_ERR_INVALID_ARG;
   if (n_max > lg::kSmallMaxN) return LOGM_ERR_UNSUPPORTED;

@@ -9,10 +9,11 @@
 
 namespace lg {
 
-// Theta_{m_k} of the paper's backward-error table (Sec. 5), k = 1..5: the
+// Theta_{m_k} of the paper's backward-error table (Sec. 5), k = 1..6: the
 // default bounds of the loop test and the order search (each entry point's
-// options may override them).
-constexpr double kThetaPaper[5] = {1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1};
+// options may override the first five; k = 6 is taken by the
+// one-block-per-matrix kernels only).
+constexpr double kThetaPaper[6] = {1.83e-8, 1.53e-4, 1.33e-2, 9.31e-2, 2.46e-1, 3.72e-1};
 
 // Host set-up done once per device (e.g. a kernel's shared-memory attribute),
 // safe when several threads drive several devices: run() calls f() with the

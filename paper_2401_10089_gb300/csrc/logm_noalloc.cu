@@ -62,7 +62,7 @@ extern "C" int logm_execute_noalloc(const logm_batch* batch, const logm_options*
       return LOGM_ERR_INVALID_ARG;
     n_max = batch->n_max;
   }
-  if (opts->k_max < 1 || opts->k_max > 5) return LOGM_ERR_INVALID_ARG;
+  if (opts->k_max < 1 || opts->k_max > 6) return LOGM_ERR_INVALID_ARG;
   if (opts->max_sqrt < 0 || opts->max_sqrt > 1000) return LOGM_ERR_INVALID_ARG;
   if (opts->max_db_iter < 1 || opts->max_db_iter > 1000) return LOGM_ERR_INVALID_ARG;
   if (opts->db_form != LOGM_DB_TWO_INVERSE && opts->db_form != LOGM_DB_PRODUCT) return LOGM_ERR_INVALID_ARG;

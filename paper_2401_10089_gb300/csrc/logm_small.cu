@@ -12,9 +12,12 @@
 //   Y     Denman-Beavers Y, later P_4
 //   W1,W2 inverses of X and Y, later P_5, P_6
 //   T1,T2 lin-comb nodes (the two factors of the next product)
+// These kernels also take k = 6 (the graph of logm_algo.cuh fits it in the
+// same seven matrices).
 #include <cmath>
 #include <cstdio>
 
+#define LG_WITH_K6 1
 #include "logm_internal.h"
 #include "block_ops.cuh"
 #include "logm_algo.cuh"
@@ -45,7 +48,7 @@ __global__ void __launch_bounds__(kThreads) k_order_keys(SmallParams p) {
   __shared__ Reduce red;
   int* hist = p.order_aux;
   int* bucket_of = p.order_aux + 2 * kOrderBuckets;
-  const double th = p.theta[theta_slot(p.k_max)];
+  const double th = LG_THETA(p.theta, p.k_max);
   for (int b = blockIdx.x; b < p.count; b += gridDim.x) {
     int n;
     int64_t off;

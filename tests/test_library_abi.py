@@ -45,9 +45,13 @@ def test_invalid_arguments_rejected_before_launch():
     b = _lib.LogmBatch()
     b.count, b.dtype, b.n_uniform, b.n_max = 1, 0, 8, 8
     o = _lib.LogmOptions()
-    o.k_max, o.precision, o.max_sqrt, o.max_db_iter = 6, 0, 40, 50  # k_max = 6 has no scheme
+    o.k_max, o.precision, o.max_sqrt, o.max_db_iter = 7, 0, 40, 50  # k_max = 7 has no scheme
     rc = L.logm_execute(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, None, None, 0, None)
     assert rc == _lib.ERR_INVALID_ARG
+    o.k_max, o.precision = 6, 1  # k = 6 has no split-precision graph
+    rc = L.logm_execute(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, None, None, 0, None)
+    assert rc == _lib.ERR_INVALID_ARG
+    o.precision = 0
     o.k_max, o.db_form = 5, 2  # no such Denman-Beavers form
     rc = L.logm_execute(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, None, None, 0, None)
     assert rc == _lib.ERR_INVALID_ARG
@@ -76,9 +80,35 @@ def test_execute_host_argument_checks():
     b.count = 0
     rc = L.logm_execute_host(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, 0, None)
     assert rc == _lib.SUCCESS  # empty batch: nothing to do
-    o.k_max = 6
+    o.k_max = 7
     rc = L.logm_execute_host(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, 0, None)
     assert rc == _lib.ERR_INVALID_ARG
+    o.k_max, b.n_uniform, b.n_max = 6, 300, 300  # k = 6: n <= 256 only
+    rc = L.logm_execute_host(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, 0, None)
+    assert rc == _lib.ERR_UNSUPPORTED
+
+
+def test_k6_option_limits():
+    # k_max = 6 is taken by the one-block-per-matrix kernels (n <= 256), with
+    # FP64 products and without the adjoint; everything else is refused
+    # before any CUDA call
+    from paper_2401_10089_gb300 import _lib
+    L = _lib.load()
+    b = _lib.LogmBatch()
+    b.count, b.dtype, b.n_uniform, b.n_max = 1, 0, 300, 300
+    o = _lib.LogmOptions()
+    o.k_max, o.precision, o.max_sqrt, o.max_db_iter = 6, 0, 40, 50
+    args = (None,) * 8 + (0, None)
+    assert L.logm_execute(ctypes.byref(b), ctypes.byref(o), *args) == _lib.ERR_UNSUPPORTED
+    assert L.logm_plan(ctypes.byref(b), ctypes.byref(o), *((None,) * 7), 0, None) == _lib.ERR_UNSUPPORTED
+    b.n_uniform = b.n_max = 64
+    ctx = ctypes.c_void_p(256)  # never dereferenced: refused first
+    rc = L.logm_execute(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, ctx, None, 0, None)
+    assert rc == _lib.ERR_UNSUPPORTED
+    rc = L.logm_backward(ctypes.byref(b), ctypes.byref(o), None, None, None, None, None, None, 0, None)
+    assert rc == _lib.ERR_UNSUPPORTED
+    L.logm_workspace_size.restype = ctypes.c_size_t
+    assert L.logm_workspace_size(ctypes.byref(b), ctypes.byref(o)) > 0
 
 
 def test_host_workspace_layout_size():

@@ -28,6 +28,11 @@ def test_fp64_device_tables():
     assert np.array_equal(table("logm_algo.cuh", "c_g5"), g)
     assert np.array_equal(table("logm_algo.cuh", "c_y5"), y)
     assert np.array_equal(table("logm_algo.cuh", "c_k4"), oracle.coeffs_k4())
+    # k = 6 (fitted; the golden file is the fit's output)
+    h6, g6, y6 = oracle.coeffs_k6()
+    assert np.array_equal(table("logm_algo.cuh", "c_h6"), h6)
+    assert np.array_equal(table("logm_algo.cuh", "c_g6"), g6)
+    assert np.array_equal(table("logm_algo.cuh", "c_y6"), y6[2:])
 
 
 def test_fp32_device_tables_are_the_rounded_values():
@@ -44,7 +49,7 @@ def test_theta_table_of_the_library():
     every entry point) against the paper's backward-error table (golden) and
     the oracle's copy."""
     src = open(os.path.join(CSRC, "logm_internal.h")).read()
-    m = re.search(r"constexpr\s+double\s+kThetaPaper\[5\]\s*=\s*\{([^}]*)\}", src)
+    m = re.search(r"constexpr\s+double\s+kThetaPaper\[6\]\s*=\s*\{([^}]*)\}", src)
     assert m
     dev = np.array([float(t) for t in re.findall(r"[-+]?\d+\.\d*(?:e[-+]?\d+)?", m.group(1))])
     gold = np.array([float(line.split()[3]) for line in open(os.path.join(GOLDEN, "theta_table.txt"))
