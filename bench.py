@@ -397,6 +397,37 @@ def main():
                            "speedup_vs_fp64": ms / (ms_fa + ms_fb)}
         forms[name] = ent
 
+    # the opt-in k = 6 order (k_max = 6, one-block-per-matrix kernels, n <= 256):
+    # the batch part of the same step, against the k_max = 5 run above
+    if not args.no_forms and n <= 256:
+        vopts = {**main, "k_max": 6}
+        try:
+            lg.logm_execute(A_dev, **vopts)
+            barrier()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = max(1, args.steps)
+            f0.record(stream)
+            for _ in range(reps):
+                L6, s6, k6, i6 = lg.logm_execute(A_dev, stats=st_fa, **vopts)
+            f1.record(stream)
+            barrier()
+            ms6 = f0.elapsed_time(f1) / reps
+            e6 = ((L6 - L).flatten(1).norm(dim=1) / L.flatten(1).norm(dim=1)).cpu().numpy()
+            sa = st_fa.cpu().numpy().reshape(-1, 4).sum(axis=0)
+            forms["k_max6"] = {
+                "options": vopts,
+                "note": "k_max = 6 is taken by the one-block-per-matrix kernels only (n <= 256)",
+                "batch256": {"ms": ms6, "matrices_per_s": count / (ms6 * 1e-3),
+                             "tflops": algorithmic_flops(st_fa.cpu().numpy(), n) / (ms6 * 1e-3) / 1e12,
+                             "speedup_vs_fp64": ms_a / ms6,
+                             "rel_err_vs_fp64": {"max": float(e6.max()), "median": float(np.median(e6))},
+                             "s_hist": np.bincount(s6.cpu().numpy()).tolist(),
+                             "k_hist": np.bincount(k6.cpu().numpy(), minlength=7).tolist(),
+                             "info_nonzero": int((i6.cpu().numpy() != 0).sum()),
+                             "work": {"db_iterations": int(sa[0]), "inverses": int(sa[1]), "products": int(sa[2])}}}
+        except RuntimeError as e:  # a refused call is recorded, not fatal to the step's own line
+            forms["k_max6"] = {"options": vopts, "error": str(e)}
+
     # differentiation form: 1024 SPD 64 x 64 (lambda log-uniform in [1e-2, 1e2]),
     # loss = sum(W o log A): forward with checkpoints, then the hand-written adjoint
     if not args.no_forms:
