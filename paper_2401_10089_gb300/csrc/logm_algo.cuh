@@ -77,7 +77,8 @@ static __constant__ double c_g6[20] = {
     0.5165656321507225, 0.1625662254422074, -0.2675459778240617, -0.03466835614054706,
     0.328082088789197, -0.34992616877127714, -1.3970630865902485, 2.542415746918083,
     -0.048059210298082834, 0.9420478294952318, -2.416723959179748, 1.3390816588113656};
-static __constant__ double c_y6[6] = {0.8200410102947662, -0.4825318072757668, -0.12989653721591463, -0.40476811140333024, 0.12143584229947445, 0.00977242585180227};
+static __constant__ double c_y6[6] = {0.8200410102947662,   -0.4825318072757668, -0.12989653721591463,
+                                      -0.40476811140333024, 0.12143584229947445, 0.00977242585180227};
 constexpr double kTheta6 = kThetaPaper[5];
 #endif
 
@@ -392,11 +393,6 @@ static __device__ int alpha_test(Ops& ops, const double* Acur, const double* AI2
 // loop's estimates (eqs. min_in, min_inp), max_in from the rough bound (eq.
 // roughmax_even; every available m_k is even), then an increasing scan that
 // takes k+1 at once when alpha_{m_k} is above Theta_k but not above Theta_{k+1}.
-#if LG_WITH_K6
-#define LG_OUTLINED __noinline__  // keeps the k = 6 plan out of the hot loops' registers
-#else
-#define LG_OUTLINED
-#endif
 template <class Ops>
 static __device__ int order_search(Ops& ops, const double* Acur, const double* AI2, int n, double nB, double nI2,
                             int k_max, const double* theta, const EstState* loop_est) {
@@ -645,8 +641,10 @@ static __device__ __forceinline__ double y64(int k, int i) {  // y_i, i = 2..k+2
 // C_Y = sum_{i<=6} y_i P_i. Then P_7 goes to W1, the last factors are
 // C_L + h_{6,7} P_7 and C_R + g_{6,7} P_7, and the last product's epilogue
 // adds scale (C_Y + y_7 P_7): z = y_8 P_8 + sum_{i<=7} y_i P_i.
+// Outlined: inlined, its temporaries raised the register pressure of the
+// whole execute kernel.
 template <class Ops>
-static __device__ LG_OUTLINED void graph_eval_k6(Ops& ops, int n, Slot& M, double scale, OutView out) {
+static __device__ __noinline__ void graph_eval_k6(Ops& ops, int n, Slot& M, double scale, OutView out) {
   double* P[7] = {nullptr, nullptr, M.Acur, M.A2, M.Y, M.W1, M.W2};
   EpiTerms none;
   none.count = 0;
