@@ -167,16 +167,23 @@ void orc_coeffs_k4(double* c) { memcpy(c, K4_C, sizeof(K4_C)); }
 static const double K6_H[20] = {
     -0.03542133528022389, 0.5305162167939017,  /* h_{2,2..3} */
     1.1735695507060024, 0.42664399607790565, -1.4401144598828934,  /* h_{3,2..4} */
-    -0.37722719586021003, 1.1748267828138759, -0.4355749562164976, -0.55350435103941,  /* h_{4,2..5} */
-    -0.13552704716524286, 0.483097031151113, -2.879391574437424, -0.779847925333845, -0.8268140965713336,  /* h_{5,2..6} */
-    4.549413425481621, -3.6536822467517673, -5.744611071943747, 3.2747363248058474, -3.4999222429973935, 5.3137561222344525}; /* h_{6,2..7} */
+    -0.37722719586021003, 1.1748267828138759, -0.4355749562164976,
+    -0.55350435103941,  /* h_{4,2..5} */
+    -0.13552704716524286, 0.483097031151113, -2.879391574437424,
+    -0.779847925333845, -0.8268140965713336,  /* h_{5,2..6} */
+    4.549413425481621, -3.6536822467517673, -5.744611071943747,
+    3.2747363248058474, -3.4999222429973935, 5.3137561222344525}; /* h_{6,2..7} */
 static const double K6_G[20] = {
     -0.25821891505961464, -0.5021334801772399,  /* g_{2,2..3} */
     1.1247378095155132, -0.7530860083722153, 2.656179396111579,  /* g_{3,2..4} */
-    -0.5198936929205077, -0.669272512275526, -1.2980185589839237, 0.5165656321507225,  /* g_{4,2..5} */
-    0.1625662254422074, -0.2675459778240617, -0.03466835614054706, 0.328082088789197, -0.34992616877127714,  /* g_{5,2..6} */
-    -1.3970630865902485, 2.542415746918083, -0.048059210298082834, 0.9420478294952318, -2.416723959179748, 1.3390816588113656}; /* g_{6,2..7} */
-static const double K6_Y[8] = {0.0, 1.0, 0.8200410102947662, -0.4825318072757668, -0.12989653721591463, -0.40476811140333024, 0.12143584229947445, 0.00977242585180227};
+    -0.5198936929205077, -0.669272512275526, -1.2980185589839237,
+    0.5165656321507225,  /* g_{4,2..5} */
+    0.1625662254422074, -0.2675459778240617, -0.03466835614054706,
+    0.328082088789197, -0.34992616877127714,  /* g_{5,2..6} */
+    -1.3970630865902485, 2.542415746918083, -0.048059210298082834,
+    0.9420478294952318, -2.416723959179748, 1.3390816588113656}; /* g_{6,2..7} */
+static const double K6_Y[8] = {0.0, 1.0, 0.8200410102947662, -0.4825318072757668, -0.12989653721591463,
+                               -0.40476811140333024, 0.12143584229947445, 0.00977242585180227};
 
 void orc_coeffs_k6(double* h, double* g, double* y) {
   memcpy(h, K6_H, sizeof(K6_H));
