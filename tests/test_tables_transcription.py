@@ -59,5 +59,5 @@ def test_theta_table_of_the_library():
     # no second copy of the table elsewhere in the library's sources
     for f in os.listdir(CSRC):
         if f != "logm_internal.h":
-            src = open(os.path.join(CSRC, f)).read()
-            assert "9.31e-2" not in src and "2.46e-1" not in src and "3.72e-1" not in src, f
+            code = re.sub(r"//[^\n]*|/\*.*?\*/", "", open(os.path.join(CSRC, f)).read(), flags=re.S)
+            assert "9.31e-2" not in code and "2.46e-1" not in code and "3.72e-1" not in code, f
