@@ -38,8 +38,10 @@
  *    Sec. 3 (degree 16, T_14 matched exactly) whose coefficients the paper
  *    does not print: solved here (orc_coeffs_k4), its Theta recomputed from
  *    them lands on the table's 9.31e-2; k = 5 is Table
- *    table_simple_experiment. k >= 6 have no coefficients in the paper, so
- *    the available orders are k in {1, 2, 3, 4, 5};
+ *    table_simple_experiment. k >= 6 have no coefficients in the paper;
+ *    k = 6 (opt-in, k_max = 6) is a scheme of the same form fitted here
+ *    (orc_coeffs_k6), used with the table's m_6 = 20 and Theta_6 = 0.372, so
+ *    the available orders are k in {1, ..., 6};
  *  - every square-root level runs eq. (ScalDB) as written (X_0 = A,
  *    Y_0 = I; Y_0 needs no inversion). Opt-in (orc_opts.reuse_root), a root
  *    of a root: from the second level on, the first Denman-Beavers step
