@@ -109,6 +109,12 @@ def test_k6_option_limits():
     assert rc == _lib.ERR_UNSUPPORTED
     L.logm_workspace_size.restype = ctypes.c_size_t
     assert L.logm_workspace_size(ctypes.byref(b), ctypes.byref(o)) > 0
+    # the allocation-free entry point takes k_max = 6 (an empty batch returns
+    # before any CUDA call) and refuses 7
+    b.count = 0
+    assert L.logm_execute_noalloc(ctypes.byref(b), ctypes.byref(o), *((None,) * 6)) == _lib.SUCCESS
+    o.k_max = 7
+    assert L.logm_execute_noalloc(ctypes.byref(b), ctypes.byref(o), *((None,) * 6)) == _lib.ERR_INVALID_ARG
 
 
 def test_host_workspace_layout_size():
