@@ -105,3 +105,20 @@ def test_execute_k6_f32_storage():
         Lr, d = oracle.logm(mats[b].astype(np.float64), k_max=6)
         assert int(info[b]) == 0
         assert rel(L[b].astype(np.float64), Lr) < 1e-6
+
+
+def test_full_size_sampled_k6():
+    """The batched FP64 configuration (512 x 256^2, A = I + E, ||E||_1 uniform
+    in [0.2, 5]) with k_max = 6: a seeded sample, the matrix with the most
+    roots and a matrix that took k = 6 against the oracle."""
+    A = workloads.identity_plus(512, 256, seed=1)
+    L, s, k, info = lg().logm_execute(dev(A), k_max=6)
+    torch.cuda.synchronize()
+    info = info.cpu().numpy()
+    assert (info == 0).all()
+    s, k, L = s.cpu().numpy(), k.cpu().numpy(), L.cpu().numpy()
+    assert (k == 6).any()
+    pick = np.random.default_rng(0).choice(512, 6, replace=False)
+    pick = np.concatenate([pick, [int(np.argmax(s)), int(np.argmax(k == 6))]])
+    for b in pick:
+        check_logm(A[b], L[b], int(s[b]), int(k[b]), int(info[b]), k_max=6)
