@@ -129,3 +129,15 @@ def test_logm_k6_random_matches_k5():
         assert d6["info"] == d5["info"] == oracle.OK
         assert d6["s"] <= d5["s"]
         assert rel(L6, L5) < 1e-12
+
+
+def test_plan_with_ai2_k6():
+    # s >= 1: the plan takes A_I2 = A_2 - 2A + I (eq. AI2) with A = A_2^{1/2};
+    # on a diagonal, alpha = max |mu - 1| exactly
+    lam = np.array([1.69, 0.64, 1.0])
+    X = np.diag(np.sqrt(lam))
+    AI2 = np.diag(lam) - 2 * X + np.eye(3)
+    fin, k, a = oracle.plan(X, AI2, k_max=6)
+    assert fin and k == 6 and a == pytest.approx(0.3, rel=1e-12)
+    fin, k, a = oracle.plan(X, AI2)  # k_max = 5: not finished at this level
+    assert not fin and k == 5
